@@ -1,0 +1,231 @@
+"""Euler numerics of the oracle: EOS, characteristic variables, WENO5-JS, Rusanov.
+
+Test infrastructure (see ``oracle/__init__``). FP64 numpy. Arrays carry the
+conserved variables on their first axis: U = (rho, rho u_0 .. rho u_{d-1}, rho e)
+(Sec. 3.1, Eqs. 1-3). The gas is calorically perfect with R = 1 (Sec. 6), so
+T = p / rho.
+"""
+import numpy as np
+
+# WENO5-JS constants (Sec. 3.2: 5-point WENO-JS nonlinear interpolation).
+EPS_WENO = 1.0e-6
+C13_12 = 13.0 / 12.0
+D0, D1, D2 = 0.0625, 0.625, 0.3125      # linear weights (1, 10, 5) / 16
+
+
+def primitives(U, dim, gamma):
+    """Primitive variables from conserved ones (Sec. 3.1, Eqs. 4-6, R = 1).
+
+    u_d = m_d / rho; p = (gamma - 1) (E - rho |u|^2 / 2); T = p / rho.
+    Returns (rho, [u_0..u_{d-1}], p, T).
+    """
+    gm1 = gamma - 1.0
+    rho = U[0]
+    u = [U[1 + d] / rho for d in range(dim)]
+    usq = u[0] * u[0]
+    for d in range(1, dim):
+        usq = usq + u[d] * u[d]
+    p = gm1 * (U[dim + 1] - 0.5 * rho * usq)
+    T = p / rho
+    return rho, u, p, T
+
+
+def conserved_from_primitive(rho, u, p, gamma):
+    """U from (rho, u, p): E = p / (gamma - 1) + rho |u|^2 / 2 (Sec. 3.1, Eqs. 4, 6)."""
+    gm1 = gamma - 1.0
+    dim = len(u)
+    usq = u[0] * u[0]
+    for d in range(1, dim):
+        usq = usq + u[d] * u[d]
+    out = [rho]
+    for d in range(dim):
+        out.append(rho * u[d])
+    out.append(p / gm1 + 0.5 * rho * usq)
+    return out
+
+
+def sound_speed(p, rho, gamma):
+    """c = sqrt(gamma p / rho) (Sec. 3.1, Eq. 7)."""
+    return np.sqrt(gamma * p / rho)
+
+
+def weno5_left(a, b, c, d, e):
+    """WENO5-JS nodal mid-point value at x_{i+1/2} from nodes i-2..i+2 (Sec. 3.2).
+
+    Candidates are the quadratic Lagrange interpolants of the three 3-point
+    sub-stencils evaluated at the mid-point; their linear combination with
+    weights (1, 10, 5)/16 is the 5-point interpolant (3, -20, 90, 60, -5)/128.
+    Smoothness indicators are the Jiang-Shu ones; alpha_k = d_k / (eps + beta_k)^2.
+    """
+    q0 = (3.0 * a - 10.0 * b + 15.0 * c) * 0.125
+    q1 = (-b + 6.0 * c + 3.0 * d) * 0.125
+    q2 = (3.0 * c + 6.0 * d - e) * 0.125
+    t0 = a - 2.0 * b + c
+    s0 = a - 4.0 * b + 3.0 * c
+    t1 = b - 2.0 * c + d
+    s1 = b - d
+    t2 = c - 2.0 * d + e
+    s2 = 3.0 * c - 4.0 * d + e
+    b0 = C13_12 * (t0 * t0) + 0.25 * (s0 * s0)
+    b1 = C13_12 * (t1 * t1) + 0.25 * (s1 * s1)
+    b2 = C13_12 * (t2 * t2) + 0.25 * (s2 * s2)
+    e0 = EPS_WENO + b0
+    e1 = EPS_WENO + b1
+    e2 = EPS_WENO + b2
+    a0 = D0 / (e0 * e0)
+    a1 = D1 / (e1 * e1)
+    a2 = D2 / (e2 * e2)
+    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2)
+
+
+def frozen_state(p_i, T_i, p_j, T_j, gamma):
+    """Frozen state of the characteristic projection at the face between nodes
+    i and j = i+1 (reading of Sec. 3.2, where the projection is deferred to the
+    authors' earlier work): pbar, Tbar are arithmetic means, rhobar = pbar / Tbar,
+    cbar = sqrt(gamma Tbar) (R = 1). Returns (z = rhobar cbar,
+    kappa = (gamma - 1) / (gamma rhobar))."""
+    pbar = 0.5 * (p_i + p_j)
+    Tbar = 0.5 * (T_i + T_j)
+    rbar = pbar / Tbar
+    cbar = np.sqrt(gamma * Tbar)
+    z = rbar * cbar
+    kap = (gamma - 1.0) / (gamma * rbar)
+    return z, kap
+
+
+def char_forward(q, z, kap):
+    """Characteristic fields of a node q = (p, un, ut, T) of the linearised
+    primitive system in (p, u, T): [p - z un, T - kappa p, ut..., p + z un]
+    (left eigenvectors for speeds u - c, u, u..., u + c)."""
+    p, un, ut, T = q
+    return [p - z * un, T - kap * p] + list(ut) + [p + z * un]
+
+
+def char_inverse(w, z, kap):
+    """Inverse of char_forward: p = (w1 + w5)/2, un = (w5 - w1)/(2 z),
+    T = w2 + kappa p, ut = w_t. Returns (p, un, ut, T)."""
+    nf = len(w)
+    p = 0.5 * (w[0] + w[nf - 1])
+    un = (w[nf - 1] - w[0]) / (2.0 * z)
+    T = w[1] + kap * p
+    return p, un, list(w[2:nf - 1]), T
+
+
+def face_flux(P, dim, gamma):
+    """Rusanov flux at the face between pencil nodes 2 and 3 (Sec. 3.2, Eqs. 11-12).
+
+    P is a list of 6 pencil nodes (i-2 .. i+3), each a tuple (p, un, ut, T) where
+    un is the velocity normal to the face and ut is the list of tangential
+    velocities in increasing dimension order. Arrays broadcast over faces.
+
+    Steps:
+      1. frozen state at the face: pbar, Tbar (arithmetic means of nodes i, i+1),
+         rhobar = pbar / Tbar, cbar = sqrt(gamma Tbar), z = rhobar cbar,
+         kappa = (gamma - 1) / (gamma rhobar);
+      2. characteristic variables of the linearised primitive system in (p, u, T):
+         w1 = p - z un (speed u - c), w2 = T - kappa p (speed u),
+         w_t = ut (speed u), w5 = p + z un (speed u + c);
+      3. left- and right-biased WENO5-JS interpolation of each field;
+      4. back to p = (w1 + w5) / 2, un = (w5 - w1) / (2 z), T = w2 + kappa p,
+         with a first-order fallback (nodes i, i+1) if p or T is not positive;
+      5. conserved states and Euler fluxes at both sides, S = max(c + |un|) and
+         F = (F^R + F^L)/2 - S (U^R - U^L)/2.
+    Returns the flux in pencil order (mass, normal momentum, tangential momenta,
+    energy).
+    """
+    gm1 = gamma - 1.0
+    nt = dim - 1
+    p2, un2, ut2, T2 = P[2]
+    p3, un3, ut3, T3 = P[3]
+    z, kap = frozen_state(p2, T2, p3, T3, gamma)
+    W = [char_forward(P[k], z, kap) for k in range(6)]
+    nf = nt + 3
+    wl = [weno5_left(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f]) for f in range(nf)]
+    wr = [weno5_left(W[5][f], W[4][f], W[3][f], W[2][f], W[1][f]) for f in range(nf)]
+    pL, unL, utL, TL = char_inverse(wl, z, kap)
+    pR, unR, utR, TR = char_inverse(wr, z, kap)
+    bad = ~((pL > 0.0) & (TL > 0.0) & (pR > 0.0) & (TR > 0.0))
+    if np.any(bad):
+        pL = np.where(bad, p2, pL)
+        unL = np.where(bad, un2, unL)
+        TL = np.where(bad, T2, TL)
+        utL = [np.where(bad, ut2[j], utL[j]) for j in range(nt)]
+        pR = np.where(bad, p3, pR)
+        unR = np.where(bad, un3, unR)
+        TR = np.where(bad, T3, TR)
+        utR = [np.where(bad, ut3[j], utR[j]) for j in range(nt)]
+
+    def side(p, un, ut, T):
+        rho = p / T
+        c = np.sqrt(gamma * T)
+        usq = un * un
+        for j in range(nt):
+            usq = usq + ut[j] * ut[j]
+        E = p / gm1 + 0.5 * rho * usq
+        mn = rho * un
+        U = [rho, mn] + [rho * ut[j] for j in range(nt)] + [E]
+        F = [mn, mn * un + p] + [mn * ut[j] for j in range(nt)] + [(E + p) * un]
+        s = c + np.abs(un)
+        return U, F, s
+
+    UL, FL, sL = side(pL, unL, utL, TL)
+    UR, FR, sR = side(pR, unR, utR, TR)
+    hS = 0.5 * np.maximum(sR, sL)
+    return [0.5 * (FR[v] + FL[v]) - hS * (UR[v] - UL[v]) for v in range(dim + 2)]
+
+
+def pencil_to_global(F, dim, d):
+    """Map a flux in pencil order (mass, normal, tangentials, energy) back to
+    the global order (mass, m_0 .. m_{d-1}, energy) for a face normal to d."""
+    tdims = [e for e in range(dim) if e != d]
+    out = [None] * (dim + 2)
+    out[0] = F[0]
+    out[1 + d] = F[1]
+    for j, e in enumerate(tdims):
+        out[1 + e] = F[2 + j]
+    out[dim + 1] = F[dim + 1]
+    return out
+
+
+def patch_rhs(A, dim, N, g, dx, gamma):
+    """Right-hand side R = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d on a patch interior
+    (Sec. 3.2, Eq. 10: divergence of the Riemann fluxes; dims in order x, y, z).
+
+    A: slot array (nv, Z, Y, X) with g ghost layers in every active dimension
+    (array axis 3 - d holds dimension d). Returns (R, faces) where R has the
+    interior shape (nv, [N]*dim reversed) and faces[d] = (F_low, F_high): the
+    fluxes on the low (index 0) and high (index N) boundary faces of dimension d,
+    in global variable order, each of shape (nv, interior transverse shape).
+    """
+    rho, u, p, T = primitives(A, dim, gamma)
+    nv = dim + 2
+    inner = [slice(None)] * 4
+    for d in range(dim):
+        inner[3 - d] = slice(g, g + N)
+    R = None
+    faces = {}
+    for d in range(dim):
+        ax = 3 - d
+        tdims = [e for e in range(dim) if e != d]
+        P = []
+        for k in range(6):
+            sl = list(inner)
+            sl[ax] = slice(k, k + N + 1)   # faces i+1/2, i = -1..N-1
+            sl = tuple(sl[1:])
+            P.append((p[sl], u[d][sl], [u[e][sl] for e in tdims], T[sl]))
+        Fp = face_flux(P, dim, gamma)
+        F = pencil_to_global(Fp, dim, d)
+        F = np.stack(F)                      # (nv, ..., N+1 along ax)
+        hi = [slice(None)] * 4
+        lo = [slice(None)] * 4
+        hi[ax] = slice(1, N + 1)
+        lo[ax] = slice(0, N)
+        div = (F[tuple(hi)] - F[tuple(lo)]) / dx[d]
+        R = -div if R is None else R - div
+        f_lo = [slice(None)] * 4
+        f_hi = [slice(None)] * 4
+        f_lo[ax] = 0
+        f_hi[ax] = N
+        faces[d] = (F[tuple(f_lo)].copy(), F[tuple(f_hi)].copy())
+    assert R.shape[0] == nv
+    return R, faces

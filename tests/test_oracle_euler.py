@@ -1,0 +1,262 @@
+"""Pins of the oracle's Euler numerics against closed forms, library routines
+and the mathematics of Sec. 3 (no GPU)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import euler, riemann
+from oracle.amr import Oracle, dmr_states, splitmix64
+from synth import workload
+
+GOLD = os.path.join(os.path.dirname(__file__), 'golden')
+
+
+def lagrange_at(xs, ys, x):
+    """Interpolating polynomial through (xs, ys) evaluated at x (numpy polyfit)."""
+    c = np.polyfit(np.asarray(xs, float), np.asarray(ys, float), len(xs) - 1)
+    return np.polyval(c, x)
+
+
+# ---------------------------------------------------------------- WENO5-JS
+def test_weno_candidates_are_quadratic_interpolants():
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=5)
+    a, b, c, d, e = v
+    q0 = (3.0 * a - 10.0 * b + 15.0 * c) * 0.125
+    q1 = (-b + 6.0 * c + 3.0 * d) * 0.125
+    q2 = (3.0 * c + 6.0 * d - e) * 0.125
+    # nodes at -2..2, mid-point at 0.5 (Sec. 3.2: interpolation to the staggered edge)
+    assert q0 == pytest.approx(lagrange_at([-2, -1, 0], v[0:3], 0.5), rel=1e-12, abs=1e-12)
+    assert q1 == pytest.approx(lagrange_at([-1, 0, 1], v[1:4], 0.5), rel=1e-12, abs=1e-12)
+    assert q2 == pytest.approx(lagrange_at([0, 1, 2], v[2:5], 0.5), rel=1e-12, abs=1e-12)
+
+
+def test_weno_smooth_limit_is_5point_lagrange(monkeypatch):
+    # with eps >> beta the nonlinear weights reach the linear ones (Sec. 3.2)
+    monkeypatch.setattr(euler, 'EPS_WENO', 1e30)
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        v = rng.normal(size=5)
+        ref = lagrange_at([-2, -1, 0, 1, 2], v, 0.5)
+        got = euler.weno5_left(*v)
+        assert got == pytest.approx(ref, rel=1e-12, abs=1e-12)
+        # and the printed weights (3, -20, 90, 60, -5)/128 are that interpolant
+        assert ref == pytest.approx(np.dot([3, -20, 90, 60, -5], v) / 128.0, rel=1e-12, abs=1e-12)
+
+
+def test_weno_constant_and_order():
+    for c in (1.0, 0.3, 1e-3, 7.5):
+        assert euler.weno5_left(c, c, c, c, c) == pytest.approx(c, rel=2e-16)
+    # fifth-order interpolation error of a smooth function
+    errs = []
+    for h in (0.1, 0.05, 0.025):
+        x = np.arange(-2, 3) * h
+        v = np.sin(1.0 + x)
+        errs.append(abs(euler.weno5_left(*v) - math.sin(1.0 + 0.5 * h)))
+    assert errs[0] / errs[1] > 20.0 and errs[1] / errs[2] > 20.0
+
+
+def test_weno_step_gets_no_weight():
+    # a jump between nodes i+1 and i+2: the stencils containing it get ~0 weight
+    v = np.array([0.0, 0.0, 0.0, 0.0, 1.0])
+    assert abs(euler.weno5_left(*v)) < 1e-6
+    v = np.array([1.0, 1.0, 1.0, 1.0, 0.0]) * 2.0
+    assert abs(euler.weno5_left(*v) - 2.0) < 1e-6
+
+
+# ------------------------------------------------- characteristic projection
+def primitive_jacobian(p, u, T, gamma, nt):
+    """A of q_t + A q_x = 0 for q = (p, un, ut..., T), derived from Eqs. 1-3 with
+    R = 1: p_t + u p_x + rho c^2 u_x = 0, u_t + u u_x + p_x / rho = 0,
+    ut_t + u ut_x = 0, T_t + u T_x + (gamma - 1) T u_x = 0."""
+    rho = p / T
+    c2 = gamma * p / rho
+    n = nt + 3
+    A = np.eye(n) * u
+    A[0, 1] = rho * c2
+    A[1, 0] = 1.0 / rho
+    A[n - 1, 1] = (gamma - 1.0) * T
+    return A
+
+
+@pytest.mark.parametrize('nt', [0, 1, 2])
+def test_characteristic_transform_diagonalises(nt):
+    gamma = 1.4
+    p, u, T = 0.7, 0.3, 1.9
+    z, kap = euler.frozen_state(p, T, p, T, gamma)
+    n = nt + 3
+
+    def q_of(vec):
+        return (vec[0], vec[1], list(vec[2:2 + nt]), vec[n - 1])
+
+    Lm = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        Lm[:, j] = euler.char_forward(q_of(e), z, kap)
+    Rm = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        pp, un, ut, TT = euler.char_inverse(list(e), z, kap)
+        Rm[:, j] = [pp, un] + list(ut) + [TT]
+    assert np.allclose(Lm @ Rm, np.eye(n), atol=1e-14)
+    A = primitive_jacobian(p, u, T, gamma, nt)
+    D = Lm @ A @ Rm
+    c = math.sqrt(gamma * T)
+    speeds = [u - c, u] + [u] * nt + [u + c]
+    assert np.allclose(D, np.diag(speeds), atol=1e-12)
+
+
+# ------------------------------------------------------------ Rusanov flux
+def euler_flux(rho, un, ut, p, gamma):
+    E = p / (gamma - 1.0) + 0.5 * rho * (un * un + sum(x * x for x in ut))
+    return [rho * un, rho * un * un + p] + [rho * un * x for x in ut] + [(E + p) * un], \
+        [rho, rho * un] + [rho * x for x in ut] + [E]
+
+
+def rusanov_ref(Lst, Rst, gamma):
+    """Eqs. 11-12 written out: F = (F^R + F^L)/2 - S (U^R - U^L)/2,
+    S = max(c^R + |u^R|, c^L + |u^L|)."""
+    FL, UL = euler_flux(*Lst, gamma)
+    FR, UR = euler_flux(*Rst, gamma)
+    cL = math.sqrt(gamma * Lst[3] / Lst[0])
+    cR = math.sqrt(gamma * Rst[3] / Rst[0])
+    S = max(cR + abs(Rst[1]), cL + abs(Lst[1]))
+    return [0.5 * (FR[v] + FL[v]) - 0.5 * S * (UR[v] - UL[v]) for v in range(len(FL))]
+
+
+def node(rho, un, ut, p):
+    return (p, un, list(ut), p / rho)
+
+
+@pytest.mark.parametrize('nt', [0, 1, 2])
+def test_rusanov_uniform_state_is_physical_flux(nt):
+    gamma = 1.4
+    st = (1.3, 0.4, [0.2, -0.1][:nt], 0.9)
+    P = [node(*st) for _ in range(6)]
+    F = euler.face_flux(P, nt + 1, gamma)
+    Fref, _ = euler_flux(*st, gamma)
+    assert np.allclose(F, Fref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize('nt', [0, 1, 2])
+def test_rusanov_step_data_gives_eq11(nt):
+    # nodes i-2..i on the left state, i+1..i+3 on the right state: WENO keeps
+    # the one-sided values, so the face flux is Eq. 11 of the two states
+    gamma = 1.4
+    Lst = (1.0, 0.75, [0.1, 0.2][:nt], 1.0)
+    Rst = (0.125, -0.2, [0.3, -0.4][:nt], 0.1)
+    P = [node(*Lst)] * 3 + [node(*Rst)] * 3
+    F = euler.face_flux(P, nt + 1, gamma)
+    ref = rusanov_ref(Lst, Rst, gamma)
+    assert np.allclose(F, ref, rtol=1e-9, atol=1e-9)
+
+
+# --------------------------------------------------------- exact Riemann solver
+def test_exact_riemann_sod_digits():
+    g = json.load(open(os.path.join(GOLD, 'sod_exact.json')))
+    ws = riemann.wave_structure(tuple(g['left']), tuple(g['right']), g['gamma'])
+    t, x0 = g['t'], g['x0']
+    tol = 0.6e-7
+    assert abs(ws['p'] - g['p_star']) < tol
+    assert abs(ws['u'] - g['u_star']) < tol
+    assert abs(ws['rho_l'] - g['rho_star_left']) < tol
+    assert abs(ws['rho_r'] - g['rho_star_right']) < tol
+    assert abs(ws['right'][1] - g['shock_speed']) < tol
+    assert abs(x0 + ws['left'][1] * t - g['x_head']) < tol
+    assert abs(x0 + ws['left'][2] * t - g['x_tail']) < tol
+    assert abs(x0 + ws['contact'] * t - g['x_contact']) < tol
+    assert abs(x0 + ws['right'][1] * t - g['x_shock']) < tol
+
+
+def test_exact_riemann_jump_relations():
+    # Rankine-Hugoniot across the right shock (mass and momentum flux in the
+    # shock frame) and the isentrope p / rho^gamma across the left rarefaction
+    gamma = 1.4
+    L, R = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    ws = riemann.wave_structure(L, R, gamma)
+    s = ws['right'][1]
+    r1, u1, p1 = R
+    r2, u2, p2 = ws['rho_r'], ws['u'], ws['p']
+    assert r1 * (u1 - s) == pytest.approx(r2 * (u2 - s), rel=1e-12)
+    assert r1 * (u1 - s) ** 2 + p1 == pytest.approx(r2 * (u2 - s) ** 2 + p2, rel=1e-12)
+    assert L[2] / L[0] ** gamma == pytest.approx(ws['p'] / ws['rho_l'] ** gamma, rel=1e-12)
+
+
+def test_dmr_states_closed_form():
+    g = json.load(open(os.path.join(GOLD, 'dmr_states.json')))
+    pre, post = dmr_states(1.4)
+    assert pre == (1.4, 0.0, 0.0, 1.0)
+    assert post[0] == pytest.approx(g['post']['rho'], rel=1e-14)
+    assert post[3] == pytest.approx(g['post']['p'], rel=1e-14)
+    sp = math.hypot(post[1], post[2])
+    assert sp == pytest.approx(g['post']['speed'], rel=1e-14)
+    assert post[1] / sp == pytest.approx(g['post']['direction'][0], rel=1e-14)
+    assert post[2] / sp == pytest.approx(g['post']['direction'][1], rel=1e-14)
+
+
+def test_splitmix64_reference_outputs():
+    g = json.load(open(os.path.join(GOLD, 'splitmix64.json')))
+    xi = splitmix64(g['seed'], np.arange(len(g['outputs_hex'])))
+    for v, h in zip(xi, g['outputs_hex']):
+        assert int(v * 2.0 ** 53) == int(h, 16) >> 11
+
+
+# ------------------------------------------------------- whole-solver pins
+def run_to(o, t_end, regrid=True):
+    while o.t < t_end - 1e-14:
+        o.step()
+        if regrid:
+            o.regrid()
+    return o
+
+
+def sod_l1(levels):
+    w = workload('sod', levels=levels)
+    o = run_to(Oracle(w), w['t_end'])
+    rho = o.leaf_field(0)[0, 0]
+    x = (np.arange(rho.size) + 0.5) / rho.size
+    ex, _, _ = riemann.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, x, 0.5, o.t)
+    return float(np.mean(np.abs(rho - ex))), o
+
+
+def test_sod_converges_to_exact_solution():
+    e1, _ = sod_l1(1)
+    e2, o2 = sod_l1(2)
+    assert e1 < 0.012
+    assert e2 < 0.8 * e1
+    # the ends stay (up to exponentially small WENO tails) at rest: mass and
+    # energy are conserved, the momentum grows by the pressure difference times t
+    s = o2.cons_sums()
+    assert s[0] == pytest.approx(0.5625, rel=1e-10)
+    assert s[2] == pytest.approx(1.375, rel=1e-10)
+    assert s[1] == pytest.approx(0.9 * 0.2, rel=1e-9)
+
+
+def test_density_wave_second_order():
+    errs = []
+    for n in (32, 64):
+        w = workload('density_wave', base_cells=(n, 1, 1), patch=16, t_end=0.1)
+        o = run_to(Oracle(w), 0.1, regrid=False)
+        rho = o.leaf_field(0)[0, 0]
+        x = (np.arange(n) + 0.5) / n
+        ex = 1.0 + 0.2 * np.sin(2.0 * math.pi * (x - o.t))
+        errs.append(np.mean(np.abs(rho - ex)))
+    assert errs[0] / errs[1] > 3.5
+
+
+def test_constant_state_preserved():
+    w = workload('constant')
+    o = Oracle(w)
+    for _ in range(4):
+        o.step()
+        o.regrid()
+    for k in o.mesh.canonical():
+        A = o.U[k][o.inner()]
+        assert np.allclose(A[0], 1.0, rtol=0, atol=1e-14)
+        assert np.allclose(A[1], 0.3, rtol=0, atol=1e-14)
+        assert np.allclose(A[2], -0.2, rtol=0, atol=1e-14)

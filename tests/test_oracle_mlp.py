@@ -1,0 +1,89 @@
+"""Pins of the oracle's refinement-indicator network (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from synth import mlp_init
+
+
+def random_samples(rng, n):
+    """1D 5-point samples (rho, u, p) with a mix of smooth data and jumps."""
+    s = np.empty((n, 5, 3))
+    base = rng.uniform(0.5, 2.0, size=(n, 1, 3))
+    s[:] = base
+    s[:, :, 1] = rng.normal(0, 0.5, size=(n, 5))
+    jump = rng.uniform(size=n) < 0.5
+    pos = rng.integers(1, 5, size=n)
+    for i in np.nonzero(jump)[0]:
+        s[i, pos[i]:, 0] *= rng.uniform(0.2, 3.0)
+        s[i, pos[i]:, 2] *= rng.uniform(0.2, 3.0)
+    s[:, :, 0] *= 1.0 + 0.01 * rng.normal(size=(n, 5))
+    return s
+
+
+@pytest.mark.parametrize('dim', [1, 2, 3])
+def test_gradient_matches_finite_differences(dim):
+    rng = np.random.default_rng(0)
+    smp = random_samples(rng, 16)
+    X = mlp.embedded_features(smp, dim, 1.4)
+    y = np.repeat(mlp.plain_flag_1d(smp, 0.05, 0.05), 2 * dim).astype(np.float64)
+    params = mlp_init(0, mlp.k_in(dim))
+    pw = mlp.bce_pos_weight(y)
+    _, g = mlp.loss_and_grad(params, X, y, pw)
+    gvec = mlp.flatten(g)
+    idx, fd = mlp.gradient_fd(params, X, y, pw, h=1e-6, n_probe=40, seed=1)
+    assert np.allclose(gvec[idx], fd, rtol=1e-5, atol=1e-9)
+
+
+@pytest.mark.parametrize('dim', [1, 2, 3])
+def test_embedding_keeps_the_plain_flag(dim):
+    # the plain sensor evaluated on the d-dimensional embedded stencil (centre
+    # and its +-1 neighbours along every axis) equals the 1D flag: transverse
+    # differences vanish
+    rng = np.random.default_rng(1)
+    smp = random_samples(rng, 200)
+    f1 = mlp.plain_flag_1d(smp, 0.05, 0.05)
+    offs = mlp.stencil_offsets(dim)
+    centre = offs.index((0, 0, 0))
+    for a in range(dim):
+        for s in (-1, 1):
+            rho, u, p = mlp.embed_1d(smp, dim, a, s)
+            flag = np.zeros(len(smp), dtype=bool)
+            for phi, th in ((rho, 0.05), (p, 0.05)):
+                for d in range(dim):
+                    e = [0, 0, 0]
+                    e[d] = 1
+                    ip = offs.index(tuple(e))
+                    im = offs.index(tuple(-x for x in e))
+                    fm, f0, fp = phi[:, im], phi[:, centre], phi[:, ip]
+                    flag |= np.abs(fp - fm) / (fp + 2.0 * f0 + fm) > th
+            assert np.array_equal(flag, f1)
+
+
+def test_features_centre_normalisation():
+    rng = np.random.default_rng(2)
+    smp = random_samples(rng, 10)
+    X = mlp.embedded_features(smp, 2, 1.4).reshape(10, 4, 25, 4)
+    c0 = np.sqrt(1.4 * smp[:, 2, 2] / smp[:, 2, 0])
+    # centre point (index 12): rho~ = 0, p~ = 0, u~ along the axis = +-u0 / c0
+    assert np.allclose(X[:, :, 12, 0], 0.0, atol=1e-15)
+    assert np.allclose(X[:, :, 12, 3], 0.0, atol=1e-15)
+    assert np.allclose(X[:, 1, 12, 1], smp[:, 2, 1] / c0)
+    assert np.allclose(X[:, 0, 12, 1], -smp[:, 2, 1] / c0)
+    assert np.allclose(X[:, 3, 12, 2], smp[:, 2, 1] / c0)
+
+
+def test_adam_training_reduces_loss():
+    rng = np.random.default_rng(3)
+    smp = random_samples(rng, 400)
+    X = mlp.embedded_features(smp, 1, 1.4)
+    y = np.repeat(mlp.plain_flag_1d(smp, 0.05, 0.05), 2).astype(np.float64)
+    params = mlp_init(0, mlp.k_in(1))
+    pw = mlp.bce_pos_weight(y)
+    st = {}
+    l0, _ = mlp.loss_and_grad(params, X, y, pw)
+    for _ in range(200):
+        _, g = mlp.loss_and_grad(params, X, y, pw)
+        mlp.adam(params, g, st, 3e-3)
+    l1, _ = mlp.loss_and_grad(params, X, y, pw)
+    assert l1 < 0.5 * l0
