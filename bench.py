@@ -1,0 +1,307 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the AMR Euler hot path on GB300.
+
+A step is one pass of the whole hot path over the hierarchy: CFL reduction,
+three SSP-RK3 stages (ghost fill, fused WENO5/Rusanov RHS + stage update,
+reflux, restriction) over every patch of every level, then flagging and
+regrid. The default workload is the 3D blast problem (128^3 base cells, 3
+levels, 16^3 patches, FP32 fields; its inputs exceed L2). The metric is
+fine-equivalent cell-updates per second: (base cells x 2^(d (L-1))) x steps /
+seconds.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank advances its own replica (no collective on the
+data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import workload  # noqa: E402
+from synth.workloads import fine_equivalent_cells  # noqa: E402
+
+METRIC = 'fine-equiv cell-updates/s per GB300, batched FP32+learned vs plain FP64, at stated L1(rho)'
+UNIT = 'cell-updates/s'
+PEAKS_FILE = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
+
+
+def load_json(path, default):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return default
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    QUERY = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+             'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+             'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', self.gpu, '--query-gpu=' + self.QUERY,
+                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(',')]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if s[1].replace('.', '').isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace('.', '').isdigit()]
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower() == 'active'})
+        sm_sorted = sorted(sm)
+        return {'sm_mhz': sm_sorted[len(sm_sorted) // 2] if sm else None,
+                'sm_max_mhz': max(mx) if mx else None, 'reasons': reasons, 'samples': len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(steps, base=32):
+    """The FP64 CPU oracle, as it stands, on the same problem at base^3 cells:
+    returns (fine-equivalent cell-updates/s, seconds, description)."""
+    from oracle.amr import Oracle
+    w = workload('blast3d', base_cells=(base, base, base))
+    o = Oracle(w)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step()
+        o.regrid()
+    dt = time.perf_counter() - t0
+    fe = fine_equivalent_cells(w)
+    desc = ('oracle (numpy FP64, single thread) on the same 3D blast problem at %d^3 base cells, 3 levels, '
+            '16^3 patches: %d step(s) of step + regrid from t = 0' % (base, steps))
+    return fe * steps / dt, dt, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        v, dt, desc = oracle_sample(1)
+        if i >= args.warmup:
+            per_step.append(dt)
+    w = workload('blast3d', base_cells=(32, 32, 32))
+    fe = fine_equivalent_cells(w)
+    total = sum(per_step)
+    val = fe * len(per_step) / total
+    line = {'impl': 'reference', 'metric': METRIC, 'value': val, 'unit': UNIT, 'n_gpus': world,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1000.0 * total / len(per_step),
+            'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+            'data': 'synthetic', 'config': {'workload': 'blast3d 32^3 base (bounded sample of 128^3), 3 levels, '
+                                            '16^3 patches, FP64 CPU oracle'},
+            'cpu_baseline': {'value': val, 'unit': UNIT, 'cores': 1, 'kind': 'oracle', 'sample': desc},
+            'e2e': {'value': val, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU
+def rhs_flops_per_launch(amr, w, flops):
+    """Algorithmic FLOPs of one fused RHS launch: faces x FLOP/face + cells x FLOP/cell."""
+    d = w['dim']
+    N = w['patch']
+    _, _, ppl = amr.diag()
+    n_patch = int(sum(ppl))
+    faces = n_patch * d * (N + 1) * N ** (d - 1)
+    cells = n_patch * N ** d
+    f = flops[str(d)]
+    return faces * f['face'] + cells * f['cell']
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--workload', default='blast3d')
+    ap.add_argument('--base', type=int, default=0, help='override base cells per dimension')
+    ap.add_argument('--precision', type=int, default=32)
+    ap.add_argument('--flagger', default='plain', choices=['plain', 'mlp'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-e2e', action='store_true')
+    args = ap.parse_args()
+
+    rank = int(os.environ.get('RANK', '0'))
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    if args.impl == 'reference':
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl')
+    __graft_entry__.build()
+    from paper_2508_05020_gb300.amr import AMR
+
+    w = workload(args.workload)
+    if args.base:
+        w['base_cells'] = tuple(args.base if d < w['dim'] else 1 for d in range(3))
+    amr = AMR(w, precision=args.precision, flagger=args.flagger)
+    stream = amr._keep[1]
+    amr.set_timing(True)
+
+    def one_step():
+        amr.step(sync=False)
+        amr.regrid()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    _, _, k0 = amr.counters()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    rhs_ms = []
+    kinds = np.zeros(8)
+    flops_rhs = []
+    flops = load_json(FLOPS_FILE, None)
+    for _ in range(args.steps):
+        amr.step(sync=False)
+        ms, n = amr.timing()
+        rhs_ms.append(ms[1] / max(n[1], 1))
+        kinds += ms
+        if flops:
+            flops_rhs.append(rhs_flops_per_launch(amr, w, flops))
+        amr.regrid()
+        ms2, _ = amr.timing()
+        kinds[5:] += ms2[5:]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    _, _, k1 = amr.counters()
+    if dist:
+        t = torch.tensor([elapsed], device='cuda')
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    fe = fine_equivalent_cells(w)
+    value = fe * args.steps * world / elapsed
+    t_now, cons, ppl = amr.diag()
+
+    peaks = load_json(PEAKS_FILE, {})
+    sm_max = float(peaks.get('sm_max_mhz', 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 FLOP
+    roof = None
+    if flops:
+        avg_ms = float(np.mean(rhs_ms))
+        achieved = float(np.mean(flops_rhs)) / (avg_ms / 1000.0) / 1e12
+        roof = {'bound': 'alu', 'kernel': 'k_rhs (fused WENO5 + Rusanov + SSP-RK3 stage)',
+                'achieved': achieved, 'peak': fp32_peak, 'unit': 'TFLOP/s', 'frac': achieved / fp32_peak,
+                'traffic': None, 'avg_launch_ms': avg_ms,
+                'peak_basis': 'FP32 ALU: 152 SMs x 128 lanes x 2 FLOP x %.0f MHz' % sm_max}
+
+    line = {'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
+            'warmup': args.warmup, 'ms_per_step': 1000.0 * elapsed / args.steps, 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32' if args.precision == 32 else 'f64',
+            'data': 'synthetic',
+            'config': {'workload': '%s base %s, %d levels, %d^%d patches, FP%d, %s flags' % (
+                args.workload, 'x'.join(str(b) for b in w['base_cells'][:w['dim']]), w['levels'], w['patch'],
+                w['dim'], args.precision, args.flagger),
+                'fine_equivalent_cells': fe, 'patches_per_level': [int(x) for x in ppl],
+                'l2': 'inputs larger than L2 (state arrays of several GB)',
+                'parallelism': 'replicas (dp%d, no data-path collective)' % world},
+            'clocks': clk, 'gpu_launches': int(k1 - k0), 'roofline': roof,
+            'phase_ms_per_step': dict(zip(['ghost', 'rhs', 'reflux', 'restrict', 'cfl', 'flag', 'closure',
+                                           'upload_fill'], [float(x) / args.steps for x in kinds])),
+            'wall_s': wall}
+
+    if rank == 0 and not args.no_e2e:
+        line['e2e'] = e2e_measure(AMR, w, args, fe)
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, desc = oracle_sample(1)
+        line['cpu_baseline'] = {'value': v, 'unit': UNIT, 'cores': 1, 'kind': 'oracle', 'sample': desc}
+    amr.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_measure(AMR, w, args, fe):
+    """The same metric through the public API with host buffers: the initial
+    hierarchy is uploaded from host memory (amr_set_state), every step calls
+    amr_step + amr_regrid + amr_get_diag (time and conservation sums read
+    back), and the final state is read back to host memory (amr_get_level)."""
+    import numpy as np
+    amr = AMR(w, precision=args.precision, flagger=args.flagger)
+    lv, co, da = [], [], []
+    for l in range(w['levels']):
+        c, x = amr.get_level(l)
+        lv.append(np.full(len(c), l, dtype=np.int32))
+        co.append(c)
+        da.append(x)
+    lv = np.concatenate(lv)
+    co = np.concatenate(co)
+    da = np.concatenate(da)
+    for _ in range(args.warmup):
+        amr.step(sync=False)
+        amr.regrid()
+        amr.diag()
+    h0, d0, _ = amr.counters()
+    t0 = time.perf_counter()
+    amr.set_state(lv, co, da, t=0.0)
+    for _ in range(args.steps):
+        amr.step(sync=False)
+        amr.regrid()
+        amr.diag()
+    for l in range(w['levels']):
+        amr.get_level(l)
+    el = time.perf_counter() - t0
+    h1, d1, _ = amr.counters()
+    amr.close()
+    return {'value': fe * args.steps / el, 'unit': UNIT,
+            'h2d_bytes_per_step': int((h1 - h0) / args.steps), 'd2h_bytes_per_step': int((d1 - d0) / args.steps),
+            'note': 'initial state uploaded and final state read back inside the timed region (amortised over '
+                    'the steps); per step amr_step + amr_regrid + amr_get_diag'}
+
+
+if __name__ == '__main__':
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * amr.h -- C ABI of the GB300 patch-based AMR Euler library (libamr).
+ *
+ * The library advances the compressible Euler equations of a calorically
+ * perfect gas (Sec. 3.1, Eqs. 1-7) on a patch hierarchy (Sec. 4.2): every
+ * patch has the same N^d cells plus 3 ghost layers per side, level-0 patches
+ * form a Cartesian layout and each is the root of a binary tree / quadtree /
+ * octree with refinement ratio 2 (Sec. 4.3). One call to amr_step advances
+ * every patch of every level by one SSP-RK3 step (Sec. 3.2) with the
+ * characteristic WENO5-JS interpolation and the Rusanov flux (Eqs. 10-12);
+ * amr_regrid applies the refinement requests under rules R1/R2 with
+ * Algorithm 1 and the coarsening rule of Sec. 4.3.
+ *
+ * Conventions for every entry point:
+ *   - return value: AMR_OK (0) or a negative AMR_ERR_* code; no exception or
+ *     longjmp crosses the ABI. On error amr_last_error(ctx) holds a message.
+ *   - a call that fails leaves the hierarchy and the state as they were,
+ *     except AMR_ERR_CUDA and AMR_ERR_NONFINITE, after which only
+ *     amr_get_*, amr_last_error and amr_destroy may be called.
+ *   - lists are in canonical order: level, then lexicographic (z, y, x)
+ *     patch coordinates. Slot (pool) indices are never exposed.
+ *   - host buffers are owned by the caller; a NULL output pointer with a
+ *     non-NULL count pointer asks for the size only (two-call protocol).
+ *   - device memory comes from the caller's allocator hook (opt->dev_alloc)
+ *     or cudaMalloc when the hook is NULL; work is issued on opt->stream.
+ *   - the library is not thread-safe per context.
+ */
+#ifndef AMR_H
+#define AMR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define AMR_OK             0
+#define AMR_ERR_ARG       -1   /* invalid argument */
+#define AMR_ERR_POOL      -2   /* patch pool capacity exceeded (regrid left unchanged) */
+#define AMR_ERR_CUDA      -3   /* a CUDA call failed */
+#define AMR_ERR_NONFINITE -4   /* non-positive density or pressure, or a non-finite wave speed */
+#define AMR_ERR_TIMEOUT   -5   /* a bounded device wait gave up */
+#define AMR_ERR_STATE     -6   /* call not allowed in the current state */
+#define AMR_ERR_MESH      -7   /* a patch set that breaks R1/R2 or the tree structure */
+
+/* boundary kinds, per dimension and side */
+#define AMR_BC_OUTFLOW     0   /* ghost = nearest interior layer */
+#define AMR_BC_REFLECT     1   /* mirror ghost k <-> interior -1-k, normal momentum negated */
+#define AMR_BC_PERIODIC    2   /* both sides of a dimension must be periodic */
+#define AMR_BC_DMR_INFLOW  3   /* double Mach reflection: post-shock state */
+#define AMR_BC_DMR_BOTTOM  4   /* post-shock for x < 1/6, reflecting wall beyond */
+#define AMR_BC_DMR_TOP     5   /* post-/pre-shock by the exact shock x_s(t) = 1/6 + (1+20t)/sqrt(3) */
+
+/* initial conditions (point-sampled at cell centres) */
+#define AMR_IC_SOD          0  /* x < 0.5: (1, 0, 1), else (0.125, 0, 0.1) */
+#define AMR_IC_SHU_OSHER    1  /* x < -4: (3.857143, 2.629369, 10.33333), else (1 + 0.2 sin 5x, 0, 1) */
+#define AMR_IC_RIEMANN2D    2  /* four quadrants split at x = y = 0.5 */
+#define AMR_IC_DMR          3  /* Mach-10 shock x = 1/6 + y/sqrt(3) into (1.4, 0, 0, 1) */
+#define AMR_IC_BLAST3D      4  /* p = 100 inside r < 0.1 of the box centre, 0.1 outside; seeded rho perturbation */
+#define AMR_IC_IMPLOSION    5  /* Sec. 6, Eq. 13: |x| + |y| < 0.15: (0.125, 0.140), else (1, 1) */
+#define AMR_IC_DENSITY_WAVE 6  /* rho = 1 + 0.2 sin(2 pi x), u_x = 1, p = 1 */
+#define AMR_IC_CONSTANT     7  /* rho = 1, u = (0.3, -0.2, 0.1), p = 1 */
+
+/* refinement indicators */
+#define AMR_FLAG_PLAIN 0       /* relative-jump sensor on rho and p over the patch band [-2, N+1]^d */
+#define AMR_FLAG_MLP   1       /* learned indicator (BF16 tensor cores) over the band [-1, N]^d */
+
+/* execution modes */
+#define AMR_MODE_BATCHED   0   /* one persistent launch per kernel over all patches, CUDA graph */
+#define AMR_MODE_PER_PATCH 1   /* one launch per patch per operation (task-per-patch baseline) */
+
+typedef struct amr_ctx amr_ctx;
+
+/* Computational domain: dim in {1,2,3}; [lo, hi] per dimension (unused
+ * dimensions ignored); boundary kind per dimension and side (AMR_BC_*). */
+typedef struct {
+    int dim;
+    double lo[3], hi[3];
+    int bc_lo[3], bc_hi[3];
+} amr_domain_t;
+
+/* Options. Zero-initialise and set what you need; amr_default_options fills
+ * the defaults (FP64, CFL 0.5, plain flags, thresholds 0.05, batched). */
+typedef struct {
+    int precision;        /* 64 (FP64 storage and arithmetic) or 32 (FP32 storage and
+                             stencil arithmetic; FP64 restriction sums, CFL and flag tests) */
+    double cfl;           /* CFL number of the step (Sec. 3.1: c sets the step size) */
+    double t_end;         /* > 0: the step is clipped so t never exceeds t_end */
+    int flagger;          /* AMR_FLAG_PLAIN or AMR_FLAG_MLP */
+    double theta_rho;     /* sensor thresholds: a cell is flagged if the relative jump */
+    double theta_p;       /*   |phi+ - phi-| / (phi+ + 2 phi0 + phi-) exceeds theta */
+    int max_patches;      /* pool capacity; <= 0 means every level fully refined */
+    uint64_t seed;        /* seed of the blast density perturbation */
+    double amp;           /* amplitude of that perturbation (0.01 for the blast problem) */
+    int mode;             /* AMR_MODE_BATCHED or AMR_MODE_PER_PATCH */
+    int use_graph;        /* 1: capture the step of the batched mode in a CUDA graph */
+    void* (*dev_alloc)(size_t bytes, void* user);   /* device allocator hook, or NULL */
+    void (*dev_free)(void* ptr, void* user);
+    void* user;
+    void* stream;         /* cudaStream_t the library issues its work on (NULL: legacy stream) */
+} amr_options_t;
+
+void amr_default_options(amr_options_t* opt);
+
+/* Create a hierarchy (Sec. 4.2-4.3): level 0 is the Cartesian layout of
+ * base_cells[d] / patch_size patches, filled with the initial condition
+ * ic_id; then levels-1 rounds of flag -> regrid with the initial condition
+ * re-sampled on new patches. ratio must be 2 (child[4] in Sec. 4.2);
+ * base_cells[d] must be multiples of patch_size, patch_size in {8, 16, 32}
+ * (3D: {8, 16}); levels in [1, 8]. gamma > 1. *out receives the context. */
+int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int base_cells[3],
+             int levels, int ratio, int patch_size, int ic_id, const amr_options_t* opt);
+
+/* One SSP-RK3 step (Sec. 3.2) of every patch of every level. dt <= 0 takes
+ * dt = CFL / max over leaf cells of sum_d (|u_d| + c) / dx_d (clipped to
+ * t_end); dt > 0 is used as given. dt_used (may be NULL) receives the step;
+ * passing NULL avoids a device-to-host synchronisation. */
+int amr_step(amr_ctx* ctx, double dt, double* dt_used);
+
+/* Flag (plain sensor or learned indicator), close the requests under R2
+ * (Algorithm 1), coarsen by the Sec. 4.3 rule, and fill new patches by
+ * limited-linear prolongation from their parents. */
+int amr_regrid(amr_ctx* ctx);
+
+/* Patches of one level: *n_patches receives their number; coords (may be
+ * NULL) receives n x dim integer patch coordinates; data (may be NULL)
+ * receives n x (dim+2) x N^d interior values as double, variables
+ * (rho, rho u_0.., rho e), cells in (z, y, x) order. */
+int amr_get_level(amr_ctx* ctx, int level, int* n_patches, int* coords, double* data);
+
+/* Diagnostics: time, sum over leaf cells of U times the cell volume (FP64,
+ * dim+2 entries), patches per level (8 entries, unused ones 0). Any pointer
+ * may be NULL. */
+int amr_get_diag(amr_ctx* ctx, double* t, double cons_sums[5], int patches_per_level[8]);
+
+/* Replace the hierarchy and state: n patches given by level (n ints), coords
+ * (n x dim ints) and interiors (n x (dim+2) x N^d doubles, layout of
+ * amr_get_level), and the time t. The set must contain every level-0 patch,
+ * complete sibling groups, and satisfy R2; otherwise AMR_ERR_MESH. */
+int amr_set_state(amr_ctx* ctx, int n, const int* levels, const int* coords,
+                  const double* data, double t);
+
+/* Refinement requests and coarsening candidates of the current state without
+ * changing it: keys are (level, cx, cy, cz) quadruples in canonical order.
+ * Two-call protocol on each list (NULL list: size only). */
+int amr_get_requests(amr_ctx* ctx, int* n_refine, int* refine_keys,
+                     int* n_coarsen, int* coarsen_keys);
+
+/* Weights of the learned indicator of dimension dim (flat float32, order
+ * W1 (64 x K), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), K = 5^d (d+2)). */
+int amr_set_mlp(amr_ctx* ctx, const float* weights, long n_weights);
+
+/* Cell-level agreement of the learned indicator with the plain sensor on the
+ * band [-1, N]^d of every leaf patch (in-domain cells): counts[0..3] =
+ * true positives, false positives, false negatives, true negatives. */
+int amr_flag_stats(amr_ctx* ctx, long long counts[4]);
+
+/* Training samples of a 1D context: for every in-domain band cell [-1, N]
+ * of every leaf patch, the 5-point stencil of (rho, u, p) (n x 5 x 3
+ * doubles) and the plain flag of its centre (n bytes). Two-call protocol. */
+int amr_harvest(amr_ctx* ctx, long* n, double* samples, uint8_t* labels);
+
+/* Per-class device timing of the batched step, for profiling: enable (1) or
+ * disable (0) CUDA events around each kernel class (the step is re-captured).
+ * amr_get_timing synchronises and returns the last step's milliseconds:
+ * ms[0] ghost fill, [1] fused RHS + stage, [2] reflux, [3] restriction,
+ * [4] CFL reduction (0 if the step had a given dt), and of the last regrid
+ * [5] flagging + request read-back (wall), [6] host closure (wall),
+ * [7] table upload + new-patch fill (wall); launches (may be NULL) receives
+ * the kernel launches behind each of [0..4]. */
+int amr_set_timing(amr_ctx* ctx, int enable);
+int amr_get_timing(amr_ctx* ctx, double ms[8], int launches[8]);
+
+/* Counters since amr_init: host-to-device and device-to-host bytes copied,
+ * kernels launched (graph launches count their kernels). */
+int amr_get_counters(amr_ctx* ctx, long long* h2d_bytes, long long* d2h_bytes, long long* kernels);
+
+void amr_destroy(amr_ctx* ctx);
+const char* amr_last_error(const amr_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Learned indicator network (K -> 64 -> 64 -> 1, ReLU), standalone calls.
+ * Inputs are host buffers; the device work uses opt->dev_alloc / opt->stream
+ * (opt may be NULL: cudaMalloc, legacy stream).
+ * ------------------------------------------------------------------------- */
+
+/* Input width K = 5^dim (dim + 2). */
+int amr_mlp_k(int dim);
+
+/* Features of 1D 5-point samples (n x 5 x 3 of rho, u, p) embedded in dim
+ * dimensions along every axis and sign (2 dim rows per sample, axis-major,
+ * sign -1 then +1), normalised by the centre cell. Output n*2*dim x K floats. */
+int amr_mlp_features(int dim, double gamma, const double* samples, long n, float* X,
+                     const amr_options_t* opt);
+
+/* Logits of n feature rows (n x K floats) with BF16 tensor-core GEMMs and
+ * FP32 accumulation. */
+int amr_mlp_infer(int dim, const float* X, long n, const float* weights, float* logits,
+                  const amr_options_t* opt);
+
+/* Weighted binary cross entropy mean(pw y softplus(-z) + (1-y) softplus(z))
+ * of n rows and its gradient w.r.t. the weights (FP32). */
+int amr_mlp_grad(int dim, const float* X, const float* y, long n, float pos_weight,
+                 const float* weights, float* grad, float* loss, const amr_options_t* opt);
+
+/* Adam training on the device: epochs over the n rows in minibatches of
+ * `batch` (order shuffled by shuffle_seed each epoch), learning rate lr.
+ * weights is read as the initial point and overwritten with the result;
+ * loss_hist (may be NULL) receives the mean loss of each epoch. */
+int amr_mlp_train(int dim, const float* X, const float* y, long n, float pos_weight,
+                  int epochs, int batch, float lr, uint64_t shuffle_seed,
+                  float* weights, float* loss_hist, const amr_options_t* opt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMR_H */

@@ -1,0 +1,1069 @@
+// C ABI of libamr (include/amr.h): context, patch pool, metadata tables,
+// step sequence (batched persistent kernels in a CUDA graph, or one launch per
+// patch per operation) and regrid.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "amr.h"
+#include "amr_internal.h"
+#include "amr_mesh.h"
+
+using namespace amr;
+
+struct amr_ctx {
+    // configuration
+    int dim = 1, N = 16, L = 1, nv = 3, precision = 64, ic = 0, mode = 0, use_graph = 1, flagger = 0;
+    double gamma = 1.4;
+    amr_options_t opt{};
+    int base_cells[3] = {1, 1, 1};
+    int cap = 0;
+    int nsm = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // hierarchy
+    Mesh mesh;
+    std::unordered_map<uint64_t, int> slot_of;
+    std::vector<uint64_t> key_of;        // slot -> packed key (valid if used)
+    std::vector<char> used;
+    std::set<int> free_slots;
+    std::vector<Key> canon;              // canonical patch list
+    std::vector<int> canon_slot;
+    int level_off_h[MAXL + 1] = {0};
+    int n_leaf = 0, n_reflux = 0;
+    std::vector<int> leaf_slots, reflux_slots;
+    // device memory
+    std::vector<void*> allocs;
+    void* U[3] = {nullptr, nullptr, nullptr};   // U0, Ua, Ub
+    void* faces = nullptr;
+    int* meta_d = nullptr;                     // all int tables, one block
+    int* meta_h = nullptr;                     // pinned mirror
+    size_t meta_ints = 0;
+    int* anyflag = nullptr;
+    int* req_d = nullptr;                      // [2 + 2 cap]: counts, refine, coarsen
+    int* req_h = nullptr;
+    double* cons_partial = nullptr;
+    double* cons_d = nullptr;
+    double* dense_d = nullptr;                 // staging for get_level / set_state
+    size_t dense_cap = 0;
+    int* slots_d = nullptr;
+    DevTime* time_d = nullptr;
+    DevTime* time_h = nullptr;
+    float* mlp_w = nullptr;
+    long mlp_n = 0;
+    int* ghost_tab = nullptr;
+    int n_ghost = 0;
+    Grid grid{};
+    // graph
+    cudaGraphExec_t graph_cfl = nullptr, graph_fixed = nullptr;
+    long long graph_kernels_cfl = 0, graph_kernels_fixed = 0;
+    // per-class CUDA-event timing of the last step (ghost, rhs, reflux, restrict, cfl)
+    bool timing = false;
+    cudaEvent_t ev[3][5] = {};
+    cudaEvent_t ev_cfl[2] = {};
+    double regrid_ms[3] = {0, 0, 0};      // flag (device), host closure, upload + new-patch fill
+    bool cfl_timed = false;
+    // counters
+    long long h2d = 0, d2h = 0, kernels = 0;
+    bool broken = false;
+    std::string err;
+};
+
+namespace {
+
+int fail(amr_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(amr_ctx* c, cudaError_t e, const char* where) {
+    if (c) c->broken = true;
+    return fail(c, AMR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+void* dalloc(amr_ctx* c, size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    void* p = nullptr;
+    if (c->opt.dev_alloc) {
+        p = c->opt.dev_alloc(bytes, c->opt.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) c->allocs.push_back(p);
+    return p;
+}
+
+void dfree_all(amr_ctx* c) {
+    for (void* p : c->allocs) {
+        if (c->opt.dev_free) c->opt.dev_free(p, c->opt.user);
+        else if (!c->opt.dev_alloc) cudaFree(p);
+    }
+    c->allocs.clear();
+}
+
+// DMR states from the Rankine-Hugoniot relations (Mach 10 into (1.4, 0, 0, 1)),
+// post-shock velocity along (cos 30, -sin 30)
+void dmr_states(double gamma, double* pre, double* post) {
+    const double M = 10.0, r1 = 1.4, p1 = 1.0;
+    const double c1 = std::sqrt(gamma * p1 / r1);
+    const double W = M * c1;
+    const double r2 = r1 * (gamma + 1.0) * M * M / ((gamma - 1.0) * M * M + 2.0);
+    const double p2 = p1 * (2.0 * gamma * M * M - (gamma - 1.0)) / (gamma + 1.0);
+    const double un = W * (1.0 - r1 / r2);
+    const double s3 = std::sqrt(3.0);
+    pre[0] = r1; pre[1] = 0.0; pre[2] = 0.0; pre[3] = p1;
+    post[0] = r2; post[1] = un * (s3 * 0.5); post[2] = -(un * 0.5); post[3] = p2;
+}
+
+// offsets of the int tables inside meta_d / meta_h
+struct MetaLayout {
+    size_t level, coord, nbr, parent, child, pflag, all_list, level_off, leaf_list, counts, reflux_list, reflux_fine,
+        new_list, total;
+    explicit MetaLayout(size_t cap) {
+        size_t o = 0;
+        level = o; o += cap;
+        coord = o; o += 3 * cap;
+        nbr = o; o += (size_t)NBR * cap;
+        parent = o; o += cap;
+        child = o; o += 8 * cap;
+        pflag = o; o += cap;
+        all_list = o; o += cap;
+        level_off = o; o += MAXL + 1;
+        leaf_list = o; o += cap;
+        counts = o; o += 4;
+        reflux_list = o; o += cap;
+        reflux_fine = o; o += 24 * cap;
+        new_list = o; o += cap;
+        total = o;
+    }
+};
+
+int slot_lookup(const amr_ctx* c, const Key& k) {
+    auto it = c->slot_of.find(pack(k));
+    return it == c->slot_of.end() ? -1 : it->second;
+}
+
+// Rebuild every metadata table and work list from the host mesh and upload them.
+int rebuild_tables(amr_ctx* c, const std::vector<Key>& created) {
+    const MetaLayout ml(c->cap);
+    int* h = c->meta_h;
+    const Mesh& m = c->mesh;
+    c->canon = m.canonical();
+    c->canon_slot.resize(c->canon.size());
+    std::fill(h + ml.nbr, h + ml.nbr + (size_t)NBR * c->cap, -2);
+    std::fill(h + ml.child, h + ml.child + 8 * (size_t)c->cap, -1);
+    std::fill(h + ml.reflux_fine, h + ml.reflux_fine + 24 * (size_t)c->cap, -1);
+    for (int l = 0; l <= MAXL; ++l) c->level_off_h[l] = 0;
+    c->leaf_slots.clear();
+    c->reflux_slots.clear();
+    int n_ref = 0;
+    for (size_t i = 0; i < c->canon.size(); ++i) {
+        const Key& k = c->canon[i];
+        const int s = slot_lookup(c, k);
+        c->canon_slot[i] = s;
+        h[ml.all_list + i] = s;
+        h[ml.level + s] = k.l;
+        h[ml.coord + 3 * s + 0] = k.x;
+        h[ml.coord + 3 * s + 1] = k.y;
+        h[ml.coord + 3 * s + 2] = k.z;
+        h[ml.parent + s] = k.l > 0 ? slot_lookup(c, Mesh::parent(k)) : -1;
+        const bool has_ch = m.has_children(k);
+        int pf = has_ch ? 1 : 0;
+        if (has_ch) {
+            const auto ch = m.children(k);
+            for (size_t j = 0; j < ch.size(); ++j) h[ml.child + 8 * s + j] = slot_lookup(c, ch[j]);
+        }
+        const int rz = c->dim == 3 ? 1 : 0, ry = c->dim >= 2 ? 1 : 0;
+        for (int oz = -rz; oz <= rz; ++oz)
+            for (int oy = -ry; oy <= ry; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    Key q{k.l, k.x + ox, k.y + oy, k.z + oz};
+                    int v;
+                    if (!m.wrap(q)) v = -2;
+                    else v = slot_lookup(c, q);
+                    h[ml.nbr + (size_t)NBR * s + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = v;
+                }
+        // coarse-fine faces: a leaf whose neighbour has children keeps its face
+        // flux and takes the fine mean; a fine patch without a same-level
+        // neighbour keeps its face flux for the coarse side
+        bool any_ref = false;
+        int fine[6][4];
+        for (int d = 0; d < c->dim; ++d)
+            for (int side = 0; side < 2; ++side) {
+                for (int j = 0; j < 4; ++j) fine[2 * d + side][j] = -1;
+                Key q = k;
+                int* qc[3] = {&q.x, &q.y, &q.z};
+                *qc[d] += side ? 1 : -1;
+                if (!m.wrap(q)) continue;
+                const bool q_exists = m.exists(q);
+                if (!has_ch && q_exists && m.has_children(q)) {
+                    pf |= 1 << (8 + 2 * d + side);
+                    any_ref = true;
+                    // children of q adjacent to the face, transverse sub-positions (hi, lo)
+                    std::vector<int> tdims;
+                    for (int e = c->dim - 1; e >= 0; --e)
+                        if (e != d) tdims.push_back(e);
+                    const int nsub = 1 << (int)tdims.size();
+                    for (int sidx = 0; sidx < nsub; ++sidx) {
+                        Key f{q.l + 1, 2 * q.x, 2 * q.y, 2 * q.z};
+                        int* fc[3] = {&f.x, &f.y, &f.z};
+                        if (c->dim < 2) f.y = 0;
+                        if (c->dim < 3) f.z = 0;
+                        *fc[d] = 2 * (*qc[d]) + (side ? 0 : 1);
+                        for (size_t t = 0; t < tdims.size(); ++t) {
+                            const int bit = (sidx >> (tdims.size() - 1 - t)) & 1;   // first tdim = hi
+                            *fc[tdims[t]] += bit;
+                        }
+                        fine[2 * d + side][sidx] = slot_lookup(c, f);
+                    }
+                }
+                if (k.l > 0 && !q_exists) pf |= 1 << (8 + 2 * d + side);
+            }
+        h[ml.pflag + s] = pf;
+        c->level_off_h[k.l + 1] = (int)i + 1;
+        if (!has_ch) c->leaf_slots.push_back(s);
+        if (any_ref) {
+            h[ml.reflux_list + n_ref] = s;
+            for (int f = 0; f < 6; ++f)
+                for (int j = 0; j < 4; ++j) h[ml.reflux_fine + ((size_t)n_ref * 6 + f) * 4 + j] = fine[f][j];
+            c->reflux_slots.push_back(s);
+            ++n_ref;
+        }
+    }
+    for (int l = 1; l <= c->L; ++l)
+        if (c->level_off_h[l] < c->level_off_h[l - 1]) c->level_off_h[l] = c->level_off_h[l - 1];
+    for (int l = 0; l <= MAXL; ++l) h[ml.level_off + l] = c->level_off_h[std::min(l, c->L)];
+    for (size_t i = 0; i < c->leaf_slots.size(); ++i) h[ml.leaf_list + i] = c->leaf_slots[i];
+    std::vector<Key> cr = created;
+    std::sort(cr.begin(), cr.end(), canon_less);
+    for (size_t i = 0; i < cr.size(); ++i) h[ml.new_list + i] = slot_lookup(c, cr[i]);
+    c->n_leaf = (int)c->leaf_slots.size();
+    c->n_reflux = n_ref;
+    h[ml.counts + 0] = (int)c->canon.size();
+    h[ml.counts + 1] = c->n_leaf;
+    h[ml.counts + 2] = n_ref;
+    h[ml.counts + 3] = (int)cr.size();
+    const size_t bytes = ml.total * sizeof(int);
+    CK(cudaMemcpyAsync(c->meta_d, c->meta_h, bytes, cudaMemcpyHostToDevice, c->stream), "upload tables");
+    c->h2d += (long long)bytes;
+    // the pinned mirror is rewritten by the next rebuild: wait for the copy
+    CK(cudaStreamSynchronize(c->stream), "upload tables");
+    return AMR_OK;
+}
+
+// give slots to new keys (lowest free first, canonical order), free deleted ones
+void assign_slots(amr_ctx* c, const std::vector<Key>& created, const std::vector<Key>& deleted) {
+    for (const auto& k : deleted) {
+        auto it = c->slot_of.find(pack(k));
+        if (it == c->slot_of.end()) continue;
+        c->used[it->second] = 0;
+        c->free_slots.insert(it->second);
+        c->slot_of.erase(it);
+    }
+    std::vector<Key> cr = created;
+    std::sort(cr.begin(), cr.end(), canon_less);
+    for (const auto& k : cr) {
+        const int s = *c->free_slots.begin();
+        c->free_slots.erase(c->free_slots.begin());
+        c->slot_of[pack(k)] = s;
+        c->key_of[s] = pack(k);
+        c->used[s] = 1;
+    }
+}
+
+int grid_size(const amr_ctx* c, int per_sm) { return c->nsm * per_sm; }
+
+template <typename T>
+T* St(amr_ctx* c, int i) { return reinterpret_cast<T*>(c->U[i]); }
+
+template <typename T>
+int fill_all_levels(amr_ctx* c, T* U, double tfrac) {
+    for (int l = 0; l < c->L; ++l) {
+        CK(Kernels<T>::ghost_fill(c->grid, U, l, tfrac, grid_size(c, 8), c->stream, -1), "ghost fill");
+        ++c->kernels;
+    }
+    return AMR_OK;
+}
+
+// Enqueue one SSP-RK3 step of the batched mode (optionally with the CFL step).
+template <typename T>
+int enqueue_step(amr_ctx* c, bool with_cfl, long long* nk) {
+    const Grid& g = c->grid;
+    long long k = 0;
+    auto mark = [&](cudaEvent_t e) { return c->timing ? cudaEventRecord(e, c->stream) : cudaSuccess; };
+    if (with_cfl) {
+        CK(mark(c->ev_cfl[0]), "event");
+        CK(Kernels<T>::cfl(g, St<T>(c, 0), grid_size(c, 8), c->stream, -1), "cfl");
+        CK(launch_finalize_dt(g, c->stream), "finalize dt");
+        CK(mark(c->ev_cfl[1]), "event");
+        k += 2;
+    }
+    const double tfrac[3] = {0.0, 1.0, 0.5};
+    for (int s = 0; s < 3; ++s) {
+        T* src = St<T>(c, s == 0 ? 0 : s);
+        T* dst = St<T>(c, s == 0 ? 1 : (s == 1 ? 2 : 0));
+        CK(mark(c->ev[s][0]), "event");
+        for (int l = 0; l < c->L; ++l) {
+            CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], grid_size(c, 8), c->stream, -1), "ghost fill");
+            ++k;
+        }
+        CK(mark(c->ev[s][1]), "event");
+        CK(Kernels<T>::rhs_stage(g, src, St<T>(c, 0), dst, reinterpret_cast<T*>(c->faces), s, grid_size(c, 2),
+                                 c->stream, -1),
+           "rhs stage");
+        CK(mark(c->ev[s][2]), "event");
+        CK(Kernels<T>::reflux(g, dst, reinterpret_cast<T*>(c->faces), s, grid_size(c, 4), c->stream, -1), "reflux");
+        CK(mark(c->ev[s][3]), "event");
+        k += 2;
+        for (int l = c->L - 1; l >= 1; --l) {
+            CK(Kernels<T>::restrict_level(g, dst, l, grid_size(c, 8), c->stream, -1), "restrict");
+            ++k;
+        }
+        CK(mark(c->ev[s][4]), "event");
+    }
+    CK(launch_advance_time(g.time, c->stream), "advance time");
+    ++k;
+    if (nk) *nk = k;
+    return AMR_OK;
+}
+
+// One launch per patch per operation (the task-per-patch baseline).
+template <typename T>
+int per_patch_step(amr_ctx* c, bool with_cfl) {
+    const Grid& g = c->grid;
+    if (with_cfl) {
+        for (int s : c->leaf_slots) {
+            CK(Kernels<T>::cfl(g, St<T>(c, 0), 4, c->stream, s), "cfl");
+            ++c->kernels;
+        }
+        CK(launch_finalize_dt(g, c->stream), "finalize dt");
+        ++c->kernels;
+    }
+    const double tfrac[3] = {0.0, 1.0, 0.5};
+    for (int s = 0; s < 3; ++s) {
+        T* src = St<T>(c, s == 0 ? 0 : s);
+        T* dst = St<T>(c, s == 0 ? 1 : (s == 1 ? 2 : 0));
+        for (int l = 0; l < c->L; ++l)
+            for (int i = c->level_off_h[l]; i < c->level_off_h[l + 1]; ++i) {
+                CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], 8, c->stream, c->canon_slot[i]), "ghost fill");
+                ++c->kernels;
+            }
+        for (size_t i = 0; i < c->canon_slot.size(); ++i) {
+            CK(Kernels<T>::rhs_stage(g, src, St<T>(c, 0), dst, reinterpret_cast<T*>(c->faces), s, 8, c->stream,
+                                     c->canon_slot[i]),
+               "rhs stage");
+            ++c->kernels;
+        }
+        for (int e = 0; e < c->n_reflux; ++e) {
+            CK(Kernels<T>::reflux(g, dst, reinterpret_cast<T*>(c->faces), s, 1, c->stream, e), "reflux");
+            ++c->kernels;
+        }
+        for (int l = c->L - 1; l >= 1; --l)
+            for (int i = c->level_off_h[l]; i < c->level_off_h[l + 1]; ++i) {
+                CK(Kernels<T>::restrict_level(g, dst, l, 4, c->stream, c->canon_slot[i]), "restrict");
+                ++c->kernels;
+            }
+    }
+    CK(launch_advance_time(g.time, c->stream), "advance time");
+    ++c->kernels;
+    return AMR_OK;
+}
+
+int read_time(amr_ctx* c) {
+    CK(cudaMemcpyAsync(c->time_h, c->time_d, sizeof(DevTime), cudaMemcpyDeviceToHost, c->stream), "read time");
+    CK(cudaStreamSynchronize(c->stream), "read time");
+    c->d2h += sizeof(DevTime);
+    if (c->time_h->err & ERR_NONFINITE) {
+        c->broken = true;
+        return fail(c, AMR_ERR_NONFINITE, "non-positive density or pressure, or non-finite wave speed");
+    }
+    if (c->time_h->err & ERR_MESH) {
+        c->broken = true;
+        return fail(c, AMR_ERR_MESH, "prolongation source missing (R2 violated)");
+    }
+    return AMR_OK;
+}
+
+template <typename T>
+int step_impl(amr_ctx* c, double dt, double* dt_used) {
+    const bool with_cfl = !(dt > 0.0);
+    if (!with_cfl) {
+        CK(launch_set_dt(c->time_d, dt, c->stream), "set dt");
+        ++c->kernels;
+        c->h2d += sizeof(double);
+    }
+    c->cfl_timed = with_cfl;
+    if (c->mode == AMR_MODE_PER_PATCH) {
+        int r = per_patch_step<T>(c, with_cfl);
+        if (r) return r;
+    } else if (c->use_graph) {
+        cudaGraphExec_t& ex = with_cfl ? c->graph_cfl : c->graph_fixed;
+        long long& nk = with_cfl ? c->graph_kernels_cfl : c->graph_kernels_fixed;
+        if (!ex) {
+            cudaGraph_t gr;
+            CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            int r = enqueue_step<T>(c, with_cfl, &nk);
+            cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
+            if (r) return r;
+            if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+            e = cudaGraphInstantiate(&ex, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return cuda_fail(c, e, "instantiate graph");
+        }
+        CK(cudaGraphLaunch(ex, c->stream), "graph launch");
+        c->kernels += nk;
+    } else {
+        long long nk = 0;
+        int r = enqueue_step<T>(c, with_cfl, &nk);
+        if (r) return r;
+        c->kernels += nk;
+    }
+    if (dt_used) {
+        int r = read_time(c);
+        if (r) return r;
+        *dt_used = c->time_h->dt;
+    }
+    return AMR_OK;
+}
+
+// flags of the current state (ghosts filled first) -> compacted request lists on the host
+template <typename T>
+int compute_requests(amr_ctx* c, std::vector<Key>& refine, std::vector<Key>& coarsen) {
+    int r = fill_all_levels<T>(c, St<T>(c, 0), 0.0);
+    if (r) return r;
+    if (c->flagger == AMR_FLAG_MLP) {
+        if (!c->mlp_w) return fail(c, AMR_ERR_STATE, "learned indicator selected but no weights set");
+        CK(Kernels<T>::flag_mlp(c->grid, St<T>(c, 0), c->mlp_w, c->anyflag, grid_size(c, 2), c->stream),
+           "flag (learned)");
+    } else {
+        CK(Kernels<T>::flag_plain(c->grid, St<T>(c, 0), c->anyflag, grid_size(c, 4), c->stream), "flag");
+    }
+    CK(launch_requests(c->grid, c->anyflag, c->req_d + 2, c->req_d + 2 + c->cap, c->req_d, c->stream), "requests");
+    c->kernels += 2;
+    CK(cudaMemcpyAsync(c->req_h, c->req_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read requests");
+    CK(cudaStreamSynchronize(c->stream), "read requests");
+    const int nr = c->req_h[0], nc = c->req_h[1];
+    if (nr > 0)
+        CK(cudaMemcpyAsync(c->req_h + 2, c->req_d + 2, nr * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "read requests");
+    if (nc > 0)
+        CK(cudaMemcpyAsync(c->req_h + 2 + c->cap, c->req_d + 2 + c->cap, nc * sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream),
+           "read requests");
+    c->d2h += (long long)(2 + nr + nc) * sizeof(int);
+    r = read_time(c);
+    if (r) return r;
+    refine.clear();
+    coarsen.clear();
+    for (int i = 0; i < nr; ++i) refine.push_back(unpack(c->key_of[c->req_h[2 + i]]));
+    for (int i = 0; i < nc; ++i) coarsen.push_back(unpack(c->key_of[c->req_h[2 + c->cap + i]]));
+    return AMR_OK;
+}
+
+template <typename T>
+int regrid_impl(amr_ctx* c, bool resample_ic) {
+    std::vector<Key> req, cand;
+    const auto t0 = std::chrono::steady_clock::now();
+    int r = compute_requests<T>(c, req, cand);
+    if (r) return r;
+    const auto t1 = std::chrono::steady_clock::now();
+    c->regrid_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    c->regrid_ms[1] = c->regrid_ms[2] = 0.0;
+    Mesh m2 = c->mesh;
+    std::vector<Key> created = m2.refine(req);
+    std::unordered_set<uint64_t> just;
+    for (const auto& k : created) just.insert(pack(k));
+    std::vector<Key> deleted = m2.coarsen(cand, just);
+    if (created.empty() && deleted.empty()) return AMR_OK;
+    if ((long long)m2.patches.size() > c->cap)
+        return fail(c, AMR_ERR_POOL, "patch pool capacity exceeded; hierarchy left unchanged");
+    c->mesh.patches.swap(m2.patches);
+    assign_slots(c, created, deleted);
+    const auto t2 = std::chrono::steady_clock::now();
+    r = rebuild_tables(c, created);
+    if (r) return r;
+    const MetaLayout ml(c->cap);
+    const int* new_list = c->meta_d + ml.new_list;
+    if (resample_ic) CK(Kernels<T>::init_ic(c->grid, St<T>(c, 0), new_list, (int)created.size(), c->stream), "ic");
+    else CK(Kernels<T>::prolong_new(c->grid, St<T>(c, 0), new_list, (int)created.size(), c->stream), "prolong");
+    ++c->kernels;
+    if (c->timing) CK(cudaStreamSynchronize(c->stream), "regrid");
+    const auto t3 = std::chrono::steady_clock::now();
+    c->regrid_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    c->regrid_ms[2] = std::chrono::duration<double, std::milli>(t3 - t2).count();
+    return AMR_OK;
+}
+
+template <typename T>
+int get_level_impl(amr_ctx* c, int level, int* n_out, int* coords, double* data) {
+    std::vector<int> slots;
+    std::vector<Key> keys;
+    for (size_t i = 0; i < c->canon.size(); ++i)
+        if (c->canon[i].l == level) {
+            keys.push_back(c->canon[i]);
+            slots.push_back(c->canon_slot[i]);
+        }
+    *n_out = (int)keys.size();
+    if (coords)
+        for (size_t i = 0; i < keys.size(); ++i) {
+            const int cc[3] = {keys[i].x, keys[i].y, keys[i].z};
+            for (int d = 0; d < c->dim; ++d) coords[i * c->dim + d] = cc[d];
+        }
+    if (data && !slots.empty()) {
+        long long ncell = 1;
+        for (int d = 0; d < c->dim; ++d) ncell *= c->N;
+        const size_t per = (size_t)c->nv * ncell;
+        const size_t chunk = std::max<size_t>(1, c->dense_cap / per);
+        for (size_t b = 0; b < slots.size(); b += chunk) {
+            const int n = (int)std::min(chunk, slots.size() - b);
+            CK(cudaMemcpyAsync(c->slots_d, slots.data() + b, n * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+               "get level");
+            CK(Kernels<T>::unpack_interiors(c->grid, St<T>(c, 0), c->slots_d, n, c->dense_d, c->stream), "unpack");
+            CK(cudaMemcpyAsync(data + b * per, c->dense_d, n * per * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream),
+               "get level");
+            CK(cudaStreamSynchronize(c->stream), "get level");
+            c->h2d += n * sizeof(int);
+            c->d2h += (long long)(n * per * sizeof(double));
+            ++c->kernels;
+        }
+    }
+    return AMR_OK;
+}
+
+template <typename T>
+int set_state_impl(amr_ctx* c, int n, const int* levels, const int* coords, const double* data, double t) {
+    Mesh m2(c->dim, c->mesh.base, c->mesh.periodic, c->L - 1);
+    m2.patches.clear();
+    std::vector<Key> keys;
+    for (int i = 0; i < n; ++i) {
+        Key k{levels[i], coords[i * c->dim], c->dim >= 2 ? coords[i * c->dim + 1] : 0,
+              c->dim == 3 ? coords[i * c->dim + 2] : 0};
+        if (k.l < 0 || k.l >= c->L) return fail(c, AMR_ERR_MESH, "level out of range");
+        if (!m2.patches.insert(pack(k)).second) return fail(c, AMR_ERR_MESH, "duplicate patch");
+        keys.push_back(k);
+    }
+    const std::string why = m2.check();
+    if (!why.empty()) return fail(c, AMR_ERR_MESH, why);
+    if ((int)keys.size() > c->cap) return fail(c, AMR_ERR_POOL, "patch pool capacity exceeded");
+    c->mesh.patches.swap(m2.patches);
+    c->slot_of.clear();
+    c->free_slots.clear();
+    for (int s = 0; s < c->cap; ++s) {
+        c->free_slots.insert(s);
+        c->used[s] = 0;
+    }
+    std::vector<Key> all = c->mesh.canonical();
+    assign_slots(c, all, {});
+    int r = rebuild_tables(c, {});
+    if (r) return r;
+    long long ncell = 1;
+    for (int d = 0; d < c->dim; ++d) ncell *= c->N;
+    const size_t per = (size_t)c->nv * ncell;
+    const size_t chunk = std::max<size_t>(1, c->dense_cap / per);
+    std::vector<int> slots(n);
+    for (int i = 0; i < n; ++i) slots[i] = slot_lookup(c, keys[i]);
+    for (int b = 0; b < n; b += (int)chunk) {
+        const int m = (int)std::min<size_t>(chunk, n - b);
+        CK(cudaMemcpyAsync(c->slots_d, slots.data() + b, m * sizeof(int), cudaMemcpyHostToDevice, c->stream), "set");
+        CK(cudaMemcpyAsync(c->dense_d, data + (size_t)b * per, m * per * sizeof(double), cudaMemcpyHostToDevice,
+                           c->stream),
+           "set");
+        CK(Kernels<T>::pack_interiors(c->grid, St<T>(c, 0), c->slots_d, m, c->dense_d, c->stream), "pack");
+        CK(cudaStreamSynchronize(c->stream), "set");
+        c->h2d += (long long)(m * sizeof(int) + m * per * sizeof(double));
+        ++c->kernels;
+    }
+    c->time_h->t = t;
+    c->time_h->dt = 0.0;
+    c->time_h->lam = 0ull;
+    c->time_h->err = 0;
+    CK(cudaMemcpyAsync(c->time_d, c->time_h, sizeof(DevTime), cudaMemcpyHostToDevice, c->stream), "set time");
+    CK(cudaStreamSynchronize(c->stream), "set time");
+    return AMR_OK;
+}
+
+template <typename T>
+int cons_impl(amr_ctx* c, double* out) {
+    CK(Kernels<T>::cons_sums(c->grid, St<T>(c, 0), c->cons_partial, c->cons_d, c->stream), "cons sums");
+    c->kernels += 2;
+    CK(cudaMemcpyAsync(out, c->cons_d, c->nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cons sums");
+    CK(cudaStreamSynchronize(c->stream), "cons sums");
+    c->d2h += c->nv * sizeof(double);
+    return AMR_OK;
+}
+
+bool valid_bc(int b) { return b >= AMR_BC_OUTFLOW && b <= AMR_BC_DMR_TOP; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void amr_default_options(amr_options_t* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = 64;
+    opt->cfl = 0.5;
+    opt->t_end = 0.0;
+    opt->flagger = AMR_FLAG_PLAIN;
+    opt->theta_rho = 0.05;
+    opt->theta_p = 0.05;
+    opt->max_patches = 0;
+    opt->seed = 0;
+    opt->amp = 0.01;
+    opt->mode = AMR_MODE_BATCHED;
+    opt->use_graph = 1;
+}
+
+int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int base_cells[3], int levels, int ratio,
+             int patch_size, int ic_id, const amr_options_t* opt) {
+    if (!out || !dom || !base_cells) return AMR_ERR_ARG;
+    *out = nullptr;
+    amr_ctx* c = new (std::nothrow) amr_ctx();
+    if (!c) return AMR_ERR_ARG;
+    if (opt) c->opt = *opt;
+    else amr_default_options(&c->opt);
+    auto bad = [&](const char* m) {
+        c->err = m;
+        *out = c;   // the caller can read the message, then destroy
+        return AMR_ERR_ARG;
+    };
+    const int dim = dom->dim;
+    if (dim < 1 || dim > 3) return bad("dim must be 1, 2 or 3");
+    if (ratio != 2) return bad("ratio must be 2");
+    if (!(patch_size == 8 || patch_size == 16 || (patch_size == 32 && dim < 3)))
+        return bad("patch size must be 8, 16 or 32 (3D: 8 or 16)");
+    if (levels < 1 || levels > MAXL) return bad("levels must be in [1, 8]");
+    if (!(gamma > 1.0)) return bad("gamma must exceed 1");
+    if (c->opt.precision != 32 && c->opt.precision != 64) return bad("precision must be 32 or 64");
+    if (ic_id < AMR_IC_SOD || ic_id > AMR_IC_CONSTANT) return bad("unknown initial condition");
+    if (!(c->opt.cfl > 0.0)) return bad("cfl must be positive");
+    if (c->opt.flagger != AMR_FLAG_PLAIN && c->opt.flagger != AMR_FLAG_MLP) return bad("unknown flagger");
+    if (c->opt.mode != AMR_MODE_BATCHED && c->opt.mode != AMR_MODE_PER_PATCH) return bad("unknown mode");
+    int bp[3] = {1, 1, 1};
+    bool periodic[3] = {false, false, false};
+    for (int d = 0; d < dim; ++d) {
+        if (base_cells[d] < patch_size || base_cells[d] % patch_size) return bad("base cells must be multiples of the patch size");
+        if (!(dom->hi[d] > dom->lo[d])) return bad("empty domain");
+        if (!valid_bc(dom->bc_lo[d]) || !valid_bc(dom->bc_hi[d])) return bad("unknown boundary kind");
+        if ((dom->bc_lo[d] == AMR_BC_PERIODIC) != (dom->bc_hi[d] == AMR_BC_PERIODIC))
+            return bad("periodic boundaries must be periodic on both sides");
+        if (dom->bc_lo[d] >= AMR_BC_DMR_INFLOW || dom->bc_hi[d] >= AMR_BC_DMR_INFLOW)
+            if (dim != 2) return bad("double-Mach boundaries are 2D only");
+        bp[d] = base_cells[d] / patch_size;
+        periodic[d] = dom->bc_lo[d] == AMR_BC_PERIODIC;
+    }
+    c->dim = dim;
+    c->N = patch_size;
+    c->L = levels;
+    c->nv = dim + 2;
+    c->gamma = gamma;
+    c->precision = c->opt.precision;
+    c->ic = ic_id;
+    c->mode = c->opt.mode;
+    c->use_graph = c->opt.use_graph;
+    c->flagger = c->opt.flagger;
+    for (int d = 0; d < 3; ++d) c->base_cells[d] = d < dim ? base_cells[d] : 1;
+    c->mesh = Mesh(dim, bp, periodic, levels - 1);
+    long long full = 0;
+    for (int l = 0; l < levels; ++l) {
+        long long n = 1;
+        for (int d = 0; d < dim; ++d) n *= (long long)bp[d] << l;
+        full += n;
+    }
+    c->cap = c->opt.max_patches > 0 ? (int)std::min<long long>(c->opt.max_patches, full) : (int)full;
+    if ((long long)c->mesh.patches.size() > c->cap) return bad("pool smaller than the base level");
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        c->err = "no CUDA device";
+        *out = c;
+        return AMR_ERR_CUDA;
+    }
+    if (c->opt.stream) {
+        c->stream = reinterpret_cast<cudaStream_t>(c->opt.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            c->err = "stream creation failed";
+            *out = c;
+            return AMR_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+
+    // pool
+    const int S = patch_size + 2 * G;
+    Grid& g = c->grid;
+    g.dim = dim;
+    g.N = patch_size;
+    g.L = levels;
+    g.nv = c->nv;
+    g.SX = (S + 7) / 8 * 8;
+    g.SY = dim >= 2 ? S : 1;
+    g.SZ = dim == 3 ? S : 1;
+    g.slot_elems = (long long)g.SX * g.SY * g.SZ;
+    g.patch_elems = g.slot_elems * c->nv;
+    g.cap = c->cap;
+    for (int l = 0; l < MAXL; ++l)
+        for (int d = 0; d < 3; ++d) {
+            g.ext[l][d] = d < dim ? (bp[d] << std::min(l, 20)) : 1;
+            g.dx[l][d] = d < dim ? (dom->hi[d] - dom->lo[d]) / (double)((long long)base_cells[d] << l) : 1.0;
+        }
+    for (int d = 0; d < 3; ++d) {
+        g.lo[d] = d < dim ? dom->lo[d] : 0.0;
+        g.periodic[d] = periodic[d] ? 1 : 0;
+        g.bc[d][0] = d < dim ? dom->bc_lo[d] : AMR_BC_OUTFLOW;
+        g.bc[d][1] = d < dim ? dom->bc_hi[d] : AMR_BC_OUTFLOW;
+        g.base_cells[d] = c->base_cells[d];
+    }
+    g.gamma = gamma;
+    g.cfl = c->opt.cfl;
+    g.t_end = c->opt.t_end;
+    g.theta_rho = c->opt.theta_rho;
+    g.theta_p = c->opt.theta_p;
+    g.ic = ic_id;
+    g.seed = c->opt.seed;
+    g.amp = c->opt.amp;
+    dmr_states(gamma, g.dmr_pre, g.dmr_post);
+
+    const size_t esz = c->precision == 64 ? 8 : 4;
+    const size_t state_bytes = (size_t)c->cap * g.patch_elems * esz;
+    long long trans = 1;
+    for (int d = 1; d < dim; ++d) trans *= patch_size;
+    const size_t face_bytes = (size_t)c->cap * 2 * dim * c->nv * trans * esz;
+    for (int i = 0; i < 3; ++i) c->U[i] = dalloc(c, state_bytes);
+    c->faces = dalloc(c, face_bytes);
+    const MetaLayout ml(c->cap);
+    c->meta_ints = ml.total;
+    c->meta_d = (int*)dalloc(c, ml.total * sizeof(int));
+    c->anyflag = (int*)dalloc(c, c->cap * sizeof(int));
+    c->req_d = (int*)dalloc(c, (2 + 2 * (size_t)c->cap) * sizeof(int));
+    c->cons_partial = (double*)dalloc(c, (size_t)c->cap * c->nv * sizeof(double));
+    c->cons_d = (double*)dalloc(c, 8 * sizeof(double));
+    c->dense_cap = std::max<size_t>((size_t)g.patch_elems * 64, (size_t)1 << 22);
+    c->dense_d = (double*)dalloc(c, c->dense_cap * sizeof(double));
+    c->slots_d = (int*)dalloc(c, c->cap * sizeof(int));
+    c->time_d = (DevTime*)dalloc(c, sizeof(DevTime));
+    for (int i = 0; i < 3; ++i)
+        if (!c->U[i]) return fail(c, AMR_ERR_CUDA, "device allocation failed");
+    if (!c->faces || !c->meta_d || !c->anyflag || !c->req_d || !c->cons_partial || !c->cons_d || !c->dense_d ||
+        !c->slots_d || !c->time_d)
+        return fail(c, AMR_ERR_CUDA, "device allocation failed");
+    if (cudaMallocHost((void**)&c->meta_h, ml.total * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->req_h, (2 + 2 * (size_t)c->cap) * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->time_h, sizeof(DevTime)) != cudaSuccess)
+        return fail(c, AMR_ERR_CUDA, "pinned host allocation failed");
+    for (int i = 0; i < 3; ++i) CK(cudaMemsetAsync(c->U[i], 0, state_bytes, c->stream), "clear pool");
+    CK(cudaMemsetAsync(c->faces, 0, face_bytes, c->stream), "clear faces");
+    CK(cudaMemsetAsync(c->anyflag, 0, c->cap * sizeof(int), c->stream), "clear flags");
+    std::memset(c->time_h, 0, sizeof(DevTime));
+    CK(cudaMemcpyAsync(c->time_d, c->time_h, sizeof(DevTime), cudaMemcpyHostToDevice, c->stream), "time");
+
+    // ghost-cell table of a slot: packed slot coordinates (x | y << 10 | z << 20)
+    std::vector<int> gt;
+    for (int z = 0; z < g.SZ; ++z)
+        for (int y = 0; y < g.SY; ++y)
+            for (int x = 0; x < S; ++x) {
+                const bool gx = x < G || x >= G + patch_size;
+                const bool gy = dim >= 2 && (y < G || y >= G + patch_size);
+                const bool gz = dim == 3 && (z < G || z >= G + patch_size);
+                if (gx || gy || gz) gt.push_back(x | ((dim >= 2 ? y : G) << 10) | ((dim == 3 ? z : G) << 20));
+            }
+    c->n_ghost = (int)gt.size();
+    c->ghost_tab = (int*)dalloc(c, gt.size() * sizeof(int));
+    if (!c->ghost_tab) return fail(c, AMR_ERR_CUDA, "device allocation failed");
+    CK(cudaMemcpyAsync(c->ghost_tab, gt.data(), gt.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "ghosts");
+    CK(cudaStreamSynchronize(c->stream), "init");
+
+    g.level = c->meta_d + ml.level;
+    g.coord = c->meta_d + ml.coord;
+    g.nbr = c->meta_d + ml.nbr;
+    g.parent = c->meta_d + ml.parent;
+    g.child = c->meta_d + ml.child;
+    g.pflag = c->meta_d + ml.pflag;
+    g.all_list = c->meta_d + ml.all_list;
+    g.level_off = c->meta_d + ml.level_off;
+    g.leaf_list = c->meta_d + ml.leaf_list;
+    g.counts = c->meta_d + ml.counts;
+    g.reflux_list = c->meta_d + ml.reflux_list;
+    g.reflux_fine = c->meta_d + ml.reflux_fine;
+    g.new_list = c->meta_d + ml.new_list;
+    g.ghost_tab = c->ghost_tab;
+    g.n_ghost = c->n_ghost;
+    g.time = c->time_d;
+    {
+        cudaError_t e = c->precision == 64 ? Kernels<double>::prepare(g) : Kernels<float>::prepare(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
+    }
+
+    // level 0 and the initial condition, then the initial hierarchy
+    c->used.assign(c->cap, 0);
+    c->key_of.assign(c->cap, 0);
+    for (int s = 0; s < c->cap; ++s) c->free_slots.insert(s);
+    std::vector<Key> base = c->mesh.canonical();
+    assign_slots(c, base, {});
+    int r = rebuild_tables(c, base);
+    if (r) return r;
+    const int* new_list = c->meta_d + ml.new_list;
+    if (c->precision == 64) {
+        CK(Kernels<double>::init_ic(g, St<double>(c, 0), new_list, (int)base.size(), c->stream), "ic");
+        for (int i = 1; i < levels; ++i)
+            if ((r = regrid_impl<double>(c, true))) return r;
+    } else {
+        CK(Kernels<float>::init_ic(g, St<float>(c, 0), new_list, (int)base.size(), c->stream), "ic");
+        for (int i = 1; i < levels; ++i)
+            if ((r = regrid_impl<float>(c, true))) return r;
+    }
+    ++c->kernels;
+    CK(cudaStreamSynchronize(c->stream), "init");
+    return AMR_OK;
+}
+
+#define GUARD(c)                                                        \
+    do {                                                                \
+        if (!(c)) return AMR_ERR_ARG;                                   \
+        if ((c)->broken) return fail((c), AMR_ERR_STATE, "context unusable after an earlier device error"); \
+        if (!(c)->U[0]) return fail((c), AMR_ERR_STATE, "context not initialised"); \
+    } while (0)
+
+int amr_step(amr_ctx* c, double dt, double* dt_used) {
+    GUARD(c);
+    if (std::isnan(dt)) return fail(c, AMR_ERR_ARG, "dt is NaN");
+    return c->precision == 64 ? step_impl<double>(c, dt, dt_used) : step_impl<float>(c, dt, dt_used);
+}
+
+int amr_regrid(amr_ctx* c) {
+    GUARD(c);
+    if (c->L == 1) return AMR_OK;
+    return c->precision == 64 ? regrid_impl<double>(c, false) : regrid_impl<float>(c, false);
+}
+
+int amr_get_level(amr_ctx* c, int level, int* n_patches, int* coords, double* data) {
+    if (!c || !n_patches) return AMR_ERR_ARG;
+    if (level < 0 || level >= c->L) return fail(c, AMR_ERR_ARG, "level out of range");
+    if (!c->U[0]) return fail(c, AMR_ERR_STATE, "context not initialised");
+    return c->precision == 64 ? get_level_impl<double>(c, level, n_patches, coords, data)
+                              : get_level_impl<float>(c, level, n_patches, coords, data);
+}
+
+int amr_get_diag(amr_ctx* c, double* t, double cons_sums[5], int patches_per_level[8]) {
+    if (!c) return AMR_ERR_ARG;
+    if (!c->U[0]) return fail(c, AMR_ERR_STATE, "context not initialised");
+    if (patches_per_level) {
+        for (int l = 0; l < 8; ++l) patches_per_level[l] = 0;
+        for (const auto& k : c->canon) patches_per_level[k.l]++;
+    }
+    if (t) {
+        CK(cudaMemcpyAsync(c->time_h, c->time_d, sizeof(DevTime), cudaMemcpyDeviceToHost, c->stream), "diag");
+        CK(cudaStreamSynchronize(c->stream), "diag");
+        c->d2h += sizeof(DevTime);
+        *t = c->time_h->t;
+    }
+    if (cons_sums) {
+        int r = c->precision == 64 ? cons_impl<double>(c, cons_sums) : cons_impl<float>(c, cons_sums);
+        if (r) return r;
+    }
+    return AMR_OK;
+}
+
+int amr_set_state(amr_ctx* c, int n, const int* levels, const int* coords, const double* data, double t) {
+    GUARD(c);
+    if (n <= 0 || !levels || !coords || !data) return fail(c, AMR_ERR_ARG, "empty state");
+    return c->precision == 64 ? set_state_impl<double>(c, n, levels, coords, data, t)
+                              : set_state_impl<float>(c, n, levels, coords, data, t);
+}
+
+int amr_get_requests(amr_ctx* c, int* n_refine, int* refine_keys, int* n_coarsen, int* coarsen_keys) {
+    GUARD(c);
+    if (!n_refine || !n_coarsen) return fail(c, AMR_ERR_ARG, "count pointers required");
+    std::vector<Key> req, cand;
+    int r = c->precision == 64 ? compute_requests<double>(c, req, cand) : compute_requests<float>(c, req, cand);
+    if (r) return r;
+    std::sort(req.begin(), req.end(), canon_less);
+    std::sort(cand.begin(), cand.end(), canon_less);
+    *n_refine = (int)req.size();
+    *n_coarsen = (int)cand.size();
+    if (refine_keys)
+        for (size_t i = 0; i < req.size(); ++i) {
+            refine_keys[4 * i] = req[i].l;
+            refine_keys[4 * i + 1] = req[i].x;
+            refine_keys[4 * i + 2] = req[i].y;
+            refine_keys[4 * i + 3] = req[i].z;
+        }
+    if (coarsen_keys)
+        for (size_t i = 0; i < cand.size(); ++i) {
+            coarsen_keys[4 * i] = cand[i].l;
+            coarsen_keys[4 * i + 1] = cand[i].x;
+            coarsen_keys[4 * i + 2] = cand[i].y;
+            coarsen_keys[4 * i + 3] = cand[i].z;
+        }
+    return AMR_OK;
+}
+
+int amr_set_mlp(amr_ctx* c, const float* w, long n) {
+    GUARD(c);
+    if (!w || n != mlp_n_weights(c->dim)) return fail(c, AMR_ERR_ARG, "weight count does not match the dimension");
+    if (!c->mlp_w) {
+        c->mlp_w = (float*)dalloc(c, n * sizeof(float));
+        if (!c->mlp_w) return fail(c, AMR_ERR_CUDA, "device allocation failed");
+    }
+    c->mlp_n = n;
+    CK(cudaMemcpyAsync(c->mlp_w, w, n * sizeof(float), cudaMemcpyHostToDevice, c->stream), "set mlp");
+    CK(cudaStreamSynchronize(c->stream), "set mlp");
+    c->h2d += n * sizeof(float);
+    return AMR_OK;
+}
+
+int amr_flag_stats(amr_ctx* c, long long counts[4]) {
+    GUARD(c);
+    if (!counts) return AMR_ERR_ARG;
+    if (!c->mlp_w) return fail(c, AMR_ERR_STATE, "no learned indicator weights set");
+    unsigned long long* d = (unsigned long long*)c->dense_d;
+    CK(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), c->stream), "stats");
+    int r;
+    cudaError_t e;
+    if (c->precision == 64) {
+        if ((r = fill_all_levels<double>(c, St<double>(c, 0), 0.0))) return r;
+        e = Kernels<double>::flag_stats(c->grid, St<double>(c, 0), c->mlp_w, d, grid_size(c, 2), c->stream);
+    } else {
+        if ((r = fill_all_levels<float>(c, St<float>(c, 0), 0.0))) return r;
+        e = Kernels<float>::flag_stats(c->grid, St<float>(c, 0), c->mlp_w, d, grid_size(c, 2), c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "flag stats");
+    unsigned long long hc[4];
+    CK(cudaMemcpyAsync(hc, d, sizeof(hc), cudaMemcpyDeviceToHost, c->stream), "stats");
+    CK(cudaStreamSynchronize(c->stream), "stats");
+    for (int i = 0; i < 4; ++i) counts[i] = (long long)hc[i];
+    return AMR_OK;
+}
+
+int amr_harvest(amr_ctx* c, long* n, double* samples, uint8_t* labels) {
+    GUARD(c);
+    if (!n) return AMR_ERR_ARG;
+    if (c->dim != 1) return fail(c, AMR_ERR_ARG, "harvest needs a 1D hierarchy");
+    const long slots = (long)c->n_leaf * (c->N + 2);
+    // samples and labels share the dense staging buffer; valid ones are
+    // compacted on the host side of the two-call protocol
+    std::vector<double> smp((size_t)slots * 15);
+    std::vector<unsigned char> lab((size_t)slots);
+    if ((size_t)slots * 16 > c->dense_cap) return fail(c, AMR_ERR_ARG, "too many samples for the staging buffer");
+    double* dsm = c->dense_d;
+    unsigned char* dlb = reinterpret_cast<unsigned char*>(c->dense_d + (size_t)slots * 15);
+    int r;
+    cudaError_t e;
+    if (c->precision == 64) {
+        if ((r = fill_all_levels<double>(c, St<double>(c, 0), 0.0))) return r;
+        e = Kernels<double>::harvest(c->grid, St<double>(c, 0), nullptr, dsm, dlb, (int)slots, c->stream);
+    } else {
+        if ((r = fill_all_levels<float>(c, St<float>(c, 0), 0.0))) return r;
+        e = Kernels<float>::harvest(c->grid, St<float>(c, 0), nullptr, dsm, dlb, (int)slots, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "harvest");
+    CK(cudaMemcpyAsync(smp.data(), dsm, smp.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "harvest");
+    CK(cudaMemcpyAsync(lab.data(), dlb, lab.size(), cudaMemcpyDeviceToHost, c->stream), "harvest");
+    CK(cudaStreamSynchronize(c->stream), "harvest");
+    c->d2h += (long long)(smp.size() * sizeof(double) + lab.size());
+    long k = 0;
+    for (long i = 0; i < slots; ++i) {
+        if (lab[i] == 255) continue;
+        if (samples) std::memcpy(samples + 15 * k, smp.data() + 15 * i, 15 * sizeof(double));
+        if (labels) labels[k] = lab[i];
+        ++k;
+    }
+    *n = k;
+    return AMR_OK;
+}
+
+int amr_set_timing(amr_ctx* c, int enable) {
+    GUARD(c);
+    const bool en = enable != 0;
+    if (en == c->timing) return AMR_OK;
+    if (en && !c->ev[0][0]) {
+        for (int s = 0; s < 3; ++s)
+            for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&c->ev[s][i]), "event");
+        CK(cudaEventCreate(&c->ev_cfl[0]), "event");
+        CK(cudaEventCreate(&c->ev_cfl[1]), "event");
+    }
+    c->timing = en;
+    // the captured steps must be re-captured with (or without) the events
+    if (c->graph_cfl) { cudaGraphExecDestroy(c->graph_cfl); c->graph_cfl = nullptr; }
+    if (c->graph_fixed) { cudaGraphExecDestroy(c->graph_fixed); c->graph_fixed = nullptr; }
+    return AMR_OK;
+}
+
+int amr_get_timing(amr_ctx* c, double ms[8], int launches[8]) {
+    GUARD(c);
+    if (!ms) return AMR_ERR_ARG;
+    if (!c->timing) return fail(c, AMR_ERR_STATE, "timing is not enabled");
+    if (c->mode != AMR_MODE_BATCHED) return fail(c, AMR_ERR_STATE, "timing covers the batched mode");
+    CK(cudaStreamSynchronize(c->stream), "timing");
+    for (int i = 0; i < 8; ++i) ms[i] = 0.0;
+    for (int s = 0; s < 3; ++s)
+        for (int i = 0; i < 4; ++i) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, c->ev[s][i], c->ev[s][i + 1]), "timing");
+            ms[i] += t;
+        }
+    if (c->cfl_timed) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->ev_cfl[0], c->ev_cfl[1]), "timing");
+        ms[4] = t;
+    }
+    ms[5] = c->regrid_ms[0];
+    ms[6] = c->regrid_ms[1];
+    ms[7] = c->regrid_ms[2];
+    if (launches) {
+        const int l[8] = {3 * c->L, 3, 3, 3 * (c->L - 1), c->cfl_timed ? 2 : 0, 0, 0, 0};
+        for (int i = 0; i < 8; ++i) launches[i] = l[i];
+    }
+    return AMR_OK;
+}
+
+int amr_get_counters(amr_ctx* c, long long* h2d, long long* d2h, long long* kernels) {
+    if (!c) return AMR_ERR_ARG;
+    if (h2d) *h2d = c->h2d;
+    if (d2h) *d2h = c->d2h;
+    if (kernels) *kernels = c->kernels;
+    return AMR_OK;
+}
+
+void amr_destroy(amr_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_cfl) cudaGraphExecDestroy(c->graph_cfl);
+    if (c->graph_fixed) cudaGraphExecDestroy(c->graph_fixed);
+    if (c->ev[0][0]) {
+        for (int s = 0; s < 3; ++s)
+            for (int i = 0; i < 5; ++i) cudaEventDestroy(c->ev[s][i]);
+        cudaEventDestroy(c->ev_cfl[0]);
+        cudaEventDestroy(c->ev_cfl[1]);
+    }
+    dfree_all(c);
+    if (c->meta_h) cudaFreeHost(c->meta_h);
+    if (c->req_h) cudaFreeHost(c->req_h);
+    if (c->time_h) cudaFreeHost(c->time_h);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* amr_last_error(const amr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,8 @@
+// FP32 kernel set (fields stored and updated in FP32; restriction sums, CFL
+// and sensor tests in FP64).
+#include "amr_launch.cuh"
+#include "amr_mlp_kernels.cuh"
+
+namespace amr {
+template struct Kernels<float>;
+}

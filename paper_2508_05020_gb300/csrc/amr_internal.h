@@ -1,0 +1,124 @@
+// Internal declarations shared by the translation units of libamr.
+//
+// Device layout of the patch pool (the patch region of Sec. 4.2, which spans
+// interior and ghost points): one array per state,
+//     U[slot][var][z][y][x],  z in [0, SZ), y in [0, SY), x in [0, SX),
+// with SZ = N + 6 in 3D (else 1), SY = N + 6 in 2D/3D (else 1), and the x
+// pitch SX = N + 6 rounded up to 8 elements so every row starts on a 16-byte
+// boundary (32-byte for FP64). Local cell index l in [-3, N+3) maps to slot
+// index l + 3. A patch's data is contiguous (nv * SZ * SY * SX elements).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace amr {
+
+constexpr int G = 3;            // ghost layers: the WENO5 pencil reaches i-2 .. i+3
+constexpr int MAXL = 8;         // maximum number of levels
+constexpr int NBR = 27;         // neighbour table entries per slot ({-1,0,1}^3)
+
+// device error bits (DevTime::err)
+constexpr int ERR_NONFINITE = 1;
+constexpr int ERR_MESH = 2;
+
+// Per-step scalars kept on the device so that a captured step needs no host input.
+struct DevTime {
+    double t;                   // time at the start of the step
+    double dt;                  // step in use
+    unsigned long long lam;     // bit pattern of the max wave-speed sum (non-negative double)
+    int err;                    // ERR_* bits
+    int pad;
+};
+
+// Read-only description of the grid and the metadata tables, passed by value.
+struct Grid {
+    int dim, N, L, nv;
+    int SX, SY, SZ;
+    long long slot_elems;       // SZ * SY * SX
+    long long patch_elems;      // nv * slot_elems
+    int cap;                    // pool capacity (slots)
+    int ext[MAXL][3];           // patches per dimension at each level
+    double dx[MAXL][3];         // cell size per level and dimension
+    double lo[3];
+    int periodic[3];
+    int bc[3][2];               // AMR_BC_* per dimension and side
+    double gamma;
+    double cfl, t_end;
+    double theta_rho, theta_p;
+    int ic;
+    unsigned long long seed;
+    double amp;
+    int base_cells[3];
+    double dmr_pre[4], dmr_post[4];   // double-Mach (rho, u, v, p) ahead of / behind the shock
+    // metadata, indexed by slot
+    const int* level;           // [cap]
+    const int* coord;           // [cap * 3]
+    const int* nbr;             // [cap * 27]: slot at offset (ox,oy,oz), index (oz+1)*9+(oy+1)*3+(ox+1);
+                                //   -1 = in-domain position without a patch, -2 = outside the domain
+    const int* parent;          // [cap]
+    const int* child;           // [cap * 8]: children in (z, y, x)-lexicographic order, -1 if none
+    const int* pflag;           // [cap]: bit 0 has children; bits 8.. save-face mask (bit 8 + 2 d + side)
+    // work lists (device), canonical order
+    const int* all_list;        // every active slot; level l occupies [level_off[l], level_off[l+1])
+    const int* level_off;       // [L + 1]
+    const int* leaf_list;       // leaf slots
+    const int* counts;          // [0] n_all, [1] n_leaf, [2] n_reflux, [3] n_new
+    const int* reflux_list;     // leaf slots with at least one coarse-fine face
+    const int* reflux_fine;     // [n_reflux * 6 * 4]: fine slots across each face (-1 if none)
+    const int* new_list;        // slots created by the last regrid
+    const int* ghost_tab;       // packed local (x,y,z)+3 of every ghost cell of a slot
+    int n_ghost;
+    DevTime* time;
+};
+
+// Kernel set of one storage precision. Implemented for float and double in
+// amr_f32.cu / amr_f64.cu; the FP64 unit is compiled without FMA contraction.
+template <typename T>
+struct Kernels {
+    // one-time kernel attributes (dynamic shared memory); call before any capture
+    static cudaError_t prepare(const Grid& g);
+    // ghost cells of every patch of `level` (same-level copy, prolongation,
+    // physical boundaries) at time t + tfrac * dt
+    static cudaError_t ghost_fill(const Grid& g, T* U, int level, double tfrac, int grid,
+                                  cudaStream_t s, int one_slot);
+    // RHS + SSP-RK3 stage of every patch (or one patch if one_slot >= 0)
+    static cudaError_t rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces,
+                                 int stage, int grid, cudaStream_t s, int one_slot);
+    static cudaError_t reflux(const Grid& g, T* Uout, const T* faces, int stage, int grid,
+                              cudaStream_t s, int one_slot);
+    // covered cells of level-1 patches from the children of level `level`
+    static cudaError_t restrict_level(const Grid& g, T* U, int level, int grid, cudaStream_t s,
+                                      int one_slot);
+    static cudaError_t cfl(const Grid& g, const T* U, int grid, cudaStream_t s, int one_slot);
+    static cudaError_t init_ic(const Grid& g, T* U, const int* list, int n, cudaStream_t s);
+    static cudaError_t prolong_new(const Grid& g, T* U, const int* list, int n, cudaStream_t s);
+    static cudaError_t flag_plain(const Grid& g, const T* U, int* anyflag, int grid,
+                                  cudaStream_t s);
+    static cudaError_t cons_sums(const Grid& g, const T* U, double* partial, double* out,
+                                 cudaStream_t s);
+    static cudaError_t unpack_interiors(const Grid& g, const T* U, const int* slots, int n,
+                                        double* out, cudaStream_t s);
+    static cudaError_t pack_interiors(const Grid& g, T* U, const int* slots, int n,
+                                      const double* in, cudaStream_t s);
+    // learned indicator: per-patch any(logit > 0) on the band [-1, N]^d of leaf patches
+    static cudaError_t flag_mlp(const Grid& g, const T* U, const float* w, int* anyflag,
+                                int grid, cudaStream_t s);
+    // per-cell plain and learned flags on the band [-1, N]^d: counts[4]
+    static cudaError_t flag_stats(const Grid& g, const T* U, const float* w,
+                                  unsigned long long* counts, int grid, cudaStream_t s);
+    static cudaError_t harvest(const Grid& g, const T* U, int* n_out, double* samples,
+                               unsigned char* labels, int max_n, cudaStream_t s);
+};
+
+// dt finalisation and request compaction (precision-independent, amr_common.cu)
+cudaError_t launch_finalize_dt(const Grid& g, cudaStream_t s);
+cudaError_t launch_set_dt(DevTime* t, double dt, cudaStream_t s);
+cudaError_t launch_advance_time(DevTime* t, cudaStream_t s);
+cudaError_t launch_requests(const Grid& g, const int* anyflag, int* out_refine, int* out_coarsen,
+                            int* out_counts, cudaStream_t s);
+
+// MLP pieces (amr_mlp.cu)
+int mlp_k(int dim);
+long mlp_n_weights(int dim);
+
+}  // namespace amr

@@ -1,0 +1,1010 @@
+// Device code of libamr, templated on the storage type T (float or double),
+// the dimension D and the patch size N. Included by amr_f32.cu and amr_f64.cu.
+//
+// Every floating-point expression is written in a fixed evaluation order. The
+// FP64 unit is compiled with -fmad=false, so each operation rounds once and the
+// FP64 path reproduces an IEEE evaluation of the same formulas on the host.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "amr_internal.h"
+#include "amr.h"
+
+namespace amr {
+
+// ---------------------------------------------------------------------------
+// arithmetic helpers: FP64 uses IEEE division and square root; FP32 uses the
+// fast approximate forms (the FP32 path is compared by tolerance, not bits)
+// ---------------------------------------------------------------------------
+template <typename T> struct Num;
+template <> struct Num<double> {
+    __device__ __forceinline__ static double div(double a, double b) { return a / b; }
+    __device__ __forceinline__ static double sqr(double a) { return sqrt(a); }
+};
+template <> struct Num<float> {
+    __device__ __forceinline__ static float div(float a, float b) { return __fdividef(a, b); }
+    __device__ __forceinline__ static float sqr(float a) { return sqrtf(a); }
+};
+
+template <int N> struct PatchShape {
+    static constexpr int S = N + 2 * G;                  // cells per slot side
+    static constexpr int SX = (S + 7) / 8 * 8;           // padded x pitch
+};
+
+__device__ __forceinline__ int floordiv(int a, int b) {
+    int q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+__device__ __forceinline__ long long slot_index(const Grid& g, int slot, int v, int sz, int sy, int sx) {
+    return (long long)slot * g.patch_elems + (long long)v * g.slot_elems +
+           ((long long)sz * g.SY + sy) * g.SX + sx;
+}
+
+// slot coordinate of local index l in an active (d < D) or inactive dimension
+template <int D>
+__device__ __forceinline__ int sc(int d, int l) { return d < D ? l + G : 0; }
+
+// ---------------------------------------------------------------------------
+// Euler primitives (Sec. 3.1, Eqs. 4-6, R = 1): u = m / rho,
+// p = (gamma - 1)(E - rho |u|^2 / 2), T = p / rho
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__device__ __forceinline__ void primitives(const T* U, T gm1, T& rho, T* u, T& p, T& Tt) {
+    rho = U[0];
+    T usq = T(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) u[d] = Num<T>::div(U[1 + d], rho);
+    usq = u[0] * u[0];
+#pragma unroll
+    for (int d = 1; d < D; ++d) usq = usq + u[d] * u[d];
+    p = gm1 * (U[D + 1] - T(0.5) * rho * usq);
+    Tt = Num<T>::div(p, rho);
+}
+
+template <int D>
+__device__ __forceinline__ double pressure_d(const double* U, double gm1) {
+    double rho = U[0];
+    double u[3];
+#pragma unroll
+    for (int d = 0; d < D; ++d) u[d] = U[1 + d] / rho;
+    double usq = u[0] * u[0];
+#pragma unroll
+    for (int d = 1; d < D; ++d) usq = usq + u[d] * u[d];
+    return gm1 * (U[D + 1] - 0.5 * rho * usq);
+}
+
+// ---------------------------------------------------------------------------
+// WENO5-JS nodal mid-point interpolation at x_{i+1/2} from nodes i-2..i+2
+// (Sec. 3.2): quadratic candidates, linear weights (1, 10, 5)/16, Jiang-Shu
+// smoothness indicators, alpha_k = d_k / (eps + beta_k)^2, eps = 1e-6
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
+    const T q0 = (T(3) * a - T(10) * b + T(15) * c) * T(0.125);
+    const T q1 = (-b + T(6) * c + T(3) * d) * T(0.125);
+    const T q2 = (T(3) * c + T(6) * d - e) * T(0.125);
+    const T t0 = a - T(2) * b + c;
+    const T s0 = a - T(4) * b + T(3) * c;
+    const T t1 = b - T(2) * c + d;
+    const T s1 = b - d;
+    const T t2 = c - T(2) * d + e;
+    const T s2 = T(3) * c - T(4) * d + e;
+    const T c1312 = T(13.0 / 12.0);
+    const T b0 = c1312 * (t0 * t0) + T(0.25) * (s0 * s0);
+    const T b1 = c1312 * (t1 * t1) + T(0.25) * (s1 * s1);
+    const T b2 = c1312 * (t2 * t2) + T(0.25) * (s2 * s2);
+    const T e0 = T(1.0e-6) + b0;
+    const T e1 = T(1.0e-6) + b1;
+    const T e2 = T(1.0e-6) + b2;
+    const T a0 = Num<T>::div(T(0.0625), e0 * e0);
+    const T a1 = Num<T>::div(T(0.625), e1 * e1);
+    const T a2 = Num<T>::div(T(0.3125), e2 * e2);
+    return Num<T>::div(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+}
+
+// ---------------------------------------------------------------------------
+// Face flux between pencil nodes 2 and 3 (Sec. 3.2, Eqs. 10-12).
+// Pencil node k holds (p, un, ut[NT], T). Frozen state: pbar, Tbar means of
+// nodes 2, 3; rhobar = pbar / Tbar; cbar = sqrt(gamma Tbar); z = rhobar cbar;
+// kappa = (gamma-1) / (gamma rhobar). Characteristic fields of the primitive
+// system in (p, u, T): w1 = p - z un, w2 = T - kappa p, w_t = ut, w5 = p + z un.
+// Left/right WENO5, inverse transform, first-order fallback if p or T is not
+// positive, Rusanov flux with S = max(c + |un|). Output in pencil order
+// (mass, normal momentum, tangential momenta, energy).
+// ---------------------------------------------------------------------------
+template <typename T, int NT>
+__device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], const T (&ut)[NT > 0 ? NT : 1][6],
+                                          const T (&Tt)[6], T gamma, T gm1, T (&F)[NT + 3]) {
+    constexpr int NF = NT + 3;
+    const T pbar = T(0.5) * (p[2] + p[3]);
+    const T Tbar = T(0.5) * (Tt[2] + Tt[3]);
+    const T rbar = Num<T>::div(pbar, Tbar);
+    const T cbar = Num<T>::sqr(gamma * Tbar);
+    const T z = rbar * cbar;
+    const T kap = Num<T>::div(gm1, gamma * rbar);
+    T wl[NF], wr[NF];
+    {
+        T w[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = p[k] - z * un[k];
+        wl[0] = weno5(w[0], w[1], w[2], w[3], w[4]);
+        wr[0] = weno5(w[5], w[4], w[3], w[2], w[1]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = Tt[k] - kap * p[k];
+        wl[1] = weno5(w[0], w[1], w[2], w[3], w[4]);
+        wr[1] = weno5(w[5], w[4], w[3], w[2], w[1]);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            wl[2 + j] = weno5(ut[j][0], ut[j][1], ut[j][2], ut[j][3], ut[j][4]);
+            wr[2 + j] = weno5(ut[j][5], ut[j][4], ut[j][3], ut[j][2], ut[j][1]);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = p[k] + z * un[k];
+        wl[NF - 1] = weno5(w[0], w[1], w[2], w[3], w[4]);
+        wr[NF - 1] = weno5(w[5], w[4], w[3], w[2], w[1]);
+    }
+    const T z2 = T(2) * z;
+    T pL = T(0.5) * (wl[0] + wl[NF - 1]);
+    T unL = Num<T>::div(wl[NF - 1] - wl[0], z2);
+    T TL = wl[1] + kap * pL;
+    T pR = T(0.5) * (wr[0] + wr[NF - 1]);
+    T unR = Num<T>::div(wr[NF - 1] - wr[0], z2);
+    T TR = wr[1] + kap * pR;
+    T utL[NT > 0 ? NT : 1], utR[NT > 0 ? NT : 1];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) { utL[j] = wl[2 + j]; utR[j] = wr[2 + j]; }
+    const bool bad = !(pL > T(0)) || !(TL > T(0)) || !(pR > T(0)) || !(TR > T(0));
+    if (bad) {
+        pL = p[2]; unL = un[2]; TL = Tt[2];
+        pR = p[3]; unR = un[3]; TR = Tt[3];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) { utL[j] = ut[j][2]; utR[j] = ut[j][3]; }
+    }
+    // conserved states and Euler fluxes at both sides
+    T UL[NF], FL[NF], UR[NF], FR[NF];
+    T sL, sR;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const T ps = side ? pR : pL;
+        const T uns = side ? unR : unL;
+        const T Ts = side ? TR : TL;
+        const T rho = Num<T>::div(ps, Ts);
+        const T c = Num<T>::sqr(gamma * Ts);
+        T usq = uns * uns;
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const T v = side ? utR[j] : utL[j];
+            usq = usq + v * v;
+        }
+        const T E = Num<T>::div(ps, gm1) + T(0.5) * rho * usq;
+        const T mn = rho * uns;
+        T* Uo = side ? UR : UL;
+        T* Fo = side ? FR : FL;
+        Uo[0] = rho;
+        Uo[1] = mn;
+        Fo[0] = mn;
+        Fo[1] = mn * uns + ps;
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const T v = side ? utR[j] : utL[j];
+            Uo[2 + j] = rho * v;
+            Fo[2 + j] = mn * v;
+        }
+        Uo[NF - 1] = E;
+        Fo[NF - 1] = (E + ps) * uns;
+        const T s = c + fabs(uns);
+        if (side) sR = s; else sL = s;
+    }
+    const T hS = T(0.5) * fmax(sR, sL);
+#pragma unroll
+    for (int v = 0; v < NF; ++v) F[v] = T(0.5) * (FR[v] + FL[v]) - hS * (UR[v] - UL[v]);
+}
+
+// ---------------------------------------------------------------------------
+// Limited-linear prolongation of the conserved variables at fine local cell l
+// of a patch (slot, level lev, coords c): coarse cell C = G // 2 in the
+// parent's Moore neighbourhood (guaranteed by R2), minmod slopes of the
+// neighbouring differences (tie: first argument U_{C+1} - U_C), child value
+// U_C + sum_d (+-1/4) s_d, dims in order; U_C for every child of C if any
+// child has rho <= 0 or p <= 0.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int N>
+__device__ void prolong_cell(const Grid& g, const T* U, int slot, const int* c, const int* l, T* out) {
+    constexpr int NV = D + 2;
+    const int par = g.parent[slot];
+    int Lc[3] = {0, 0, 0}, s[3] = {0, 0, 0}, oc[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int Gd = c[d] * N + l[d];
+        const int Gc = Gd >> 1;                 // floor (arithmetic shift)
+        s[d] = Gd - 2 * Gc;
+        const int PC = c[d] >> 1;
+        oc[d] = floordiv(Gc, N) - PC;
+        Lc[d] = Gc - (PC + oc[d]) * N;
+    }
+    const int Q = par >= 0 ? g.nbr[par * NBR + (oc[2] + 1) * 9 + (oc[1] + 1) * 3 + (oc[0] + 1)] : -1;
+    if (Q < 0) {
+        atomicOr(&g.time->err, ERR_MESH);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out[v] = T(0);
+        return;
+    }
+    const int bx = sc<D>(0, Lc[0]), by = sc<D>(1, Lc[1]), bz = sc<D>(2, Lc[2]);
+    T UC[NV], slope[D][NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) UC[v] = U[slot_index(g, Q, v, bz, by, bx)];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int ex = d == 0, ey = d == 1, ez = d == 2;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const T up = U[slot_index(g, Q, v, bz + ez, by + ey, bx + ex)];
+            const T um = U[slot_index(g, Q, v, bz - ez, by - ey, bx - ex)];
+            const T a = up - UC[v];
+            const T b = UC[v] - um;
+            const T pick = fabs(a) <= fabs(b) ? a : b;
+            slope[d][v] = (a * b <= T(0)) ? T(0) : pick;
+        }
+    }
+    const T gm1 = T(g.gamma) - T(1);
+    bool ok = true;
+    T chosen[NV];
+#pragma unroll
+    for (int ch = 0; ch < (1 << D); ++ch) {
+        T v[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = UC[k];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const bool up = (ch >> d) & 1;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] = up ? v[k] + T(0.25) * slope[d][k] : v[k] - T(0.25) * slope[d][k];
+        }
+        T rho, u[D], p, Tt;
+        primitives<T, D>(v, gm1, rho, u, p, Tt);
+        ok = ok && (rho > T(0)) && (p > T(0));
+        bool mine = true;
+#pragma unroll
+        for (int d = 0; d < D; ++d) mine = mine && (((ch >> d) & 1) == s[d]);
+        if (mine) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) chosen[k] = v[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = ok ? chosen[k] : UC[k];
+}
+
+// value of an in-domain cell of a patch: interior, same-level neighbour or prolongation
+template <typename T, int D, int N>
+__device__ void in_domain_value(const Grid& g, const T* U, int slot, const int* c, const int* l, T* out) {
+    constexpr int NV = D + 2;
+    int o[3] = {0, 0, 0};
+    bool inside = true;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        o[d] = l[d] < 0 ? -1 : (l[d] >= N ? 1 : 0);
+        inside = inside && o[d] == 0;
+    }
+    if (inside) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            out[v] = U[slot_index(g, slot, v, sc<D>(2, l[2]), sc<D>(1, l[1]), sc<D>(0, l[0]))];
+        return;
+    }
+    const int nb = g.nbr[slot * NBR + (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1)];
+    if (nb >= 0) {
+        const int sx = sc<D>(0, l[0] - o[0] * N), sy = sc<D>(1, l[1] - o[1] * N), sz = sc<D>(2, l[2] - o[2] * N);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out[v] = U[slot_index(g, nb, v, sz, sy, sx)];
+        return;
+    }
+    prolong_cell<T, D, N>(g, U, slot, c, l, out);
+}
+
+// post- or pre-shock conserved state of the double Mach reflection
+template <typename T, int D>
+__device__ __forceinline__ void dmr_state(const Grid& g, bool behind, T* out);
+
+// Ghost value of local cell l of a patch: physical boundary rules applied from
+// the highest out-of-domain dimension down (the outcome of filling the
+// boundary dimension by dimension in the order x, y, z), then the in-domain
+// value of the mapped cell.
+template <typename T, int D, int N>
+__device__ void ghost_value(const Grid& g, const T* U, int slot, int* l, double t, T* out,
+                            const double* pre, const double* post) {
+    constexpr int NV = D + 2;
+    const int lev = g.level[slot];
+    int c[3] = {g.coord[slot * 3 + 0], g.coord[slot * 3 + 1], g.coord[slot * 3 + 2]};
+    int neg = 0;
+    for (int it = 0; it < D; ++it) {
+        int dd = -1, side = 0;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+            if (dd >= 0 || g.periodic[d]) continue;
+            const int Gd = c[d] * N + l[d];
+            const int n = g.ext[lev][d] * N;
+            if (Gd < 0) { dd = d; side = 0; }
+            else if (Gd >= n) { dd = d; side = 1; }
+        }
+        if (dd < 0) break;
+        const int kind = g.bc[dd][side];
+        const int Gd = c[dd] * N + l[dd];
+        const int n = g.ext[lev][dd] * N;
+        bool dirichlet = false, behind = false;
+        if (kind == AMR_BC_DMR_INFLOW) {
+            dirichlet = true;
+            behind = true;
+        } else if (kind == AMR_BC_DMR_BOTTOM || kind == AMR_BC_DMR_TOP) {
+            const double x = g.lo[0] + ((double)(c[0] * N + l[0]) + 0.5) * g.dx[lev][0];
+            if (kind == AMR_BC_DMR_BOTTOM) {
+                behind = x < 1.0 / 6.0;
+                dirichlet = behind;
+            } else {
+                behind = x < 1.0 / 6.0 + (1.0 + 20.0 * t) / sqrt(3.0);
+                dirichlet = true;
+            }
+        }
+        if (dirichlet) {
+            const double* st = behind ? post : pre;     // (rho, u, v, p)
+            const double r = st[0], ux = st[1], uy = st[2], pp = st[3];
+            const double usq = ux * ux + uy * uy;
+            double Uc[4];
+            Uc[0] = r;
+            Uc[1] = r * ux;
+            Uc[2] = r * uy;
+            Uc[3] = pp / (g.gamma - 1.0) + 0.5 * r * usq;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) out[v] = T(v < 4 ? Uc[v] : 0.0);
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+                if ((neg >> d) & 1) out[1 + d] = -out[1 + d];
+            return;
+        }
+        int Gs;
+        if (kind == AMR_BC_OUTFLOW) {
+            Gs = side ? n - 1 : 0;
+        } else {                                   // reflecting wall (also DMR bottom beyond 1/6)
+            Gs = side ? 2 * n - 1 - Gd : -1 - Gd;
+            neg ^= 1 << dd;
+        }
+        l[dd] = Gs - c[dd] * N;
+    }
+    in_domain_value<T, D, N>(g, U, slot, c, l, out);
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+        if ((neg >> d) & 1) out[1 + d] = -out[1 + d];
+}
+
+// ---------------------------------------------------------------------------
+// K1-K3: ghost fill of every patch of one level (one thread per ghost cell)
+// ---------------------------------------------------------------------------
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
+                                               double4 pre, double4 post) {
+    constexpr int NV = D + 2;
+    const int lo = g.level_off[level], hi = g.level_off[level + 1];
+    const int npatch = one_slot >= 0 ? 1 : hi - lo;
+    const long long total = (long long)npatch * g.n_ghost;
+    const double t = g.time->t + tfrac * g.time->dt;
+    const double pr[4] = {pre.x, pre.y, pre.z, pre.w};
+    const double po[4] = {post.x, post.y, post.z, post.w};
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)(it / g.n_ghost);
+        const int gi = (int)(it - (long long)pi * g.n_ghost);
+        const int slot = one_slot >= 0 ? one_slot : g.all_list[lo + pi];
+        const int pk = g.ghost_tab[gi];
+        int l[3] = {(pk & 1023) - G, ((pk >> 10) & 1023) - G, ((pk >> 20) & 1023) - G};
+        const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
+        T val[NV];
+        ghost_value<T, D, N>(g, U, slot, l, t, val, pr, po);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[slot_index(g, slot, v, sz, sy, sx)] = val[v];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: fused right-hand side and SSP-RK3 stage of a chunk of one patch.
+// The chunk (DZ planes in 3D, the whole patch in 1D/2D) plus its ghost halo
+// is staged in shared memory as primitives (p, u_0.., T); face fluxes of one
+// dimension at a time go to a shared buffer; each thread accumulates the
+// divergence of its own cells in registers, then writes
+// U_out = a U0 + b (U_s + dt R)  (a = 0, b = 1 in stage 1).
+// ---------------------------------------------------------------------------
+template <int D, int N, int DZ> struct Chunk {
+    static constexpr int S = N + 2 * G;
+    static constexpr int CX = N, CY = D >= 2 ? N : 1, CZ = D == 3 ? DZ : 1;
+    static constexpr int QX = S, QY = D >= 2 ? S : 1, QZ = D == 3 ? DZ + 2 * G : 1;
+    static constexpr int QN = QX * QY * QZ;
+    static constexpr int CELLS = CX * CY * CZ;
+    static constexpr int NCH = D == 3 ? N / DZ : 1;
+    static constexpr int F0 = (CX + 1) * CY * CZ;
+    static constexpr int F1 = D >= 2 ? CX * (CY + 1) * CZ : 0;
+    static constexpr int F2 = D == 3 ? CX * CY * (CZ + 1) : 0;
+    static constexpr int FMAX = F0 > F1 ? (F0 > F2 ? F0 : F2) : (F1 > F2 ? F1 : F2);
+    static constexpr int TRANS = D == 1 ? 1 : (D == 2 ? N : N * N);   // cells on a patch face
+};
+
+template <typename T, int D, int N, int DZ>
+constexpr size_t rhs_smem_bytes() {
+    using C = Chunk<D, N, DZ>;
+    return sizeof(T) * ((size_t)(D + 2) * C::QN + (size_t)(D + 2) * C::FMAX);
+}
+
+template <typename T, int D, int N, int DZ, int NTH>
+__global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, const T* U0,
+                                             T* Uout, T* __restrict__ faces,
+                                             int stage, int one_slot) {
+    using C = Chunk<D, N, DZ>;
+    constexpr int NV = D + 2;
+    constexpr int NT = D - 1;
+    constexpr int CPT = (C::CELLS + NTH - 1) / NTH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* q = reinterpret_cast<T*>(smem_raw);                 // [NV][QZ][QY][QX]
+    T* Fs = q + NV * C::QN;                               // [NV][FMAX]
+    const T gamma = T(g.gamma);
+    const T gm1 = T(g.gamma) - T(1);
+    const double dtd = g.time->dt;
+    const T dt = T(dtd);
+    const T ra = stage == 0 ? T(0) : (stage == 1 ? T(0.75) : T(1.0 / 3.0));
+    const T rb = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2.0 / 3.0));
+    const int npatch = one_slot >= 0 ? 1 : g.counts[0];
+    const int n_items = npatch * C::NCH;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int pi = item / C::NCH;
+        const int z0 = (item - pi * C::NCH) * DZ;        // first interior plane of the chunk (3D)
+        const int slot = one_slot >= 0 ? one_slot : g.all_list[pi];
+        const int lev = g.level[slot];
+        const int pf = g.pflag[slot];
+        // 1. stage the chunk and its halo as primitives
+        for (int idx = threadIdx.x; idx < C::QN; idx += NTH) {
+            const int qx = idx % C::QX;
+            const int qy = (idx / C::QX) % C::QY;
+            const int qz = idx / (C::QX * C::QY);
+            const int sz = D == 3 ? z0 + qz : 0;
+            T Uc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Uc[v] = Us[slot_index(g, slot, v, sz, qy, qx)];
+            T rho, u[D], p, Tt;
+            primitives<T, D>(Uc, gm1, rho, u, p, Tt);
+            q[idx] = p;
+#pragma unroll
+            for (int d = 0; d < D; ++d) q[(1 + d) * C::QN + idx] = u[d];
+            q[(D + 1) * C::QN + idx] = Tt;
+        }
+        __syncthreads();
+        T R[CPT][NV];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int ex = d == 0, ey = d == 1, ez = d == 2;
+            const int FX = C::CX + ex, FY = C::CY + ey, FZ = C::CZ + ez;
+            const int nf = FX * FY * FZ;
+            const int step = d == 0 ? 1 : (d == 1 ? C::QX : C::QX * C::QY);
+            for (int f = threadIdx.x; f < nf; f += NTH) {
+                const int fi = f % FX;
+                const int fj = (f / FX) % FY;
+                const int fk = f / (FX * FY);
+                // smem index of pencil node 0 (cell index - 3 along d; G = 3)
+                const int bx = (D >= 1 ? fi + G : 0) - (ex ? G : 0);
+                const int by = (D >= 2 ? fj + G : 0) - (ey ? G : 0);
+                const int bz = (D == 3 ? fk + G : 0) - (ez ? G : 0);
+                const int base = (bz * C::QY + by) * C::QX + bx;
+                T pp[6], un[6], ut[NT > 0 ? NT : 1][6], Tt[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const int id = base + k * step;
+                    pp[k] = q[id];
+                    un[k] = q[(1 + d) * C::QN + id];
+                    Tt[k] = q[(D + 1) * C::QN + id];
+                    int j = 0;
+#pragma unroll
+                    for (int e = 0; e < D; ++e) {
+                        if (e == d) continue;
+                        ut[j][k] = q[(1 + e) * C::QN + id];
+                        ++j;
+                    }
+                }
+                T Fp[NT + 3];
+                face_flux<T, NT>(pp, un, ut, Tt, gamma, gm1, Fp);
+                // pencil order -> global variable order
+                T Fg[NV];
+                Fg[0] = Fp[0];
+                Fg[1 + d] = Fp[1];
+                {
+                    int j = 0;
+#pragma unroll
+                    for (int e = 0; e < D; ++e) {
+                        if (e == d) continue;
+                        Fg[1 + e] = Fp[2 + j];
+                        ++j;
+                    }
+                }
+                Fg[NV - 1] = Fp[NT + 2];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Fs[v * C::FMAX + f] = Fg[v];
+                // patch-boundary faces needed by the coarse-fine flux correction
+                const int fd = d == 0 ? fi : (d == 1 ? fj : fk + z0);
+                const int side = fd == 0 ? 0 : (fd == N ? 1 : -1);
+                if (side >= 0 && ((pf >> (8 + 2 * d + side)) & 1)) {
+                    int tidx;
+                    if (D == 1) tidx = 0;
+                    else if (D == 2) tidx = d == 0 ? fj : fi;
+                    else tidx = d == 0 ? (fk + z0) * N + fj : (d == 1 ? (fk + z0) * N + fi : fj * N + fi);
+                    T* dst = faces + ((long long)slot * 2 * D + 2 * d + side) * NV * C::TRANS + tidx;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) dst[v * C::TRANS] = Fg[v];
+                }
+            }
+            __syncthreads();
+            const T dxd = T(g.dx[lev][d]);
+#pragma unroll
+            for (int n = 0; n < CPT; ++n) {
+                const int cidx = threadIdx.x + n * NTH;
+                if (cidx < C::CELLS) {
+                    const int ci = cidx % C::CX;
+                    const int cj = (cidx / C::CX) % C::CY;
+                    const int ck = cidx / (C::CX * C::CY);
+                    const int flo = (ck * FY + cj) * FX + ci;
+                    const int fhi = flo + (d == 0 ? 1 : (d == 1 ? FX : FX * FY));
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const T dv = Num<T>::div(Fs[v * C::FMAX + fhi] - Fs[v * C::FMAX + flo], dxd);
+                        R[n][v] = d == 0 ? -dv : R[n][v] - dv;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // 3. stage update of the chunk's cells
+#pragma unroll
+        for (int n = 0; n < CPT; ++n) {
+            const int cidx = threadIdx.x + n * NTH;
+            if (cidx < C::CELLS) {
+                const int ci = cidx % C::CX;
+                const int cj = (cidx / C::CX) % C::CY;
+                const int ck = cidx / (C::CX * C::CY);
+                const int sx = ci + G, sy = D >= 2 ? cj + G : 0, sz = D == 3 ? z0 + ck + G : 0;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const long long id = slot_index(g, slot, v, sz, sy, sx);
+                    const T us = Us[id];
+                    T o;
+                    if (stage == 0) o = us + dt * R[n][v];
+                    else o = ra * U0[id] + rb * (us + dt * R[n][v]);
+                    Uout[id] = o;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: coarse-fine flux correction. For each leaf patch with a face whose
+// same-level neighbour has children, the coarse face flux F_c is replaced by
+// the mean F_f of the 2^(d-1) fine face fluxes (summed in lexicographic
+// z, y, x order, times 2^-(d-1)), applied to the stage result as
+// U -/+ b dt (F_f - F_c) / dx on the high/low face; faces x-, x+, y-, ... in turn.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(256) k_reflux(Grid g, T* Uout, const T* __restrict__ faces, int stage,
+                                                int one_item) {
+    constexpr int NV = D + 2;
+    constexpr int TRANS = Chunk<D, N, 1>::TRANS;
+    const T rb = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2.0 / 3.0));
+    const T dt = T(g.time->dt);
+    const int n = one_item >= 0 ? one_item + 1 : g.counts[2];
+    for (int e = one_item >= 0 ? one_item : blockIdx.x; e < n; e += gridDim.x) {
+        const int slot = g.reflux_list[e];
+        const int lev = g.level[slot];
+        for (int d = 0; d < D; ++d) {
+            for (int side = 0; side < 2; ++side) {
+                const int* fs = g.reflux_fine + ((long long)e * 6 + 2 * d + side) * 4;
+                if (fs[0] < 0) continue;
+                const T dx = T(g.dx[lev][d]);
+                for (int t = threadIdx.x; t < TRANS; t += blockDim.x) {
+                    const int th = D == 3 ? t / N : 0;       // transverse (hi, lo) in (z, y, x) order
+                    const int tl = D == 1 ? 0 : (D == 3 ? t % N : t);
+                    int cell[3] = {0, 0, 0};
+                    cell[d] = side ? N - 1 : 0;
+                    {
+                        int j = 0;
+                        for (int e2 = D - 1; e2 >= 0; --e2) {   // hi transverse first
+                            if (e2 == d) continue;
+                            cell[e2] = (D == 3 && j == 0) ? th : tl;
+                            ++j;
+                        }
+                    }
+                    const int sx = cell[0] + G, sy = D >= 2 ? cell[1] + G : 0, sz = D == 3 ? cell[2] + G : 0;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        T acc = T(0);
+                        bool first = true;
+                        for (int ah = 0; ah < (D == 3 ? 2 : 1); ++ah) {
+                            for (int al = 0; al < (D >= 2 ? 2 : 1); ++al) {
+                                const int fh = 2 * th + ah, fl = 2 * tl + al;
+                                const int ph = fh / N, pl = fl / N;
+                                const int lh = fh % N, ll = fl % N;
+                                const int fslot = D == 3 ? fs[ph * 2 + pl] : (D == 2 ? fs[pl] : fs[0]);
+                                const int fidx = D == 3 ? lh * N + ll : (D == 2 ? ll : 0);
+                                if (fslot < 0) {             // inconsistent table: report, skip
+                                    atomicOr(&g.time->err, ERR_MESH);
+                                    continue;
+                                }
+                                const T val = faces[((long long)fslot * 2 * D + 2 * d + (1 - side)) * NV * TRANS +
+                                                    v * TRANS + fidx];
+                                acc = first ? val : acc + val;
+                                first = false;
+                            }
+                        }
+                        const T Ff = acc * T(D == 3 ? 0.25 : (D == 2 ? 0.5 : 1.0));
+                        const T Fc = faces[((long long)slot * 2 * D + 2 * d + side) * NV * TRANS + v * TRANS + t];
+                        const T diff = Num<T>::div(Ff - Fc, dx);
+                        const long long id = slot_index(g, slot, v, sz, sy, sx);
+                        const T u = Uout[id];
+                        Uout[id] = side ? u - rb * (dt * diff) : u + rb * (dt * diff);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K6: restriction of level `level` into its parents: the covered coarse cell
+// takes (sum of its 2^d children in lexicographic z, y, x order) * 2^-d,
+// summed in FP64
+// ---------------------------------------------------------------------------
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int one_slot) {
+    constexpr int NV = D + 2;
+    constexpr int H = N / 2;
+    constexpr int HC = D == 1 ? H : (D == 2 ? H * H : H * H * H);
+    const int lo = g.level_off[level], hi = g.level_off[level + 1];
+    const int npatch = one_slot >= 0 ? 1 : hi - lo;
+    const long long total = (long long)npatch * HC;
+    const double scale = D == 1 ? 0.5 : (D == 2 ? 0.25 : 0.125);
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)(it / HC);
+        const int ci = (int)(it - (long long)pi * HC);
+        const int slot = one_slot >= 0 ? one_slot : g.all_list[lo + pi];
+        const int par = g.parent[slot];
+        if (par < 0) {
+            atomicOr(&g.time->err, ERR_MESH);
+            continue;
+        }
+        const int cx = ci % H, cy = D >= 2 ? (ci / H) % H : 0, cz = D == 3 ? ci / (H * H) : 0;
+        const int ox = (g.coord[slot * 3 + 0] & 1) * H, oy = D >= 2 ? (g.coord[slot * 3 + 1] & 1) * H : 0,
+                  oz = D == 3 ? (g.coord[slot * 3 + 2] & 1) * H : 0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double acc = 0.0;
+            bool first = true;
+            for (int az = 0; az < (D == 3 ? 2 : 1); ++az)
+                for (int ay = 0; ay < (D >= 2 ? 2 : 1); ++ay)
+                    for (int ax = 0; ax < 2; ++ax) {
+                        const double val = (double)U[slot_index(g, slot, v, D == 3 ? 2 * cz + az + G : 0,
+                                                                D >= 2 ? 2 * cy + ay + G : 0, 2 * cx + ax + G)];
+                        acc = first ? val : acc + val;
+                        first = false;
+                    }
+            U[slot_index(g, par, v, D == 3 ? oz + cz + G : 0, D >= 2 ? oy + cy + G : 0, ox + cx + G)] =
+                T(acc * scale);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K7: CFL reduction over leaf cells: lambda = sum_d (|u_d| + c) / dx_d in FP64,
+// c = sqrt(gamma p / rho); block max by warp shuffles, grid max by atomicMax
+// on the bit pattern (valid for non-negative doubles)
+// ---------------------------------------------------------------------------
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
+    constexpr int NV = D + 2;
+    constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
+    const int npatch = one_slot >= 0 ? 1 : g.counts[1];
+    const long long total = (long long)npatch * NC;
+    const double gm1 = g.gamma - 1.0;
+    double lmax = 0.0;
+    bool bad = false;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)(it / NC);
+        const int ci = (int)(it - (long long)pi * NC);
+        const int slot = one_slot >= 0 ? one_slot : g.leaf_list[pi];
+        const int lev = g.level[slot];
+        const int x = ci % N, y = D >= 2 ? (ci / N) % N : 0, z = D == 3 ? ci / (N * N) : 0;
+        double Uc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            Uc[v] = (double)U[slot_index(g, slot, v, D == 3 ? z + G : 0, D >= 2 ? y + G : 0, x + G)];
+        const double rho = Uc[0];
+        double u[3];
+#pragma unroll
+        for (int d = 0; d < D; ++d) u[d] = Uc[1 + d] / rho;
+        double usq = u[0] * u[0];
+#pragma unroll
+        for (int d = 1; d < D; ++d) usq = usq + u[d] * u[d];
+        const double p = gm1 * (Uc[D + 1] - 0.5 * rho * usq);
+        if (!(rho > 0.0) || !(p > 0.0)) bad = true;
+        const double c = sqrt(g.gamma * p / rho);
+        double lam = (fabs(u[0]) + c) / g.dx[lev][0];
+#pragma unroll
+        for (int d = 1; d < D; ++d) lam = lam + (fabs(u[d]) + c) / g.dx[lev][d];
+        if (!(lam <= 1.0e300)) bad = true;
+        else lmax = fmax(lmax, lam);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = lmax;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&g.time->err, ERR_NONFINITE);
+    if (wid == 0) {
+        double m = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) atomicMax(&g.time->lam, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K9 (plain): relative-jump sensor on rho and p over the band [-2, N+1]^d of
+// each leaf patch (in-domain cells), evaluated in FP64:
+// s = |phi+ - phi-| / (phi+ + 2 phi0 + phi-) > theta; per-patch OR.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* anyflag) {
+    constexpr int NV = D + 2;
+    constexpr int B = N + 4;
+    constexpr int NB = D == 1 ? B : (D == 2 ? B * B : B * B * B);
+    const int npatch = g.counts[1];
+    const double gm1 = g.gamma - 1.0;
+    for (int pi = blockIdx.x; pi < npatch; pi += gridDim.x) {
+        const int slot = g.leaf_list[pi];
+        const int lev = g.level[slot];
+        const int c[3] = {g.coord[slot * 3], g.coord[slot * 3 + 1], g.coord[slot * 3 + 2]};
+        bool any = false;
+        for (int bi = threadIdx.x; bi < NB; bi += blockDim.x) {
+            int l[3] = {bi % B - 2, D >= 2 ? (bi / B) % B - 2 : 0, D == 3 ? bi / (B * B) - 2 : 0};
+            bool indom = true;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                if (g.periodic[d]) continue;
+                const int Gd = c[d] * N + l[d];
+                indom = indom && Gd >= 0 && Gd < g.ext[lev][d] * N;
+            }
+            if (!indom) continue;
+            bool f = false;
+            double Uc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                Uc[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2]), sc<D>(1, l[1]), sc<D>(0, l[0]))];
+            const double r0 = Uc[0];
+            const double p0 = pressure_d<D>(Uc, gm1);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                double Um[NV], Up[NV];
+                const int ex = d == 0, ey = d == 1, ez = d == 2;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    Um[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2] - ez), sc<D>(1, l[1] - ey),
+                                                 sc<D>(0, l[0] - ex))];
+                    Up[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2] + ez), sc<D>(1, l[1] + ey),
+                                                 sc<D>(0, l[0] + ex))];
+                }
+                const double rm = Um[0], rp = Up[0];
+                const double pm = pressure_d<D>(Um, gm1), pp = pressure_d<D>(Up, gm1);
+                const double sr = fabs(rp - rm) / (rp + 2.0 * r0 + rm);
+                const double sp = fabs(pp - pm) / (pp + 2.0 * p0 + pm);
+                f = f || (sr > g.theta_rho) || (sp > g.theta_p);
+            }
+            any = any || f;
+        }
+        const int res = __syncthreads_or(any);
+        if (threadIdx.x == 0) anyflag[slot] = res ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K13: initial conditions point-sampled at cell centres (FP64, then stored)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double splitmix_unit(unsigned long long seed, unsigned long long n) {
+    // output n+1 of SplitMix64 seeded with `seed` (Steele, Lea, Flood 2014), 53-bit mantissa
+    unsigned long long z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * 0x1.0p-53;
+}
+
+template <int D>
+__device__ void ic_primitive(const Grid& g, const double* X, const int* Gi, int lev, const double* pre,
+                             const double* post, double& rho, double* u, double& p) {
+    const double x = X[0];
+    for (int d = 0; d < 3; ++d) u[d] = 0.0;
+    switch (g.ic) {
+    case AMR_IC_SOD: {
+        const bool left = x < 0.5;
+        rho = left ? 1.0 : 0.125;
+        p = left ? 1.0 : 0.1;
+    } break;
+    case AMR_IC_SHU_OSHER: {
+        const bool left = x < -4.0;
+        rho = left ? 3.857143 : 1.0 + 0.2 * sin(5.0 * x);
+        u[0] = left ? 2.629369 : 0.0;
+        p = left ? 10.33333 : 1.0;
+    } break;
+    case AMR_IC_RIEMANN2D: {
+        const bool east = x > 0.5, north = X[1] > 0.5;
+        if (east && north) { rho = 1.5; u[0] = 0.0; u[1] = 0.0; p = 1.5; }
+        else if (!east && north) { rho = 0.5323; u[0] = 1.206; u[1] = 0.0; p = 0.3; }
+        else if (!east && !north) { rho = 0.138; u[0] = 1.206; u[1] = 1.206; p = 0.029; }
+        else { rho = 0.5323; u[0] = 0.0; u[1] = 1.206; p = 0.3; }
+    } break;
+    case AMR_IC_DMR: {
+        const bool behind = x < 1.0 / 6.0 + X[1] / sqrt(3.0);
+        const double* st = behind ? post : pre;
+        rho = st[0]; u[0] = st[1]; u[1] = st[2]; p = st[3];
+    } break;
+    case AMR_IC_BLAST3D: {
+        const double dxc = X[0] - 0.5, dyc = X[1] - 0.5, dzc = X[2] - 0.5;
+        const double r2 = dxc * dxc + dyc * dyc + dzc * dzc;
+        p = r2 < 0.01 ? 100.0 : 0.1;
+        const long long ib0 = Gi[0] >> lev, ib1 = Gi[1] >> lev, ib2 = Gi[2] >> lev;
+        const long long lin = (ib2 * g.base_cells[1] + ib1) * g.base_cells[0] + ib0;
+        const double xi = splitmix_unit(g.seed, (unsigned long long)lin);
+        rho = 1.0 + g.amp * (2.0 * xi - 1.0);
+    } break;
+    case AMR_IC_IMPLOSION: {
+        const bool inside = fabs(X[0]) + fabs(X[1]) < 0.15;
+        rho = inside ? 0.125 : 1.0;
+        p = inside ? 0.140 : 1.0;
+    } break;
+    case AMR_IC_DENSITY_WAVE: {
+        rho = 1.0 + 0.2 * sin(2.0 * 3.141592653589793 * x);
+        u[0] = 1.0;
+        p = 1.0;
+    } break;
+    default: {   // AMR_IC_CONSTANT
+        rho = 1.0; p = 1.0;
+        u[0] = 0.3; u[1] = -0.2; u[2] = 0.1;
+    } break;
+    }
+}
+
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(256) k_init_ic(Grid g, T* U, const int* list, int n, double4 pre4, double4 post4) {
+    constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
+    const double pre[4] = {pre4.x, pre4.y, pre4.z, pre4.w};
+    const double post[4] = {post4.x, post4.y, post4.z, post4.w};
+    const double gm1 = g.gamma - 1.0;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < (long long)n * NC;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)(it / NC);
+        const int ci = (int)(it - (long long)pi * NC);
+        const int slot = list[pi];
+        const int lev = g.level[slot];
+        const int l[3] = {ci % N, D >= 2 ? (ci / N) % N : 0, D == 3 ? ci / (N * N) : 0};
+        int Gi[3];
+        double X[3];
+        for (int d = 0; d < 3; ++d) {
+            Gi[d] = d < D ? g.coord[slot * 3 + d] * N + l[d] : 0;
+            X[d] = g.lo[d] + ((double)Gi[d] + 0.5) * g.dx[lev][d];
+        }
+        double rho, u[3], p;
+        ic_primitive<D>(g, X, Gi, lev, pre, post, rho, u, p);
+        double usq = u[0] * u[0];
+        for (int d = 1; d < D; ++d) usq = usq + u[d] * u[d];
+        const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
+        U[slot_index(g, slot, 0, sz, sy, sx)] = T(rho);
+        for (int d = 0; d < D; ++d) U[slot_index(g, slot, 1 + d, sz, sy, sx)] = T(rho * u[d]);
+        U[slot_index(g, slot, D + 1, sz, sy, sx)] = T(p / gm1 + 0.5 * rho * usq);
+    }
+}
+
+// K12: interiors of new patches by prolongation from their parents
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(256) k_prolong_new(Grid g, T* U, const int* list, int n) {
+    constexpr int NV = D + 2;
+    constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < (long long)n * NC;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)(it / NC);
+        const int ci = (int)(it - (long long)pi * NC);
+        const int slot = list[pi];
+        int l[3] = {ci % N, D >= 2 ? (ci / N) % N : 0, D == 3 ? ci / (N * N) : 0};
+        const int c[3] = {g.coord[slot * 3], g.coord[slot * 3 + 1], g.coord[slot * 3 + 2]};
+        T val[NV];
+        prolong_cell<T, D, N>(g, U, slot, c, l, val);
+        const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[slot_index(g, slot, v, sz, sy, sx)] = val[v];
+    }
+}
+
+// K8: conservation sums over leaf cells (per-patch partials, then a fixed-order total)
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(256) k_cons_partial(Grid g, const T* U, double* partial) {
+    constexpr int NV = D + 2;
+    constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
+    __shared__ double red[NV][256];
+    const int npatch = g.counts[1];
+    for (int pi = blockIdx.x; pi < npatch; pi += gridDim.x) {
+        const int slot = g.leaf_list[pi];
+        double acc[NV];
+        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+        for (int ci = threadIdx.x; ci < NC; ci += blockDim.x) {
+            const int x = ci % N, y = D >= 2 ? (ci / N) % N : 0, z = D == 3 ? ci / (N * N) : 0;
+            for (int v = 0; v < NV; ++v)
+                acc[v] += (double)U[slot_index(g, slot, v, D == 3 ? z + G : 0, D >= 2 ? y + G : 0, x + G)];
+        }
+        for (int v = 0; v < NV; ++v) red[v][threadIdx.x] = acc[v];
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s)
+                for (int v = 0; v < NV; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x < NV) {
+            const int lev = g.level[slot];
+            double vol = 1.0;
+            for (int d = 0; d < D; ++d) vol *= g.dx[lev][d];
+            partial[(long long)pi * NV + threadIdx.x] = red[threadIdx.x][0] * vol;
+        }
+        __syncthreads();
+    }
+}
+
+template <int NV>
+__global__ void k_cons_total(const int* counts, const double* partial, double* out) {
+    __shared__ double red[NV][256];
+    const int n = counts[1];
+    double acc[NV];
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int v = 0; v < NV; ++v) acc[v] += partial[(long long)i * NV + v];
+    for (int v = 0; v < NV; ++v) red[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int v = 0; v < NV; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < NV) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+// dense interiors <-> pool
+template <typename T, int D, int N>
+__global__ void k_unpack(Grid g, const T* U, const int* slots, int n, double* out) {
+    constexpr int NV = D + 2;
+    constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < (long long)n * NV * NC;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(it % NC);
+        const int v = (int)((it / NC) % NV);
+        const int pi = (int)(it / ((long long)NC * NV));
+        const int x = ci % N, y = D >= 2 ? (ci / N) % N : 0, z = D == 3 ? ci / (N * N) : 0;
+        out[it] = (double)U[slot_index(g, slots[pi], v, D == 3 ? z + G : 0, D >= 2 ? y + G : 0, x + G)];
+    }
+}
+
+template <typename T, int D, int N>
+__global__ void k_pack(Grid g, T* U, const int* slots, int n, const double* in) {
+    constexpr int NV = D + 2;
+    constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < (long long)n * NV * NC;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(it % NC);
+        const int v = (int)((it / NC) % NV);
+        const int pi = (int)(it / ((long long)NC * NV));
+        const int x = ci % N, y = D >= 2 ? (ci / N) % N : 0, z = D == 3 ? ci / (N * N) : 0;
+        U[slot_index(g, slots[pi], v, D == 3 ? z + G : 0, D >= 2 ? y + G : 0, x + G)] = T(in[it]);
+    }
+}
+
+}  // namespace amr

@@ -1,0 +1,139 @@
+// Kernel launchers of one storage precision: dispatch on (dimension, patch
+// size) to the template instances of amr_kernels.cuh. Included once by each
+// precision unit (amr_f32.cu, amr_f64.cu) with AMR_T set to its type.
+#pragma once
+#include "amr_kernels.cuh"
+
+namespace amr {
+
+// chunk depth (3D) and block size of the fused RHS kernel per precision
+template <typename T, int D, int N> struct RhsCfg {
+    static constexpr int DZ = D == 3 ? (sizeof(T) == 8 ? 2 : 4) : 1;
+    static constexpr int NTH = D == 1 ? 64 : 256;
+};
+
+#define AMR_DISPATCH(g, CALL)                                   \
+    switch ((g).dim * 100 + (g).N) {                            \
+    case 108: { constexpr int D = 1, N = 8; CALL; } break;      \
+    case 116: { constexpr int D = 1, N = 16; CALL; } break;     \
+    case 132: { constexpr int D = 1, N = 32; CALL; } break;     \
+    case 208: { constexpr int D = 2, N = 8; CALL; } break;      \
+    case 216: { constexpr int D = 2, N = 16; CALL; } break;     \
+    case 232: { constexpr int D = 2, N = 32; CALL; } break;     \
+    case 308: { constexpr int D = 3, N = 8; CALL; } break;      \
+    case 316: { constexpr int D = 3, N = 16; CALL; } break;     \
+    default: return cudaErrorInvalidValue;                      \
+    }
+
+inline double4 d4(const double* v) { return make_double4(v[0], v[1], v[2], v[3]); }
+
+template <typename T, int D, int N>
+static cudaError_t rhs_launch(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
+                              cudaStream_t s, int one_slot) {
+    using C = RhsCfg<T, D, N>;
+    constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
+    auto kern = k_rhs<T, D, N, C::DZ, C::NTH>;
+    kern<<<grid, C::NTH, smem, s>>>(g, Us, U0, Uout, faces, stage, one_slot);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int N>
+static cudaError_t rhs_prepare() {
+    using C = RhsCfg<T, D, N>;
+    constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
+    return cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+template <typename T>
+cudaError_t Kernels<T>::prepare(const Grid& g) {
+    AMR_DISPATCH(g, return (rhs_prepare<T, D, N>()));
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Kernels<T>::ghost_fill(const Grid& g, T* U, int level, double tfrac, int grid, cudaStream_t s,
+                                   int one_slot) {
+    AMR_DISPATCH(g, (k_ghost<T, D, N><<<grid, 256, 0, s>>>(g, U, level, tfrac, one_slot, d4(g.dmr_pre),
+                                                            d4(g.dmr_post))));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
+                                  cudaStream_t s, int one_slot) {
+    AMR_DISPATCH(g, return (rhs_launch<T, D, N>(g, Us, U0, Uout, faces, stage, grid, s, one_slot)));
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Kernels<T>::reflux(const Grid& g, T* Uout, const T* faces, int stage, int grid, cudaStream_t s,
+                               int one_item) {
+    AMR_DISPATCH(g, (k_reflux<T, D, N><<<grid, 256, 0, s>>>(g, Uout, faces, stage, one_item)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::restrict_level(const Grid& g, T* U, int level, int grid, cudaStream_t s, int one_slot) {
+    AMR_DISPATCH(g, (k_restrict<T, D, N><<<grid, 256, 0, s>>>(g, U, level, one_slot)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::cfl(const Grid& g, const T* U, int grid, cudaStream_t s, int one_slot) {
+    AMR_DISPATCH(g, (k_cfl<T, D, N><<<grid, 256, 0, s>>>(g, U, one_slot)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::init_ic(const Grid& g, T* U, const int* list, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)(((long long)n * 4096 + 255) / 256 < 65536 ? ((long long)n * 4096 + 255) / 256 : 65536);
+    AMR_DISPATCH(g, (k_init_ic<T, D, N><<<grid, 256, 0, s>>>(g, U, list, n, d4(g.dmr_pre), d4(g.dmr_post))));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::prolong_new(const Grid& g, T* U, const int* list, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)(((long long)n * 4096 + 255) / 256 < 65536 ? ((long long)n * 4096 + 255) / 256 : 65536);
+    AMR_DISPATCH(g, (k_prolong_new<T, D, N><<<grid, 256, 0, s>>>(g, U, list, n)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::flag_plain(const Grid& g, const T* U, int* anyflag, int grid, cudaStream_t s) {
+    AMR_DISPATCH(g, (k_flag_plain<T, D, N><<<grid, 256, 0, s>>>(g, U, anyflag)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::cons_sums(const Grid& g, const T* U, double* partial, double* out, cudaStream_t s) {
+    AMR_DISPATCH(g, (k_cons_partial<T, D, N><<<1024, 256, 0, s>>>(g, U, partial)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (g.nv) {
+    case 3: k_cons_total<3><<<1, 256, 0, s>>>(g.counts, partial, out); break;
+    case 4: k_cons_total<4><<<1, 256, 0, s>>>(g.counts, partial, out); break;
+    default: k_cons_total<5><<<1, 256, 0, s>>>(g.counts, partial, out); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::unpack_interiors(const Grid& g, const T* U, const int* slots, int n, double* out,
+                                         cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    AMR_DISPATCH(g, (k_unpack<T, D, N><<<1024, 256, 0, s>>>(g, U, slots, n, out)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::pack_interiors(const Grid& g, T* U, const int* slots, int n, const double* in,
+                                       cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    AMR_DISPATCH(g, (k_pack<T, D, N><<<1024, 256, 0, s>>>(g, U, slots, n, in)));
+    return cudaGetLastError();
+}
+
+}  // namespace amr
