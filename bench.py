@@ -151,6 +151,7 @@ def main():
     ap.add_argument('--base', type=int, default=0, help='override base cells per dimension')
     ap.add_argument('--precision', type=int, default=32)
     ap.add_argument('--flagger', default='plain', choices=['plain', 'mlp'])
+    ap.add_argument('--weights', default=None, help='float32 .npy weights of the learned indicator')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     args = ap.parse_args()
@@ -175,7 +176,11 @@ def main():
     w = workload(args.workload)
     if args.base:
         w['base_cells'] = tuple(args.base if d < w['dim'] else 1 for d in range(3))
-    amr = AMR(w, precision=args.precision, flagger=args.flagger)
+    weights = None
+    if args.flagger == 'mlp':
+        path = args.weights or os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights', 'indicator_d%d.npy' % w['dim'])
+        weights = np.load(path).astype(np.float32)
+    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights)
     stream = amr._keep[1]
     amr.set_timing(True)
 
@@ -253,7 +258,7 @@ def main():
             'wall_s': wall}
 
     if rank == 0 and not args.no_e2e:
-        line['e2e'] = e2e_measure(AMR, w, args, fe)
+        line['e2e'] = e2e_measure(AMR, w, args, fe, weights)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, desc = oracle_sample(1)
         line['cpu_baseline'] = {'value': v, 'unit': UNIT, 'cores': 1, 'kind': 'oracle', 'sample': desc}
@@ -265,13 +270,13 @@ def main():
     return 0
 
 
-def e2e_measure(AMR, w, args, fe):
+def e2e_measure(AMR, w, args, fe, weights=None):
     """The same metric through the public API with host buffers: the initial
     hierarchy is uploaded from host memory (amr_set_state), every step calls
     amr_step + amr_regrid + amr_get_diag (time and conservation sums read
     back), and the final state is read back to host memory (amr_get_level)."""
     import numpy as np
-    amr = AMR(w, precision=args.precision, flagger=args.flagger)
+    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights)
     lv, co, da = [], [], []
     for l in range(w['levels']):
         c, x = amr.get_level(l)

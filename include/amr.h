@@ -100,6 +100,10 @@ typedef struct {
     void (*dev_free)(void* ptr, void* user);
     void* user;
     void* stream;         /* cudaStream_t the library issues its work on (NULL: legacy stream) */
+    const float* mlp_weights;  /* host weights of the learned indicator (layout of amr_set_mlp), copied
+                                  at init; NULL: the initial hierarchy uses the plain sensor and
+                                  amr_set_mlp must precede the first amr_regrid */
+    long mlp_n_weights;
 } amr_options_t;
 
 void amr_default_options(amr_options_t* opt);
@@ -163,7 +167,8 @@ int amr_flag_stats(amr_ctx* ctx, long long counts[4]);
 int amr_harvest(amr_ctx* ctx, long* n, double* samples, uint8_t* labels);
 
 /* Per-class device timing of the batched step, for profiling: enable (1) or
- * disable (0) CUDA events around each kernel class (the step is re-captured).
+ * disable (0) CUDA events around each kernel class. While enabled, the step
+ * is issued launch by launch instead of through the captured CUDA graph.
  * amr_get_timing synchronises and returns the last step's milliseconds:
  * ms[0] ghost fill, [1] fused RHS + stage, [2] reflux, [3] restriction,
  * [4] CFL reduction (0 if the step had a given dt), and of the last regrid

@@ -38,7 +38,7 @@ class Options(C.Structure):
                 ('max_patches', C.c_int), ('seed', C.c_uint64), ('amp', C.c_double),
                 ('mode', C.c_int), ('use_graph', C.c_int),
                 ('dev_alloc', ALLOC_FN), ('dev_free', FREE_FN), ('user', C.c_void_p),
-                ('stream', C.c_void_p)]
+                ('stream', C.c_void_p), ('mlp_weights', C.c_void_p), ('mlp_n_weights', C.c_long)]
 
 
 class AMRError(RuntimeError):
@@ -155,7 +155,7 @@ class AMR:
     """One hierarchy on the current CUDA device (see include/amr.h)."""
 
     def __init__(self, w, precision=64, flagger='plain', mode='batched', use_graph=True,
-                 max_patches=0, torch_memory=True):
+                 max_patches=0, torch_memory=True, mlp_weights=None):
         self.lib = load()
         self.w = dict(w)
         self.dim = w['dim']
@@ -172,6 +172,10 @@ class AMR:
         self.opt, self._keep = make_options(precision, w['cfl'], w['t_end'], flagger, w['theta_rho'],
                                             w['theta_p'], max_patches, w.get('seed', 0), w.get('amp', 0.01),
                                             mode, use_graph, torch_memory)
+        if mlp_weights is not None:
+            self._w_host = np.ascontiguousarray(mlp_weights, dtype=np.float32)
+            self.opt.mlp_weights = _ptr(self._w_host)
+            self.opt.mlp_n_weights = self._w_host.size
         base = (C.c_int * 3)(*w['base_cells'])
         ctx = C.c_void_p()
         rc = self.lib.amr_init(C.byref(ctx), C.byref(dom), w['gamma'], base, self.L, 2, self.N,

@@ -76,6 +76,7 @@ struct amr_ctx {
     // counters
     long long h2d = 0, d2h = 0, kernels = 0;
     bool broken = false;
+    bool initialising = false;
     std::string err;
 };
 
@@ -412,7 +413,7 @@ int step_impl(amr_ctx* c, double dt, double* dt_used) {
     if (c->mode == AMR_MODE_PER_PATCH) {
         int r = per_patch_step<T>(c, with_cfl);
         if (r) return r;
-    } else if (c->use_graph) {
+    } else if (c->use_graph && !c->timing) {
         cudaGraphExec_t& ex = with_cfl ? c->graph_cfl : c->graph_fixed;
         long long& nk = with_cfl ? c->graph_kernels_cfl : c->graph_kernels_fixed;
         if (!ex) {
@@ -447,7 +448,7 @@ template <typename T>
 int compute_requests(amr_ctx* c, std::vector<Key>& refine, std::vector<Key>& coarsen) {
     int r = fill_all_levels<T>(c, St<T>(c, 0), 0.0);
     if (r) return r;
-    if (c->flagger == AMR_FLAG_MLP) {
+    if (c->flagger == AMR_FLAG_MLP && (c->mlp_w || !c->initialising)) {
         if (!c->mlp_w) return fail(c, AMR_ERR_STATE, "learned indicator selected but no weights set");
         CK(Kernels<T>::flag_mlp(c->grid, St<T>(c, 0), c->mlp_w, c->anyflag, grid_size(c, 2), c->stream),
            "flag (learned)");
@@ -812,9 +813,22 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     {
         cudaError_t e = c->precision == 64 ? Kernels<double>::prepare(g) : Kernels<float>::prepare(g);
         if (e != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
+        e = c->precision == 64 ? Kernels<double>::prepare_mlp(g) : Kernels<float>::prepare_mlp(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
     }
 
+    if (c->opt.mlp_weights) {
+        if (c->opt.mlp_n_weights != mlp_n_weights(dim)) return bad("weight count does not match the dimension");
+        c->mlp_w = (float*)dalloc(c, c->opt.mlp_n_weights * sizeof(float));
+        if (!c->mlp_w) return fail(c, AMR_ERR_CUDA, "device allocation failed");
+        c->mlp_n = c->opt.mlp_n_weights;
+        CK(cudaMemcpyAsync(c->mlp_w, c->opt.mlp_weights, c->mlp_n * sizeof(float), cudaMemcpyHostToDevice,
+                           c->stream), "weights");
+        c->h2d += c->mlp_n * sizeof(float);
+    }
+    c->opt.mlp_weights = nullptr;     // host pointer not kept
     // level 0 and the initial condition, then the initial hierarchy
+    c->initialising = true;
     c->used.assign(c->cap, 0);
     c->key_of.assign(c->cap, 0);
     for (int s = 0; s < c->cap; ++s) c->free_slots.insert(s);
@@ -834,6 +848,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     }
     ++c->kernels;
     CK(cudaStreamSynchronize(c->stream), "init");
+    c->initialising = false;
     return AMR_OK;
 }
 
@@ -936,7 +951,8 @@ int amr_flag_stats(amr_ctx* c, long long counts[4]) {
     GUARD(c);
     if (!counts) return AMR_ERR_ARG;
     if (!c->mlp_w) return fail(c, AMR_ERR_STATE, "no learned indicator weights set");
-    unsigned long long* d = (unsigned long long*)c->dense_d;
+    unsigned long long* d = (unsigned long long*)c->dense_d;     // 4 counters + per-slot scratch flags
+    if ((size_t)c->cap + 16 > c->dense_cap * 2) return fail(c, AMR_ERR_STATE, "staging buffer too small");
     CK(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), c->stream), "stats");
     int r;
     cudaError_t e;
@@ -1002,10 +1018,9 @@ int amr_set_timing(amr_ctx* c, int enable) {
         CK(cudaEventCreate(&c->ev_cfl[0]), "event");
         CK(cudaEventCreate(&c->ev_cfl[1]), "event");
     }
+    // timed steps are issued launch by launch (events around each kernel
+    // class); the captured graphs are used again once timing is off
     c->timing = en;
-    // the captured steps must be re-captured with (or without) the events
-    if (c->graph_cfl) { cudaGraphExecDestroy(c->graph_cfl); c->graph_cfl = nullptr; }
-    if (c->graph_fixed) { cudaGraphExecDestroy(c->graph_fixed); c->graph_fixed = nullptr; }
     return AMR_OK;
 }
 

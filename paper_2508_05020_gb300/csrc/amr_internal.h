@@ -77,6 +77,7 @@ template <typename T>
 struct Kernels {
     // one-time kernel attributes (dynamic shared memory); call before any capture
     static cudaError_t prepare(const Grid& g);
+    static cudaError_t prepare_mlp(const Grid& g);
     // ghost cells of every patch of `level` (same-level copy, prolongation,
     // physical boundaries) at time t + tfrac * dt
     static cudaError_t ghost_fill(const Grid& g, T* U, int level, double tfrac, int grid,

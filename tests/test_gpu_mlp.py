@@ -1,0 +1,160 @@
+"""The learned refinement indicator on the GPU (through the C ABI) against the
+FP64 oracle network: features, BF16 tensor-core logits, FP32 gradients,
+training, and the fused per-patch flagging inside the AMR hierarchy."""
+import numpy as np
+import pytest
+
+from synth import mlp_init, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module', autouse=True)
+def cuda():
+    torch = pytest.importorskip('torch')
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+def samples(seed, n):
+    rng = np.random.default_rng(seed)
+    s = np.empty((n, 5, 3))
+    s[:] = rng.uniform(0.5, 2.0, size=(n, 1, 3))
+    s[:, :, 1] = rng.normal(0, 0.5, size=(n, 5))
+    jump = rng.uniform(size=n) < 0.5
+    pos = rng.integers(1, 5, size=n)
+    for i in np.nonzero(jump)[0]:
+        s[i, pos[i]:, 0] *= rng.uniform(0.3, 3.0)
+        s[i, pos[i]:, 2] *= rng.uniform(0.3, 3.0)
+    s[:, :, 0] *= 1.0 + 0.01 * rng.normal(size=(n, 5))
+    return s
+
+
+def bf16(x):
+    """Round to the nearest BF16 (ties to even), as __float2bfloat16_rn does."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def flat(p):
+    from oracle import mlp
+    return mlp.flatten(p).astype(np.float32)
+
+
+@pytest.mark.parametrize('dim', [1, 2, 3])
+def test_features_match_oracle(dim):
+    from oracle import mlp
+    from paper_2508_05020_gb300 import amr
+    s = samples(0, 64)
+    Xg = amr.mlp_features(dim, 1.4, s)
+    Xr = mlp.embedded_features(s, dim, 1.4)
+    assert Xg.shape == Xr.shape
+    assert np.allclose(Xg, Xr, rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize('dim', [1, 2, 3])
+def test_bf16_logits(dim):
+    # the oracle network evaluated in FP64 on the BF16-rounded weights,
+    # features and hidden activations the tensor-core kernel uses
+    from oracle import mlp
+    from paper_2508_05020_gb300 import amr
+    s = samples(1, 200)
+    X = mlp.embedded_features(s, dim, 1.4).astype(np.float32)
+    p = mlp_init(0, mlp.k_in(dim))
+    w = flat(p)
+    z = amr.mlp_infer(dim, X, w)
+    q = mlp.unflatten(w.astype(np.float64), mlp.k_in(dim))
+    a1 = bf16(X) @ bf16(q['W1']).T + q['b1']
+    h1 = bf16(np.maximum(a1, 0.0))
+    a2 = h1 @ bf16(q['W2']).T + q['b2']
+    zr = np.maximum(a2, 0.0) @ q['W3'][0] + q['b3'][0]
+    scale = max(1.0, float(np.sqrt(np.mean(zr ** 2))))
+    assert np.max(np.abs(z - zr)) <= 2e-2 * scale
+    # and against plain FP64 (no BF16 rounding) within the BF16 error budget
+    zf, _ = mlp.forward(q, X.astype(np.float64))
+    assert np.max(np.abs(z - zf)) <= 0.1 * scale
+
+
+@pytest.mark.parametrize('dim', [1, 2, 3])
+def test_fp32_gradient_matches_oracle(dim):
+    from oracle import mlp
+    from paper_2508_05020_gb300 import amr
+    s = samples(2, 96)
+    X = mlp.embedded_features(s, dim, 1.4)
+    y = np.repeat(mlp.plain_flag_1d(s, 0.05, 0.05), 2 * dim).astype(np.float64)
+    p = mlp_init(0, mlp.k_in(dim))
+    pw = mlp.bce_pos_weight(y)
+    lr, gr = mlp.loss_and_grad(p, X, y, pw)
+    lg, gg = amr.mlp_grad(dim, X.astype(np.float32), y.astype(np.float32), pw, flat(p))
+    gref = mlp.flatten(gr)
+    assert abs(lg - lr) <= 1e-5 * max(1.0, abs(lr))
+    assert np.linalg.norm(gg - gref) <= 1e-4 * np.linalg.norm(gref)
+
+
+def test_training_learns_the_plain_flag():
+    from oracle import mlp
+    from paper_2508_05020_gb300 import amr
+    s = samples(3, 4000)
+    t = samples(4, 1000)
+    dim = 2
+    X = amr.mlp_features(dim, 1.4, s)
+    y = np.repeat(mlp.plain_flag_1d(s, 0.05, 0.05), 2 * dim).astype(np.float32)
+    pw = mlp.bce_pos_weight(y)
+    w0 = flat(mlp_init(0, mlp.k_in(dim)))
+    w, hist = amr.mlp_train(dim, X, y, pw, w0, epochs=30, batch=256, lr=2e-3, seed=1)
+    assert hist[-1] < 0.5 * hist[0]
+    Xt = amr.mlp_features(dim, 1.4, t)
+    yt = np.repeat(mlp.plain_flag_1d(t, 0.05, 0.05), 2 * dim)
+    pred = amr.mlp_infer(dim, Xt, w) > 0
+    tp = np.sum(pred & yt)
+    recall = tp / max(1, np.sum(yt))
+    precision = tp / max(1, np.sum(pred))
+    assert recall > 0.9 and precision > 0.8, (recall, precision)
+
+
+def test_fused_flags_agree_with_oracle_flagger():
+    # identical state on both sides; per-patch decisions may differ only where
+    # the oracle's largest band logit is within the BF16 margin of zero
+    from oracle import mlp
+    from oracle.amr import Oracle
+    from paper_2508_05020_gb300.amr import AMR
+    w = workload('riemann2d', base_cells=(32, 32, 1), patch=8)
+    r = Oracle(w)
+    for _ in range(2):
+        r.step()
+        r.regrid()
+    p = mlp_init(5, mlp.k_in(2))
+    p['b3'][:] = -0.5
+    wf = flat(p)
+    q = mlp.unflatten(wf.astype(np.float64), mlp.k_in(2))
+    r.flag_override = mlp.make_flagger(q, 1.4)
+    g = AMR(w, flagger='mlp')
+    g.set_mlp(wf)
+    keys = r.mesh.canonical()
+    g.set_state(np.array([k[0] for k in keys]), np.array([[k[1][0], k[1][1]] for k in keys]),
+                np.stack([r.U[k][r.inner()].reshape((4, 8, 8)) for k in keys]), t=r.t)
+    rg, cg = g.requests()
+    rr, cr, af = r.requests()
+    # margin per leaf patch: max logit over its in-domain band cells
+    margin = {}
+    for k in af:
+        R, Us, P, cells = mlp.cell_stencils(r, k)
+        z, _ = mlp.forward(q, mlp.features(R, Us, P, 1.4))
+        ok = np.ones(len(z), dtype=bool)
+        for d in range(2):
+            gidx = k[1][d] * r.N + cells[:, d]
+            ok &= (gidx >= 0) & (gidx < r.mesh.extent(k[0])[d] * r.N)
+        margin[k] = float(np.max(z[ok]))
+    sg = {(int(x[0]), (int(x[1]), int(x[2]), int(x[3]))) for x in rg}
+    sr = set(rr)
+    for k in sg ^ sr:
+        assert abs(margin[k]) < 0.05, (k, margin[k])
+    assert len(sg ^ sr) <= max(1, len(sr) // 20)
+    counts = g.flag_stats()
+    assert counts.sum() > 0
+    g.close()

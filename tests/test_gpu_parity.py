@@ -56,7 +56,7 @@ def compare(gpu, ref, tol=TOL64):
 def run_both(w, steps, regrid=True, **kw):
     g = amr(w, **kw)
     r = oracle(w)
-    compare(g, r, tol=1e-14)           # initial hierarchy and point-sampled state
+    compare(g, r, tol=1e-15)           # initial hierarchy and point-sampled state
     for _ in range(steps):
         dg = g.step()
         dr = r.step()
@@ -67,21 +67,27 @@ def run_both(w, steps, regrid=True, **kw):
     return g, r
 
 
-@pytest.mark.parametrize('name,kw,steps', [
-    ('sod', {}, 25),
-    ('sod', dict(levels=2, patch=8, base_cells=(32, 1, 1)), 15),
-    ('shu_osher', {}, 6),
-    ('riemann2d', dict(base_cells=(32, 32, 1), patch=8), 4),
-    ('riemann2d', dict(base_cells=(64, 64, 1)), 2),
-    ('dmr', dict(base_cells=(64, 16, 1), patch=8, levels=3), 3),
-    ('implosion', dict(base_cells=(32, 32, 1), patch=8, levels=3), 4),
-    ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2), 2),
-    ('blast3d', dict(base_cells=(32, 32, 32), patch=16, levels=2), 1),
+# the FP64 path evaluates the oracle's expressions operation for operation
+# (no FMA contraction, IEEE division and square root), so it reproduces the
+# oracle bit for bit; only initial conditions with sin() (CUDA's sin against
+# the host's) may differ in the last bit, and there the 1e-9 bar applies
+@pytest.mark.parametrize('name,kw,steps,tol', [
+    ('sod', {}, 25, 0.0),
+    ('sod', dict(levels=2, patch=8, base_cells=(32, 1, 1)), 15, 0.0),
+    ('shu_osher', {}, 6, TOL64),
+    ('density_wave', dict(levels=2, patch=16), 5, TOL64),
+    ('riemann2d', dict(base_cells=(32, 32, 1), patch=8), 4, 0.0),
+    ('riemann2d', dict(base_cells=(64, 64, 1)), 2, 0.0),
+    ('dmr', dict(base_cells=(64, 16, 1), patch=8, levels=3), 3, 0.0),
+    ('implosion', dict(base_cells=(32, 32, 1), patch=8, levels=3), 4, 0.0),
+    ('constant', {}, 3, 0.0),
+    ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2), 2, 0.0),
+    ('blast3d', dict(base_cells=(32, 32, 32), patch=16, levels=2), 1, 0.0),
 ])
-def test_fp64_matches_oracle(name, kw, steps):
+def test_fp64_matches_oracle(name, kw, steps, tol):
     w = workload(name, **kw)
     g, r = run_both(w, steps)
-    compare(g, r)
+    compare(g, r, tol=tol)
     tg, cg, _ = g.diag()
     assert abs(tg - r.t) <= 1e-12 * r.t
     g.close()
