@@ -128,6 +128,21 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ----------------------------------------------------------------------------- ranks
+def combine_ranks(elapsed, units, dist=None, device='cpu'):
+    """Whole-job timing over ranks: (max elapsed, total units). Each rank runs its
+    own replica, so the only exchange is this scalar reduction after the timed
+    region (gloo on CPU in tests, NCCL under torchrun on GPUs)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return elapsed, units
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ----------------------------------------------------------------------------- GPU
 def rhs_flops_per_launch(amr, w, flops):
     """Algorithmic FLOPs of one fused RHS launch: faces x FLOP/face + cells x FLOP/cell."""
@@ -209,25 +224,23 @@ def main():
         amr.step(sync=False)
         ms, n = amr.timing()
         rhs_ms.append(ms[1] / max(n[1], 1))
-        kinds += ms
+        kinds[:5] += ms[:5]                 # device classes of this step
         if flops:
             flops_rhs.append(rhs_flops_per_launch(amr, w, flops))
         amr.regrid()
         ms2, _ = amr.timing()
-        kinds[5:] += ms2[5:]
+        kinds[5:] += ms2[5:]                # phases of this step's regrid
     ev1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1000.0
     _, _, k1 = amr.counters()
-    if dist:
-        t = torch.tensor([elapsed], device='cuda')
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        dist.barrier()
     fe = fine_equivalent_cells(w)
-    value = fe * args.steps * world / elapsed
+    elapsed, units = combine_ranks(elapsed, float(fe * args.steps), dist, device='cuda')
+    if dist:
+        dist.barrier()
+    value = units / elapsed
     t_now, cons, ppl = amr.diag()
 
     peaks = load_json(PEAKS_FILE, {})
