@@ -218,6 +218,29 @@ int amr_mlp_train(int dim, const float* X, const float* y, long n, float pos_wei
                   int epochs, int batch, float lr, uint64_t shuffle_seed,
                   float* weights, float* loss_hist, const amr_options_t* opt);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free variant of amr_mlp_grad (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory: code running inside a
+ * task-based runtime that owns all device memory and only maps buffers for
+ * its tasks, code that issues work while a CUDA stream capture is in progress,
+ * and real-time loops where an allocation could synchronise the device.
+ * X (n x K floats), y (n floats), weights (flat layout of amr_set_mlp), grad
+ * (same layout, output) and loss (one float, output) are DEVICE pointers owned
+ * by the caller; work is issued on `stream` (a cudaStream_t, NULL = legacy
+ * stream) and not synchronised. The hidden activations use a fixed scratch
+ * array compiled into the library (about 2.1 MB on every GPU that loads it,
+ * held until the process exits), so n is limited to
+ * AMR_MLP_NOALLOC_MAX_ROWS; larger n returns AMR_ERR_ARG. The call allocates
+ * nothing. Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call outside any
+ * stream capture. Every call shares the one array: calls that overlap on the
+ * GPU (other streams, other host threads) race and give wrong results.
+ * Returns AMR_OK, AMR_ERR_ARG or AMR_ERR_CUDA. */
+#define AMR_MLP_NOALLOC_MAX_ROWS 2048
+int amr_mlp_grad_noalloc(int dim, const float* X, const float* y, long n, float pos_weight,
+                         const float* weights, float* grad, float* loss, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,8 @@ SIGNATURES = [
                                C.c_void_p, C.c_void_p, C.POINTER(Options)]),
     ('amr_mlp_train', C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_long, C.c_float, C.c_int, C.c_int,
                                 C.c_float, C.c_uint64, C.c_void_p, C.c_void_p, C.POINTER(Options)]),
+    ('amr_mlp_grad_noalloc', C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_long, C.c_float, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]),
 ]
 
 

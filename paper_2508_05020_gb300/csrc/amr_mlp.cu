@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "amr.h"
@@ -367,3 +368,67 @@ int amr_mlp_train(int dim, const float* X, const float* y, long n, float pw, int
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free gradient: amr_mlp_grad_noalloc.
+//
+// Some callers cannot allocate device memory: code running inside a task-based
+// runtime that owns the whole device memory (a task there only gets the
+// buffers the runtime maps for it, and an allocation behind the runtime's back
+// can fail or fragment its pool), code issuing work while a CUDA stream
+// capture is in progress (allocation is not allowed there), and real-time
+// loops where an allocation may synchronise the device. For them the hidden
+// activations of the forward/backward pass live in the fixed array below,
+// which every GPU that loads this library holds until the process exits:
+// 4 x 2048 x 64 + 2 x 2048 + 64 floats (about 2.1 MB).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr long NOALLOC_ROWS = AMR_MLP_NOALLOC_MAX_ROWS;
+constexpr size_t NOALLOC_FLOATS = 4 * NOALLOC_ROWS * MLP_H + 2 * NOALLOC_ROWS + 64;
+}  // namespace
+
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_FLOATS];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on device `dev` (current). In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device with cudaGetSymbolAddress and cached.
+float* noalloc_scratch(int dev) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (dev >= 0 && dev < NOALLOC_MAX_DEVICES && g_noalloc_ptr[dev]) return g_noalloc_ptr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    if (dev >= 0 && dev < NOALLOC_MAX_DEVICES) g_noalloc_ptr[dev] = reinterpret_cast<float*>(p);
+    return reinterpret_cast<float*>(p);
+}
+}  // namespace
+
+extern "C" int amr_mlp_grad_noalloc(int dim, const float* X, const float* y, long n, float pos_weight,
+                                    const float* weights, float* grad, float* loss, void* stream) {
+    if (dim < 1 || dim > 3 || !X || !y || !weights || !grad || !loss || n <= 0) return AMR_ERR_ARG;
+    if (n > AMR_MLP_NOALLOC_MAX_ROWS) return AMR_ERR_ARG;      // beyond the fixed scratch
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AMR_ERR_CUDA;
+    float* base = noalloc_scratch(dev);
+    if (!base) return AMR_ERR_CUDA;
+    const size_t hs = (size_t)NOALLOC_ROWS * MLP_H;
+    float* H1 = base;
+    float* H2 = base + hs;
+    float* dH1 = base + 2 * hs;
+    float* dH2 = base + 3 * hs;
+    float* dz = base + 4 * hs;
+    float* lv = dz + NOALLOC_ROWS;
+    float* lacc = lv + NOALLOC_ROWS;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the loss accumulator keeps the previous call's value: clear it
+    if (cudaMemsetAsync(lacc, 0, sizeof(float), s) != cudaSuccess) return AMR_ERR_CUDA;
+    if (fwd_bwd(dim, X, nullptr, y, (int)n, pos_weight, weights, grad, lacc, 1.0f / (float)n, H1, H2, dz, lv, dH1,
+                dH2, s))
+        return AMR_ERR_CUDA;
+    if (cudaMemcpyAsync(loss, lacc, sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return AMR_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? AMR_OK : AMR_ERR_CUDA;
+}
