@@ -167,6 +167,7 @@ def main():
     ap.add_argument('--precision', type=int, default=32)
     ap.add_argument('--flagger', default='plain', choices=['plain', 'mlp'])
     ap.add_argument('--weights', default=None, help='float32 .npy weights of the learned indicator')
+    ap.add_argument('--max-patches', type=int, default=0, help='pool capacity (0: every level fully refined)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     args = ap.parse_args()
@@ -195,7 +196,7 @@ def main():
     if args.flagger == 'mlp':
         path = args.weights or os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights', 'indicator_d%d.npy' % w['dim'])
         weights = np.load(path).astype(np.float32)
-    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights)
+    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights, max_patches=args.max_patches)
     stream = amr._keep[1]
     amr.set_timing(True)
 

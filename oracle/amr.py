@@ -562,8 +562,10 @@ class Oracle:
     # ---- refinement sensor and regrid -----------------------------------------
     def patch_flags(self, key):
         """Cell flags on the patch band [-2, N+1]^d (in-domain cells only): for
-        phi in (rho, p) and each dimension, s = |phi_+ - phi_-| / (phi_+ + 2 phi_0
-        + phi_-); a cell is flagged if s > theta. Requires filled ghosts."""
+        phi in (rho, p) and each dimension, the relative jump
+        s = |phi_+ - phi_-| / (phi_+ + 2 phi_0 + phi_-) exceeds theta, evaluated
+        without the division as |phi_+ - phi_-| > theta (phi_+ + 2 phi_0 + phi_-)
+        (the same test for positive rho and p). Requires filled ghosts."""
         A = self.U[key]
         rho, u, p, T = euler.primitives(A, self.dim, self.gamma)
         l, c = key
@@ -578,8 +580,7 @@ class Oracle:
                 slm[ax] = slice(G - 3, G + N + 1)
                 slp[ax] = slice(G - 1, G + N + 3)
                 fm, f0, fp = phi[tuple(slm)], phi[tuple(sl0)], phi[tuple(slp)]
-                s = np.abs(fp - fm) / (fp + 2.0 * f0 + fm)
-                f = s > th
+                f = np.abs(fp - fm) > th * (fp + 2.0 * f0 + fm)
                 flag = f if flag is None else (flag | f)
         # in-domain mask
         mask = np.ones(flag.shape, dtype=bool)

@@ -148,8 +148,7 @@ def plain_flag_1d(samples, theta_rho, theta_p):
     out = np.zeros(samples.shape[0], dtype=bool)
     for j, th in ((0, theta_rho), (2, theta_p)):
         fm, f0, fp = samples[:, 1, j], samples[:, 2, j], samples[:, 3, j]
-        s = np.abs(fp - fm) / (fp + 2.0 * f0 + fm)
-        out |= s > th
+        out |= np.abs(fp - fm) > th * (fp + 2.0 * f0 + fm)
     return out
 
 

@@ -416,8 +416,13 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
 template <int D, int N, int DZ> struct Chunk {
     static constexpr int S = N + 2 * G;
     static constexpr int CX = N, CY = D >= 2 ? N : 1, CZ = D == 3 ? DZ : 1;
-    static constexpr int QX = S, QY = D >= 2 ? S : 1, QZ = D == 3 ? DZ + 2 * G : 1;
-    static constexpr int QN = QX * QY * QZ;
+    // staged cells per variable: 1D/2D the whole slot; 3D the DZ centre planes
+    // in full (S x S) and the 2G halo planes only over the interior N x N, the
+    // only part the z-faces read
+    static constexpr int QX = S, QY = D >= 2 ? S : 1, QZ = D == 3 ? DZ : 1;
+    static constexpr int QC = QX * QY * QZ;                       // centre cells
+    static constexpr int QH = D == 3 ? 2 * G * N * N : 0;         // compact halo cells
+    static constexpr int QN = QC + QH;
     static constexpr int CELLS = CX * CY * CZ;
     static constexpr int NCH = D == 3 ? N / DZ : 1;
     static constexpr int F0 = (CX + 1) * CY * CZ;
@@ -460,10 +465,18 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
         const int pf = g.pflag[slot];
         // 1. stage the chunk and its halo as primitives
         for (int idx = threadIdx.x; idx < C::QN; idx += NTH) {
-            const int qx = idx % C::QX;
-            const int qy = (idx / C::QX) % C::QY;
-            const int qz = idx / (C::QX * C::QY);
-            const int sz = D == 3 ? z0 + qz : 0;
+            int qx, qy, sz;
+            if (idx < C::QC) {                               // centre planes, full S x S
+                qx = idx % C::QX;
+                qy = (idx / C::QX) % C::QY;
+                sz = D == 3 ? z0 + G + idx / (C::QX * C::QY) : 0;
+            } else {                                         // 3D halo planes, interior N x N
+                const int h = idx - C::QC;
+                qx = h % N + G;
+                qy = (h / N) % N + G;
+                const int zh = h / (N * N);
+                sz = z0 + (zh < G ? zh : zh + DZ);
+            }
             T Uc[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) Uc[v] = Us[slot_index(g, slot, v, sz, qy, qx)];
@@ -476,51 +489,54 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
         }
         __syncthreads();
         T R[CPT][NV];
-#pragma unroll
+        // one rolled loop over the dimensions: a single copy of the face-flux
+        // code keeps the kernel inside the instruction cache
+#pragma unroll 1
         for (int d = 0; d < D; ++d) {
             const int ex = d == 0, ey = d == 1, ez = d == 2;
             const int FX = C::CX + ex, FY = C::CY + ey, FZ = C::CZ + ez;
             const int nf = FX * FY * FZ;
-            const int step = d == 0 ? 1 : (d == 1 ? C::QX : C::QX * C::QY);
+            const int step = d == 0 ? 1 : C::QX;          // x and y pencils stay in one centre plane
+            // tangential velocity components in increasing dimension order
+            const int t1 = d == 0 ? 1 : 0;
+            const int t2 = d == 2 ? 1 : 2;
             for (int f = threadIdx.x; f < nf; f += NTH) {
                 const int fi = f % FX;
                 const int fj = (f / FX) % FY;
                 const int fk = f / (FX * FY);
                 // smem index of pencil node 0 (cell index - 3 along d; G = 3)
-                const int bx = (D >= 1 ? fi + G : 0) - (ex ? G : 0);
-                const int by = (D >= 2 ? fj + G : 0) - (ey ? G : 0);
-                const int bz = (D == 3 ? fk + G : 0) - (ez ? G : 0);
-                const int base = (bz * C::QY + by) * C::QX + bx;
+                int base = 0;
+                if (d < 2) {
+                    const int bx = fi + G - (ex ? G : 0);
+                    const int by = (D >= 2 ? fj + G : 0) - (ey ? G : 0);
+                    base = ((D == 3 ? fk : 0) * C::QY + by) * C::QX + bx;
+                }
                 T pp[6], un[6], ut[NT > 0 ? NT : 1][6], Tt[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
-                    const int id = base + k * step;
+                    int id;
+                    if (D < 3 || d < 2) {
+                        id = base + k * step;
+                    } else {                                 // z pencil: halo plane or centre plane
+                        const int zz = fk + k;               // staged z index 0 .. DZ + 5
+                        id = (zz >= G && zz < G + DZ)
+                                 ? ((zz - G) * C::QY + fj + G) * C::QX + fi + G
+                                 : C::QC + ((zz < G ? zz : zz - DZ) * N + fj) * N + fi;
+                    }
                     pp[k] = q[id];
                     un[k] = q[(1 + d) * C::QN + id];
                     Tt[k] = q[(D + 1) * C::QN + id];
-                    int j = 0;
-#pragma unroll
-                    for (int e = 0; e < D; ++e) {
-                        if (e == d) continue;
-                        ut[j][k] = q[(1 + e) * C::QN + id];
-                        ++j;
-                    }
+                    if (NT >= 1) ut[0][k] = q[(1 + t1) * C::QN + id];
+                    if (NT >= 2) ut[NT > 1 ? 1 : 0][k] = q[(1 + t2) * C::QN + id];
                 }
                 T Fp[NT + 3];
                 face_flux<T, NT>(pp, un, ut, Tt, gamma, gm1, Fp);
                 // pencil order -> global variable order
                 T Fg[NV];
                 Fg[0] = Fp[0];
-                Fg[1 + d] = Fp[1];
-                {
-                    int j = 0;
 #pragma unroll
-                    for (int e = 0; e < D; ++e) {
-                        if (e == d) continue;
-                        Fg[1 + e] = Fp[2 + j];
-                        ++j;
-                    }
-                }
+                for (int e = 0; e < D; ++e)
+                    Fg[1 + e] = e == d ? Fp[1] : (e == t1 ? Fp[NT >= 1 ? 2 : 1] : Fp[NT >= 2 ? 3 : 1]);
                 Fg[NV - 1] = Fp[NT + 2];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Fs[v * C::FMAX + f] = Fg[v];
@@ -539,6 +555,7 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
             }
             __syncthreads();
             const T dxd = T(g.dx[lev][d]);
+            const int fstep = d == 0 ? 1 : (d == 1 ? FX : FX * FY);
 #pragma unroll
             for (int n = 0; n < CPT; ++n) {
                 const int cidx = threadIdx.x + n * NTH;
@@ -547,7 +564,7 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
                     const int cj = (cidx / C::CX) % C::CY;
                     const int ck = cidx / (C::CX * C::CY);
                     const int flo = (ck * FY + cj) * FX + ci;
-                    const int fhi = flo + (d == 0 ? 1 : (d == 1 ? FX : FX * FY));
+                    const int fhi = flo + fstep;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         const T dv = Num<T>::div(Fs[v * C::FMAX + fhi] - Fs[v * C::FMAX + flo], dxd);
@@ -708,7 +725,8 @@ __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
     constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
     const int npatch = one_slot >= 0 ? 1 : g.counts[1];
     const long long total = (long long)npatch * NC;
-    const double gm1 = g.gamma - 1.0;
+    const T gamma = T(g.gamma);
+    const T gm1 = T(g.gamma) - T(1);
     double lmax = 0.0;
     bool bad = false;
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
@@ -718,25 +736,20 @@ __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
         const int slot = one_slot >= 0 ? one_slot : g.leaf_list[pi];
         const int lev = g.level[slot];
         const int x = ci % N, y = D >= 2 ? (ci / N) % N : 0, z = D == 3 ? ci / (N * N) : 0;
-        double Uc[NV];
+        T Uc[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-            Uc[v] = (double)U[slot_index(g, slot, v, D == 3 ? z + G : 0, D >= 2 ? y + G : 0, x + G)];
-        const double rho = Uc[0];
-        double u[3];
+            Uc[v] = U[slot_index(g, slot, v, D == 3 ? z + G : 0, D >= 2 ? y + G : 0, x + G)];
+        T rho, u[D], p, Tt;
+        primitives<T, D>(Uc, gm1, rho, u, p, Tt);
+        if (!(rho > T(0)) || !(p > T(0))) bad = true;
+        const T c = Num<T>::sqr(Num<T>::div(gamma * p, rho));
+        T lam = Num<T>::div(fabs(u[0]) + c, T(g.dx[lev][0]));
 #pragma unroll
-        for (int d = 0; d < D; ++d) u[d] = Uc[1 + d] / rho;
-        double usq = u[0] * u[0];
-#pragma unroll
-        for (int d = 1; d < D; ++d) usq = usq + u[d] * u[d];
-        const double p = gm1 * (Uc[D + 1] - 0.5 * rho * usq);
-        if (!(rho > 0.0) || !(p > 0.0)) bad = true;
-        const double c = sqrt(g.gamma * p / rho);
-        double lam = (fabs(u[0]) + c) / g.dx[lev][0];
-#pragma unroll
-        for (int d = 1; d < D; ++d) lam = lam + (fabs(u[d]) + c) / g.dx[lev][d];
-        if (!(lam <= 1.0e300)) bad = true;
-        else lmax = fmax(lmax, lam);
+        for (int d = 1; d < D; ++d) lam = lam + Num<T>::div(fabs(u[d]) + c, T(g.dx[lev][d]));
+        const double ld = (double)lam;
+        if (!(ld <= 1.0e300)) bad = true;
+        else lmax = fmax(lmax, ld);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -754,23 +767,51 @@ __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
 
 // ---------------------------------------------------------------------------
 // K9 (plain): relative-jump sensor on rho and p over the band [-2, N+1]^d of
-// each leaf patch (in-domain cells), evaluated in FP64:
-// s = |phi+ - phi-| / (phi+ + 2 phi0 + phi-) > theta; per-patch OR.
+// each leaf patch (in-domain cells): a cell is flagged if for some dimension
+// |phi+ - phi-| > theta (phi+ + 2 phi0 + phi-) for phi in (rho, p) (the
+// relative jump above theta, without the division). rho and p of the whole
+// slot are staged in shared memory once per patch, in the storage precision;
+// per-patch OR by __syncthreads_or.
 // ---------------------------------------------------------------------------
+template <int D, int N> struct FlagStage {
+    static constexpr int S = N + 2 * G;
+    static constexpr int SX = S, SY = D >= 2 ? S : 1, SZ = D == 3 ? S : 1;
+    static constexpr int NS = SX * SY * SZ;
+};
+
+template <typename T, int D, int N>
+constexpr size_t flag_smem_bytes() { return 2 * sizeof(T) * FlagStage<D, N>::NS; }
+
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* anyflag) {
+    using F = FlagStage<D, N>;
     constexpr int NV = D + 2;
     constexpr int B = N + 4;
     constexpr int NB = D == 1 ? B : (D == 2 ? B * B : B * B * B);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* srho = reinterpret_cast<T*>(smem_raw);
+    T* sp = srho + F::NS;
     const int npatch = g.counts[1];
-    const double gm1 = g.gamma - 1.0;
+    const T gm1 = T(g.gamma) - T(1);
+    const T thr = T(g.theta_rho), thp = T(g.theta_p);
     for (int pi = blockIdx.x; pi < npatch; pi += gridDim.x) {
         const int slot = g.leaf_list[pi];
         const int lev = g.level[slot];
         const int c[3] = {g.coord[slot * 3], g.coord[slot * 3 + 1], g.coord[slot * 3 + 2]};
+        for (int idx = threadIdx.x; idx < F::NS; idx += blockDim.x) {
+            const int x = idx % F::SX, y = (idx / F::SX) % F::SY, z = idx / (F::SX * F::SY);
+            T Uc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Uc[v] = U[slot_index(g, slot, v, z, y, x)];
+            T rho, u[D], p, Tt;
+            primitives<T, D>(Uc, gm1, rho, u, p, Tt);
+            srho[idx] = rho;
+            sp[idx] = p;
+        }
+        __syncthreads();
         bool any = false;
         for (int bi = threadIdx.x; bi < NB; bi += blockDim.x) {
-            int l[3] = {bi % B - 2, D >= 2 ? (bi / B) % B - 2 : 0, D == 3 ? bi / (B * B) - 2 : 0};
+            const int l[3] = {bi % B - 2, D >= 2 ? (bi / B) % B - 2 : 0, D == 3 ? bi / (B * B) - 2 : 0};
             bool indom = true;
 #pragma unroll
             for (int d = 0; d < D; ++d) {
@@ -779,29 +820,15 @@ __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* any
                 indom = indom && Gd >= 0 && Gd < g.ext[lev][d] * N;
             }
             if (!indom) continue;
+            const int i0 = (sc<D>(2, l[2]) * F::SY + sc<D>(1, l[1])) * F::SX + sc<D>(0, l[0]);
+            const T r0 = srho[i0], p0 = sp[i0];
             bool f = false;
-            double Uc[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-                Uc[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2]), sc<D>(1, l[1]), sc<D>(0, l[0]))];
-            const double r0 = Uc[0];
-            const double p0 = pressure_d<D>(Uc, gm1);
 #pragma unroll
             for (int d = 0; d < D; ++d) {
-                double Um[NV], Up[NV];
-                const int ex = d == 0, ey = d == 1, ez = d == 2;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    Um[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2] - ez), sc<D>(1, l[1] - ey),
-                                                 sc<D>(0, l[0] - ex))];
-                    Up[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2] + ez), sc<D>(1, l[1] + ey),
-                                                 sc<D>(0, l[0] + ex))];
-                }
-                const double rm = Um[0], rp = Up[0];
-                const double pm = pressure_d<D>(Um, gm1), pp = pressure_d<D>(Up, gm1);
-                const double sr = fabs(rp - rm) / (rp + 2.0 * r0 + rm);
-                const double sp = fabs(pp - pm) / (pp + 2.0 * p0 + pm);
-                f = f || (sr > g.theta_rho) || (sp > g.theta_p);
+                const int st = d == 0 ? 1 : (d == 1 ? F::SX : F::SX * F::SY);
+                const T rm = srho[i0 - st], rp = srho[i0 + st];
+                const T pm = sp[i0 - st], pp = sp[i0 + st];
+                f = f || (fabs(rp - rm) > thr * (rp + T(2) * r0 + rm)) || (fabs(pp - pm) > thp * (pp + T(2) * p0 + pm));
             }
             any = any || f;
         }

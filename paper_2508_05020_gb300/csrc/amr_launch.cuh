@@ -41,8 +41,11 @@ template <typename T, int D, int N>
 static cudaError_t rhs_prepare() {
     using C = RhsCfg<T, D, N>;
     constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
-    return cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_flag_plain<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)flag_smem_bytes<T, D, N>());
 }
 
 template <typename T>
@@ -103,7 +106,7 @@ cudaError_t Kernels<T>::prolong_new(const Grid& g, T* U, const int* list, int n,
 
 template <typename T>
 cudaError_t Kernels<T>::flag_plain(const Grid& g, const T* U, int* anyflag, int grid, cudaStream_t s) {
-    AMR_DISPATCH(g, (k_flag_plain<T, D, N><<<grid, 256, 0, s>>>(g, U, anyflag)));
+    AMR_DISPATCH(g, (k_flag_plain<T, D, N><<<grid, 256, flag_smem_bytes<T, D, N>(), s>>>(g, U, anyflag)));
     return cudaGetLastError();
 }
 

@@ -36,9 +36,9 @@ __global__ void k_harvest(Grid g, const T* U, double* samples, unsigned char* la
             samples[it * 15 + k * 3 + 1] = u[k];
             samples[it * 15 + k * 3 + 2] = p[k];
         }
-        const double sr = fabs(r[3] - r[1]) / (r[3] + 2.0 * r[2] + r[1]);
-        const double sp = fabs(p[3] - p[1]) / (p[3] + 2.0 * p[2] + p[1]);
-        labels[it] = indom ? ((sr > g.theta_rho || sp > g.theta_p) ? 1 : 0) : 255;
+        const bool fr = fabs(r[3] - r[1]) > g.theta_rho * (r[3] + 2.0 * r[2] + r[1]);
+        const bool fp = fabs(p[3] - p[1]) > g.theta_p * (p[3] + 2.0 * p[2] + p[1]);
+        labels[it] = indom ? ((fr || fp) ? 1 : 0) : 255;
     }
 }
 
@@ -87,25 +87,26 @@ constexpr size_t mlp_flag_smem() {
 template <typename T, int D, int N>
 __device__ bool plain_flag_cell(const Grid& g, const T* U, int slot, const int* l) {
     constexpr int NV = D + 2;
-    const double gm1 = g.gamma - 1.0;
-    double Uc[NV];
+    const T gm1 = T(g.gamma) - T(1);
+    auto rho_p = [&](int dx, int dy, int dz, T& r, T& p) {
+        T Uc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Uc[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2]), sc<D>(1, l[1]), sc<D>(0, l[0]))];
-    const double r0 = Uc[0], p0 = pressure_d<D>(Uc, gm1);
+        for (int v = 0; v < NV; ++v)
+            Uc[v] = U[slot_index(g, slot, v, sc<D>(2, l[2] + dz), sc<D>(1, l[1] + dy), sc<D>(0, l[0] + dx))];
+        T u[D], Tt;
+        primitives<T, D>(Uc, gm1, r, u, p, Tt);
+    };
+    T r0, p0;
+    rho_p(0, 0, 0, r0, p0);
     bool f = false;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        double Um[NV], Up[NV];
         const int ex = d == 0, ey = d == 1, ez = d == 2;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            Um[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2] - ez), sc<D>(1, l[1] - ey), sc<D>(0, l[0] - ex))];
-            Up[v] = (double)U[slot_index(g, slot, v, sc<D>(2, l[2] + ez), sc<D>(1, l[1] + ey), sc<D>(0, l[0] + ex))];
-        }
-        const double pm = pressure_d<D>(Um, gm1), pp = pressure_d<D>(Up, gm1);
-        const double sr = fabs(Up[0] - Um[0]) / (Up[0] + 2.0 * r0 + Um[0]);
-        const double sp = fabs(pp - pm) / (pp + 2.0 * p0 + pm);
-        f = f || (sr > g.theta_rho) || (sp > g.theta_p);
+        T rm, pm, rp, pp;
+        rho_p(-ex, -ey, -ez, rm, pm);
+        rho_p(ex, ey, ez, rp, pp);
+        f = f || (fabs(rp - rm) > T(g.theta_rho) * (rp + T(2) * r0 + rm)) ||
+            (fabs(pp - pm) > T(g.theta_p) * (pp + T(2) * p0 + pm));
     }
     return f;
 }
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(256) k_flag_mlp(Grid g, const T* __restrict__ 
         koff[k] = (kind << 28) | (f * P::PLANE + (oz * P::PY + oy) * P::PX + ox + (1 << 20));
     }
     __syncthreads();
-    const double gm1 = g.gamma - 1.0;
+    const T gm1 = T(g.gamma) - T(1);
     const int npatch = g.counts[1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int gq = lane >> 2;
@@ -147,14 +148,15 @@ __global__ void __launch_bounds__(256) k_flag_mlp(Grid g, const T* __restrict__ 
         for (int idx = threadIdx.x; idx < P::PLANE; idx += blockDim.x) {
             const int px = idx % P::PX, py = (idx / P::PX) % P::PY, pz = idx / (P::PX * P::PY);
             const int sz = D == 3 ? zb0 - 2 + pz + G : 0;
-            double Uc[D + 2];
+            T Uc[D + 2];
 #pragma unroll
-            for (int v = 0; v < D + 2; ++v) Uc[v] = (double)U[slot_index(g, slot, v, sz, py, px)];
-            const double rho = Uc[0];
+            for (int v = 0; v < D + 2; ++v) Uc[v] = U[slot_index(g, slot, v, sz, py, px)];
+            T rho, u[D], p, Tt;
+            primitives<T, D>(Uc, gm1, rho, u, p, Tt);
             prim[idx] = (float)rho;
 #pragma unroll
-            for (int d = 0; d < D; ++d) prim[(1 + d) * P::PLANE + idx] = (float)(Uc[1 + d] / rho);
-            prim[(F - 1) * P::PLANE + idx] = (float)pressure_d<D>(Uc, gm1);
+            for (int d = 0; d < D; ++d) prim[(1 + d) * P::PLANE + idx] = (float)u[d];
+            prim[(F - 1) * P::PLANE + idx] = (float)p;
         }
         __syncthreads();
         constexpr int TILES = (P::CELLS + 15) / 16;

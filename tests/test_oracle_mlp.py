@@ -56,7 +56,7 @@ def test_embedding_keeps_the_plain_flag(dim):
                     ip = offs.index(tuple(e))
                     im = offs.index(tuple(-x for x in e))
                     fm, f0, fp = phi[:, im], phi[:, centre], phi[:, ip]
-                    flag |= np.abs(fp - fm) / (fp + 2.0 * f0 + fm) > th
+                    flag |= np.abs(fp - fm) > th * (fp + 2.0 * f0 + fm)
             assert np.array_equal(flag, f1)
 
 
