@@ -296,7 +296,7 @@ T* St(amr_ctx* c, int i) { return reinterpret_cast<T*>(c->U[i]); }
 template <typename T>
 int fill_all_levels(amr_ctx* c, T* U, double tfrac) {
     for (int l = 0; l < c->L; ++l) {
-        CK(Kernels<T>::ghost_fill(c->grid, U, l, tfrac, grid_size(c, 8), c->stream, -1), "ghost fill");
+        CK(Kernels<T>::ghost_fill(c->grid, U, l, tfrac, grid_size(c, 16), c->stream, -1), "ghost fill");
         ++c->kernels;
     }
     return AMR_OK;
@@ -321,7 +321,7 @@ int enqueue_step(amr_ctx* c, bool with_cfl, long long* nk) {
         T* dst = St<T>(c, s == 0 ? 1 : (s == 1 ? 2 : 0));
         CK(mark(c->ev[s][0]), "event");
         for (int l = 0; l < c->L; ++l) {
-            CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], grid_size(c, 8), c->stream, -1), "ghost fill");
+            CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], grid_size(c, 16), c->stream, -1), "ghost fill");
             ++k;
         }
         CK(mark(c->ev[s][1]), "event");

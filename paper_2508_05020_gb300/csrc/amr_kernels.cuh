@@ -201,6 +201,33 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
     for (int v = 0; v < NF; ++v) F[v] = T(0.5) * (FR[v] + FL[v]) - hS * (UR[v] - UL[v]);
 }
 
+// Metadata of one patch staged in shared memory by the CTA that serves it:
+// level, coordinates, its 27-entry neighbour table and its parent's.
+struct PatchMeta {
+    int slot, lev, par;
+    int c[3];
+    int nbr[NBR];
+    int pnbr[NBR];
+};
+
+__device__ __forceinline__ void load_meta(const Grid& g, int slot, PatchMeta& m) {
+    const int t = threadIdx.x;
+    if (t == 0) {
+        m.slot = slot;
+        m.lev = g.level[slot];
+        m.par = g.parent[slot];
+        m.c[0] = g.coord[slot * 3];
+        m.c[1] = g.coord[slot * 3 + 1];
+        m.c[2] = g.coord[slot * 3 + 2];
+    }
+    if (t < NBR) m.nbr[t] = g.nbr[slot * NBR + t];
+    if (t >= 32 && t < 32 + NBR) {
+        const int par = g.parent[slot];
+        m.pnbr[t - 32] = par >= 0 ? g.nbr[par * NBR + t - 32] : -1;
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Limited-linear prolongation of the conserved variables at fine local cell l
 // of a patch (slot, level lev, coords c): coarse cell C = G // 2 in the
@@ -210,9 +237,10 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
 // child has rho <= 0 or p <= 0.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
-__device__ void prolong_cell(const Grid& g, const T* U, int slot, const int* c, const int* l, T* out) {
+__device__ void prolong_cell(const Grid& g, const T* U, const PatchMeta& m, const int* l, T* out) {
     constexpr int NV = D + 2;
-    const int par = g.parent[slot];
+    const int* c = m.c;
+    const int par = m.par;
     int Lc[3] = {0, 0, 0}, s[3] = {0, 0, 0}, oc[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -223,7 +251,7 @@ __device__ void prolong_cell(const Grid& g, const T* U, int slot, const int* c, 
         oc[d] = floordiv(Gc, N) - PC;
         Lc[d] = Gc - (PC + oc[d]) * N;
     }
-    const int Q = par >= 0 ? g.nbr[par * NBR + (oc[2] + 1) * 9 + (oc[1] + 1) * 3 + (oc[0] + 1)] : -1;
+    const int Q = par >= 0 ? m.pnbr[(oc[2] + 1) * 9 + (oc[1] + 1) * 3 + (oc[0] + 1)] : -1;
     if (Q < 0) {
         atomicOr(&g.time->err, ERR_MESH);
 #pragma unroll
@@ -278,8 +306,9 @@ __device__ void prolong_cell(const Grid& g, const T* U, int slot, const int* c, 
 
 // value of an in-domain cell of a patch: interior, same-level neighbour or prolongation
 template <typename T, int D, int N>
-__device__ void in_domain_value(const Grid& g, const T* U, int slot, const int* c, const int* l, T* out) {
+__device__ void in_domain_value(const Grid& g, const T* U, const PatchMeta& m, const int* l, T* out) {
     constexpr int NV = D + 2;
+    const int slot = m.slot;
     int o[3] = {0, 0, 0};
     bool inside = true;
 #pragma unroll
@@ -293,14 +322,14 @@ __device__ void in_domain_value(const Grid& g, const T* U, int slot, const int* 
             out[v] = U[slot_index(g, slot, v, sc<D>(2, l[2]), sc<D>(1, l[1]), sc<D>(0, l[0]))];
         return;
     }
-    const int nb = g.nbr[slot * NBR + (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1)];
+    const int nb = m.nbr[(o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1)];
     if (nb >= 0) {
         const int sx = sc<D>(0, l[0] - o[0] * N), sy = sc<D>(1, l[1] - o[1] * N), sz = sc<D>(2, l[2] - o[2] * N);
 #pragma unroll
         for (int v = 0; v < NV; ++v) out[v] = U[slot_index(g, nb, v, sz, sy, sx)];
         return;
     }
-    prolong_cell<T, D, N>(g, U, slot, c, l, out);
+    prolong_cell<T, D, N>(g, U, m, l, out);
 }
 
 // post- or pre-shock conserved state of the double Mach reflection
@@ -312,11 +341,11 @@ __device__ __forceinline__ void dmr_state(const Grid& g, bool behind, T* out);
 // boundary dimension by dimension in the order x, y, z), then the in-domain
 // value of the mapped cell.
 template <typename T, int D, int N>
-__device__ void ghost_value(const Grid& g, const T* U, int slot, int* l, double t, T* out,
+__device__ void ghost_value(const Grid& g, const T* U, const PatchMeta& m, int* l, double t, T* out,
                             const double* pre, const double* post) {
     constexpr int NV = D + 2;
-    const int lev = g.level[slot];
-    int c[3] = {g.coord[slot * 3 + 0], g.coord[slot * 3 + 1], g.coord[slot * 3 + 2]};
+    const int lev = m.lev;
+    const int* c = m.c;
     int neg = 0;
     for (int it = 0; it < D; ++it) {
         int dd = -1, side = 0;
@@ -371,37 +400,45 @@ __device__ void ghost_value(const Grid& g, const T* U, int slot, int* l, double 
         }
         l[dd] = Gs - c[dd] * N;
     }
-    in_domain_value<T, D, N>(g, U, slot, c, l, out);
+    in_domain_value<T, D, N>(g, U, m, l, out);
 #pragma unroll
     for (int d = 0; d < D; ++d)
         if ((neg >> d) & 1) out[1 + d] = -out[1 + d];
 }
 
 // ---------------------------------------------------------------------------
-// K1-K3: ghost fill of every patch of one level (one thread per ghost cell)
+// K1-K3: ghost fill of every patch of one level. A work item is a patch and a
+// run of 512 of its ghost cells (slot order); the CTA stages the patch's
+// metadata in shared memory once per item.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
                                                double4 pre, double4 post) {
     constexpr int NV = D + 2;
+    __shared__ PatchMeta m;
     const int lo = g.level_off[level], hi = g.level_off[level + 1];
     const int npatch = one_slot >= 0 ? 1 : hi - lo;
-    const long long total = (long long)npatch * g.n_ghost;
     const double t = g.time->t + tfrac * g.time->dt;
     const double pr[4] = {pre.x, pre.y, pre.z, pre.w};
     const double po[4] = {post.x, post.y, post.z, post.w};
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
-         it += (long long)gridDim.x * blockDim.x) {
-        const int pi = (int)(it / g.n_ghost);
-        const int gi = (int)(it - (long long)pi * g.n_ghost);
+    constexpr int CHUNK = 512;                           // ghost cells per work item
+    const int nchunk = (g.n_ghost + CHUNK - 1) / CHUNK;
+    for (int item = blockIdx.x; item < npatch * nchunk; item += gridDim.x) {
+        const int pi = item / nchunk;
+        const int g0 = (item - pi * nchunk) * CHUNK;
+        const int g1 = min(g0 + CHUNK, g.n_ghost);
         const int slot = one_slot >= 0 ? one_slot : g.all_list[lo + pi];
-        const int pk = g.ghost_tab[gi];
-        int l[3] = {(pk & 1023) - G, ((pk >> 10) & 1023) - G, ((pk >> 20) & 1023) - G};
-        const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
-        T val[NV];
-        ghost_value<T, D, N>(g, U, slot, l, t, val, pr, po);
+        load_meta(g, slot, m);
+        for (int gi = g0 + threadIdx.x; gi < g1; gi += blockDim.x) {
+            const int pk = g.ghost_tab[gi];
+            int l[3] = {(pk & 1023) - G, ((pk >> 10) & 1023) - G, ((pk >> 20) & 1023) - G};
+            const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
+            T val[NV];
+            ghost_value<T, D, N>(g, U, m, l, t, val, pr, po);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) U[slot_index(g, slot, v, sz, sy, sx)] = val[v];
+            for (int v = 0; v < NV; ++v) U[slot_index(g, slot, v, sz, sy, sx)] = val[v];
+        }
+        __syncthreads();
     }
 }
 
@@ -934,23 +971,24 @@ __global__ void __launch_bounds__(256) k_init_ic(Grid g, T* U, const int* list, 
     }
 }
 
-// K12: interiors of new patches by prolongation from their parents
+// K12: interiors of new patches by prolongation from their parents (one CTA per patch)
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_prolong_new(Grid g, T* U, const int* list, int n) {
     constexpr int NV = D + 2;
     constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < (long long)n * NC;
-         it += (long long)gridDim.x * blockDim.x) {
-        const int pi = (int)(it / NC);
-        const int ci = (int)(it - (long long)pi * NC);
+    __shared__ PatchMeta m;
+    for (int pi = blockIdx.x; pi < n; pi += gridDim.x) {
         const int slot = list[pi];
-        int l[3] = {ci % N, D >= 2 ? (ci / N) % N : 0, D == 3 ? ci / (N * N) : 0};
-        const int c[3] = {g.coord[slot * 3], g.coord[slot * 3 + 1], g.coord[slot * 3 + 2]};
-        T val[NV];
-        prolong_cell<T, D, N>(g, U, slot, c, l, val);
-        const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
+        load_meta(g, slot, m);
+        for (int ci = threadIdx.x; ci < NC; ci += blockDim.x) {
+            int l[3] = {ci % N, D >= 2 ? (ci / N) % N : 0, D == 3 ? ci / (N * N) : 0};
+            T val[NV];
+            prolong_cell<T, D, N>(g, U, m, l, val);
+            const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) U[slot_index(g, slot, v, sz, sy, sx)] = val[v];
+            for (int v = 0; v < NV; ++v) U[slot_index(g, slot, v, sz, sy, sx)] = val[v];
+        }
+        __syncthreads();
     }
 }
 

@@ -99,7 +99,7 @@ cudaError_t Kernels<T>::init_ic(const Grid& g, T* U, const int* list, int n, cud
 template <typename T>
 cudaError_t Kernels<T>::prolong_new(const Grid& g, T* U, const int* list, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int grid = (int)(((long long)n * 4096 + 255) / 256 < 65536 ? ((long long)n * 4096 + 255) / 256 : 65536);
+    const int grid = n < 65536 ? n : 65536;
     AMR_DISPATCH(g, (k_prolong_new<T, D, N><<<grid, 256, 0, s>>>(g, U, list, n)));
     return cudaGetLastError();
 }

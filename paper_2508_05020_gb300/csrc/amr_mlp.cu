@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256) k_infer(const float* __restrict__ X, long
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MlpSmem<D>& s = *reinterpret_cast<MlpSmem<D>*>(smem_raw);
     constexpr int K = MlpSmem<D>::K;
+    (void)K;
     mlp_stage_weights<D>(s, w);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -72,7 +73,13 @@ __global__ void __launch_bounds__(256) k_infer(const float* __restrict__ X, long
         const long r0 = tile * 16 + g, r1 = r0 + 8;
         const float* x0 = X + (r0 < n ? r0 : n - 1) * K;
         const float* x1 = X + (r1 < n ? r1 : n - 1) * K;
-        auto feat = [&](int h, int k) -> float { return k < K ? (h ? x1[k] : x0[k]) : 0.f; };
+        constexpr int F = D + 2, NP = mlp_npts(D), PTS = mlp_pts(D);
+        auto feat = [&](int h, int kp) -> float {
+            const int f = kp / PTS, j = kp - f * PTS;
+            if (j >= NP) return 0.f;
+            const int k = j * F + f;
+            return h ? x1[k] : x0[k];
+        };
         const float2 zz = mlp_tile<D>(s, feat);
         if ((lane & 3) == 0) {
             if (r0 < n) z[r0] = zz.x;

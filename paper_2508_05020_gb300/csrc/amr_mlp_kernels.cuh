@@ -56,34 +56,6 @@ cudaError_t Kernels<T>::harvest(const Grid& g, const T* U, int* n_out, double* s
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// K10: learned indicator on the band [-1, N]^d of every leaf patch. One work
-// item is a leaf patch (1D/2D) or a slab of DZ band planes of it (3D). The
-// primitives (rho, u.., p) of the slab and its +-2 halo are staged in shared
-// memory in FP32; each warp takes 16 band cells at a time and builds the
-// normalised 5^d stencil features straight into the BF16 A fragments of the
-// tensor-core MLP (mlp_tile). A patch is flagged if any in-domain band cell
-// has a positive logit; slabs of an already flagged patch are skipped.
-// With `stats`, the plain sensor of every band cell is evaluated too (FP64,
-// as in k_flag_plain) and the agreement counts TP, FP, FN, TN accumulated.
-// ---------------------------------------------------------------------------
-template <int D, int N> struct MlpBand {
-    static constexpr int B = N + 2;                       // band cells per dimension
-    static constexpr int S = N + 2 * G;                   // slot cells per dimension
-    static constexpr int DZ = D == 3 ? 2 : 1;
-    static constexpr int NSLAB = D == 3 ? B / DZ : 1;
-    static constexpr int PX = S, PY = D >= 2 ? S : 1, PZ = D == 3 ? DZ + 4 : 1;
-    static constexpr int PLANE = PX * PY * PZ;            // floats per primitive field
-    static constexpr int CELLS = D == 1 ? B : (D == 2 ? B * B : B * B * DZ);
-    static constexpr int F = D + 2;
-};
-
-template <int D, int N>
-constexpr size_t mlp_flag_smem() {
-    using P = MlpBand<D, N>;
-    return (sizeof(MlpSmem<D>) + 15) / 16 * 16 + sizeof(int) * mlp_kpad(D) + sizeof(float) * P::F * P::PLANE + 16;
-}
-
 template <typename T, int D, int N>
 __device__ bool plain_flag_cell(const Grid& g, const T* U, int slot, const int* l) {
     constexpr int NV = D + 2;
@@ -111,30 +83,75 @@ __device__ bool plain_flag_cell(const Grid& g, const T* U, int slot, const int* 
     return f;
 }
 
-template <typename T, int D, int N>
-__global__ void __launch_bounds__(256) k_flag_mlp(Grid g, const T* __restrict__ U, const float* __restrict__ w,
-                                                  int* anyflag, unsigned long long* stats) {
+// ---------------------------------------------------------------------------
+// K10: learned indicator on the band [-1, N]^d of every leaf patch. One work
+// item is a leaf patch (1D/2D) or a slab of DZ band planes of it (3D). The
+// primitives (rho, u.., p) of the slab and its +-2 halo are staged in shared
+// memory in FP32. Band cells are taken 128 at a time (a GEMM tile, 16 rows per
+// warp): all threads write the centre-normalised 5^d stencil features of the
+// tile into a double-buffered 64-wide K chunk in shared memory (BF16, padded
+// rows), and each warp accumulates layer 1 on the tensor cores from that chunk
+// (ldmatrix + mma.sync). Layer 2 and the output follow in registers. A patch is
+// flagged if any in-domain band cell has a positive logit; items of an already
+// flagged patch are skipped. With `stats` the plain sensor of every band cell
+// is evaluated too and the agreement counts TP, FP, FN, TN accumulated.
+// ---------------------------------------------------------------------------
+template <int D, int N> struct MlpBand {
+    static constexpr int B = N + 2;                       // band cells per dimension
+    static constexpr int S = N + 2 * G;                   // slot cells per dimension
+    static constexpr int DZ = D == 3 ? 3 : 1;
+    static constexpr int NSLAB = D == 3 ? B / DZ : 1;
+    static constexpr int PX = S, PY = D >= 2 ? S : 1, PZ = D == 3 ? DZ + 4 : 1;
+    static constexpr int PLANE = PX * PY * PZ;            // floats per primitive field
+    static constexpr int CELLS = D == 1 ? B : (D == 2 ? B * B : B * B * DZ);
+    static constexpr int F = D + 2;
+    static constexpr int NTH = 512;                       // 16 warps
+    static constexpr int M = 256;                         // rows of a GEMM tile (16 per warp)
+    static constexpr int KC = 32;                         // K chunk
+    static constexpr int AP = KC + 8;                     // A row pitch (bf16): 80 B, conflict-free ldmatrix
+    static constexpr int TILES = (CELLS + M - 1) / M;
+};
+
+template <int D, int N>
+constexpr size_t mlp_flag_smem() {
     using P = MlpBand<D, N>;
-    constexpr int K = mlp_kin(D), KP = mlp_kpad(D), F = P::F;
+    return (sizeof(MlpSmem<D>) + 15) / 16 * 16 + sizeof(int) * mlp_pts(D) + sizeof(float) * P::F * P::PLANE +
+           2 * sizeof(__nv_bfloat16) * P::M * P::AP + sizeof(int) * 8 * P::M + 64;
+}
+
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(512, 1) k_flag_mlp(Grid g, const T* __restrict__ U, const float* __restrict__ w,
+                                                     int* anyflag, unsigned long long* stats) {
+    using P = MlpBand<D, N>;
+    constexpr int K = mlp_kin(D), KP = mlp_kpad(D), F = P::F, M = P::M, KC = P::KC, AP = P::AP;
+    constexpr int NCHUNK = (KP + KC - 1) / KC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MlpSmem<D>& ms = *reinterpret_cast<MlpSmem<D>*>(smem_raw);
-    int* koff = reinterpret_cast<int*>(smem_raw + (sizeof(MlpSmem<D>) + 15) / 16 * 16);
-    float* prim = reinterpret_cast<float*>(koff + KP);
+    constexpr int NP = mlp_npts(D), PTS = mlp_pts(D);
+    int* krel = reinterpret_cast<int*>(smem_raw + (sizeof(MlpSmem<D>) + 15) / 16 * 16);
+    float* prim = reinterpret_cast<float*>(krel + PTS);
+    __nv_bfloat16* abuf = reinterpret_cast<__nv_bfloat16*>(
+        (reinterpret_cast<uintptr_t>(prim + F * P::PLANE) + 15) & ~uintptr_t(15));
+    int* rcen = reinterpret_cast<int*>(abuf + 2 * M * AP);
+    float* rsc = reinterpret_cast<float*>(rcen + M);      // [3][M]: 1/rho0, 1/c0, 1/p0
+    int* rval = reinterpret_cast<int*>(rsc + 3 * M);
+    int* rlc = rval + M;                                  // [3][M]: local cell
     __shared__ int skip;
     mlp_stage_weights<D>(ms, w);
-    // feature k -> (field, offset of the stencil point relative to the centre cell)
-    for (int k = threadIdx.x; k < KP; k += blockDim.x) {
-        if (k >= K) { koff[k] = -1; continue; }
-        const int j = k / F, f = k - j * F;
+    (void)K;
+    // stencil point j -> offset of its cell from the centre cell (padding points: 0)
+    for (int j = threadIdx.x; j < PTS; j += blockDim.x) {
         const int ox = j % 5 - 2, oy = D >= 2 ? (j / 5) % 5 - 2 : 0, oz = D == 3 ? j / 25 - 2 : 0;
-        const int kind = f == 0 ? 0 : (f == F - 1 ? 2 : 1);                   // rho, velocity, p
-        koff[k] = (kind << 28) | (f * P::PLANE + (oz * P::PY + oy) * P::PX + ox + (1 << 20));
+        krel[j] = j < NP ? (oz * P::PY + oy) * P::PX + ox : 0;
     }
     __syncthreads();
     const T gm1 = T(g.gamma) - T(1);
     const int npatch = g.counts[1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2;
+    // feature-fill role: lane = row within a 32-row group, the warp picks the
+    // group and the half of the K chunk
+    const int frow = (warp & 7) * 32 + lane, fhalf = warp >> 3;
     for (int item = blockIdx.x; item < npatch * P::NSLAB; item += gridDim.x) {
         const int pi = item / P::NSLAB, slab = item - pi * P::NSLAB;
         const int slot = g.leaf_list[pi];
@@ -159,44 +176,73 @@ __global__ void __launch_bounds__(256) k_flag_mlp(Grid g, const T* __restrict__ 
             prim[(F - 1) * P::PLANE + idx] = (float)p;
         }
         __syncthreads();
-        constexpr int TILES = (P::CELLS + 15) / 16;
-        for (int tile = warp; tile < TILES; tile += nw) {
-            int cen[2], lc[2][3];
-            bool valid[2];
-            float ir[2], ic[2], ip[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = tile * 16 + gq + 8 * h;
-                valid[h] = r < P::CELLS;
-                const int rr = valid[h] ? r : P::CELLS - 1;
+        for (int tile = 0; tile < P::TILES; ++tile) {
+            // per-row data of the tile
+            if (threadIdx.x < M) {
+                const int r = tile * M + threadIdx.x;
+                const bool inb = r < P::CELLS;
+                const int rr = inb ? r : P::CELLS - 1;
                 const int bx = rr % P::B, by = D >= 2 ? (rr / P::B) % P::B : 0, bz = D == 3 ? rr / (P::B * P::B) : 0;
-                lc[h][0] = bx - 1;
-                lc[h][1] = D >= 2 ? by - 1 : 0;
-                lc[h][2] = D == 3 ? zb0 + bz : 0;
-                const int qx = lc[h][0] + G, qy = D >= 2 ? lc[h][1] + G : 0, qz = D == 3 ? bz + 2 : 0;
-                cen[h] = (qz * P::PY + qy) * P::PX + qx;
-                const float r0 = prim[cen[h]], p0 = prim[(F - 1) * P::PLANE + cen[h]];
-                ir[h] = 1.f / r0;
-                ip[h] = 1.f / p0;
-                ic[h] = rsqrtf((float)g.gamma * p0 * ir[h]);
-                bool indom = true;
+                const int l0 = bx - 1, l1 = D >= 2 ? by - 1 : 0, l2 = D == 3 ? zb0 + bz : 0;
+                const int qx = l0 + G, qy = D >= 2 ? l1 + G : 0, qz = D == 3 ? bz + 2 : 0;
+                const int cen = (qz * P::PY + qy) * P::PX + qx;
+                const float r0 = prim[cen], p0 = prim[(F - 1) * P::PLANE + cen];
+                const float ir = 1.f / r0;
+                bool indom = inb;
+                const int lcv[3] = {l0, l1, l2};
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
                     if (g.periodic[d]) continue;
-                    const int Gd = c[d] * N + lc[h][d];
+                    const int Gd = c[d] * N + lcv[d];
                     indom = indom && Gd >= 0 && Gd < g.ext[lev][d] * N;
                 }
-                valid[h] = valid[h] && indom;
+                rcen[threadIdx.x] = cen;
+                rsc[threadIdx.x] = ir;
+                rsc[M + threadIdx.x] = rsqrtf((float)g.gamma * p0 * ir);
+                rsc[2 * M + threadIdx.x] = 1.f / p0;
+                rval[threadIdx.x] = indom ? 1 : 0;
+                rlc[threadIdx.x] = l0;
+                rlc[M + threadIdx.x] = l1;
+                rlc[2 * M + threadIdx.x] = l2;
             }
-            auto feat = [&](int h, int k) -> float {
-                const int o = koff[k];
-                if (o < 0) return 0.f;
-                const int kind = o >> 28;
-                const float v = prim[cen[h] + (o & 0x0FFFFFFF) - (1 << 20)];
-                return kind == 0 ? v * ir[h] - 1.f : (kind == 2 ? v * ip[h] - 1.f : v * ic[h]);
+            __syncthreads();
+            const int mcen = rcen[frow];
+            const float sc0 = rsc[frow], sc1 = rsc[M + frow], sc2 = rsc[2 * M + frow];
+            // 16 features of chunk `cc` for this thread's row into buffer `b`: one
+            // field f and 16 consecutive stencil points (field-major K)
+            auto fill = [&](int cc, int b) {
+                __nv_bfloat16* dst = abuf + (size_t)b * M * AP + frow * AP + fhalf * 16;
+                const int k0 = cc * KC + fhalf * 16;
+                if (k0 >= KP) return;                    // past the padded K (1D): never multiplied
+                const int f = k0 / PTS, j0 = k0 - f * PTS;
+                const float sc = f == 0 ? sc0 : (f == F - 1 ? sc2 : sc1);
+                const float sh = (f == 0 || f == F - 1) ? -1.f : 0.f;
+                const float* pf = prim + f * P::PLANE + mcen;
+                uint32_t wv[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float x0 = pf[krel[j0 + 2 * e]], x1 = pf[krel[j0 + 2 * e + 1]];
+                    wv[e] = pack_bf16(x0 * sc + sh, x1 * sc + sh);
+                }
+                *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                *reinterpret_cast<uint4*>(dst + 8) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
             };
-            const float2 z = mlp_tile<D>(ms, feat);
-            const bool m0 = valid[0] && z.x > 0.f, m1 = valid[1] && z.y > 0.f;
+            float acc[8][4];
+#pragma unroll
+            for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+            fill(0, 0);
+            __syncthreads();
+            for (int cc = 0; cc < NCHUNK; ++cc) {
+                if (cc + 1 < NCHUNK) fill(cc + 1, (cc + 1) & 1);
+                const __nv_bfloat16* arows = abuf + (size_t)(cc & 1) * M * AP + warp * 16 * AP;
+#pragma unroll
+                for (int kk = 0; kk < KC; kk += 16)
+                    if (cc * KC + kk < KP) mma_l1_step<D>(ms, arows, AP, kk, cc * KC + kk, acc);
+                __syncthreads();
+            }
+            const float2 z = mlp_epilogue<D>(ms, acc);
+            const int row0 = warp * 16 + gq, row1 = row0 + 8;
+            const bool m0 = rval[row0] && z.x > 0.f, m1 = rval[row1] && z.y > 0.f;
             const bool any = __any_sync(0xffffffffu, m0 || m1);
             if (any && lane == 0) atomicOr(&anyflag[slot], 1);
             if (stats) {
@@ -204,8 +250,10 @@ __global__ void __launch_bounds__(256) k_flag_mlp(Grid g, const T* __restrict__ 
                 if ((lane & 3) == 0) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        if (!valid[h]) continue;
-                        const bool pf = plain_flag_cell<T, D, N>(g, U, slot, lc[h]);
+                        const int row = h ? row1 : row0;
+                        if (!rval[row]) continue;
+                        const int lc[3] = {rlc[row], rlc[M + row], rlc[2 * M + row]};
+                        const bool pf = plain_flag_cell<T, D, N>(g, U, slot, lc);
                         const bool lf = h ? m1 : m0;
                         cnt[pf ? (lf ? 0 : 2) : (lf ? 1 : 3)] += 1;
                     }
@@ -218,6 +266,12 @@ __global__ void __launch_bounds__(256) k_flag_mlp(Grid g, const T* __restrict__ 
                     if (lane == 0 && v) atomicAdd(&stats[q], v);
                 }
             }
+            __syncthreads();
+            if (!stats) {                                    // the rest of a flagged patch is skipped
+                if (threadIdx.x == 0) skip = *((volatile int*)&anyflag[slot]);
+                __syncthreads();
+                if (skip) break;
+            }
         }
         __syncthreads();
     }
@@ -227,7 +281,7 @@ template <typename T, int D, int N>
 static cudaError_t flag_mlp_launch(const Grid& g, const T* U, const float* w, int* anyflag,
                                    unsigned long long* stats, int grid, cudaStream_t s) {
     constexpr size_t smem = mlp_flag_smem<D, N>();
-    k_flag_mlp<T, D, N><<<grid, 256, smem, s>>>(g, U, w, anyflag, stats);
+    k_flag_mlp<T, D, N><<<grid, MlpBand<D, N>::NTH, smem, s>>>(g, U, w, anyflag, stats);
     return cudaGetLastError();
 }
 
