@@ -398,6 +398,10 @@ int read_time(amr_ctx* c) {
         c->broken = true;
         return fail(c, AMR_ERR_MESH, "prolongation source missing (R2 violated)");
     }
+    if (c->time_h->err & ERR_TIMEOUT) {
+        c->broken = true;
+        return fail(c, AMR_ERR_TIMEOUT, "a bounded wait on the tensor cores gave up");
+    }
     return AMR_OK;
 }
 

@@ -20,6 +20,7 @@ constexpr int NBR = 27;         // neighbour table entries per slot ({-1,0,1}^3)
 // device error bits (DevTime::err)
 constexpr int ERR_NONFINITE = 1;
 constexpr int ERR_MESH = 2;
+constexpr int ERR_TIMEOUT = 4;        // a bounded device wait gave up
 
 // Per-step scalars kept on the device so that a captured step needs no host input.
 struct DevTime {

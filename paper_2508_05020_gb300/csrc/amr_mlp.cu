@@ -5,6 +5,7 @@
 // every reduction is a fixed-order loop, no atomics.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -13,6 +14,7 @@
 #include "amr.h"
 #include "amr_internal.h"
 #include "amr_mlp_core.cuh"
+#include "amr_mlp_tc.cuh"
 
 namespace amr {
 int mlp_k(int dim) { return mlp_kin(dim); }
@@ -56,36 +58,64 @@ __global__ void k_features(int D, double gamma, const double* __restrict__ smp, 
     }
 }
 
-// standalone inference on feature rows (n x K floats)
+// standalone inference on feature rows (n x K floats, ABI feature order) on
+// the tcgen05 core: 128-row tiles, features copied (BF16) into the canonical
+// field-major chunk layout. Rows a timed-out CTA did not reach stay NaN.
+template <int D> struct InferLayout {
+    static constexpr size_t ABUF = (sizeof(MlpTcSmem<D>) + 127) / 128 * 128;
+    static constexpr size_t HBUF = ABUF + 2 * sizeof(__nv_bfloat16) * TC_M * TC_KC;
+    static constexpr size_t SLOTS = HBUF + sizeof(__nv_bfloat16) * TC_M * MLP_H;
+    static constexpr size_t TOTAL = SLOTS + 4 * sizeof(uint64_t) + 128;
+};
+
 template <int D>
-__global__ void __launch_bounds__(256) k_infer(const float* __restrict__ X, long n, const float* __restrict__ w,
-                                               float* __restrict__ z) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MlpSmem<D>& s = *reinterpret_cast<MlpSmem<D>*>(smem_raw);
-    constexpr int K = MlpSmem<D>::K;
-    (void)K;
-    mlp_stage_weights<D>(s, w);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int g = lane >> 2;
-    const long tiles = (n + 15) / 16;
-    for (long tile = (long)blockIdx.x * nw + warp; tile < tiles; tile += (long)gridDim.x * nw) {
-        const long r0 = tile * 16 + g, r1 = r0 + 8;
-        const float* x0 = X + (r0 < n ? r0 : n - 1) * K;
-        const float* x1 = X + (r1 < n ? r1 : n - 1) * K;
-        constexpr int F = D + 2, NP = mlp_npts(D), PTS = mlp_pts(D);
-        auto feat = [&](int h, int kp) -> float {
-            const int f = kp / PTS, j = kp - f * PTS;
-            if (j >= NP) return 0.f;
-            const int k = j * F + f;
-            return h ? x1[k] : x0[k];
+__global__ void __launch_bounds__(512, 1) k_infer(const float* __restrict__ X, long n, const float* __restrict__ w,
+                                                  float* __restrict__ z, int* err) {
+    using Lay = InferLayout<D>;
+    constexpr int K = mlp_kin(D), KP = mlp_kpad(D), F = D + 2, NP = mlp_npts(D), PTS = mlp_pts(D);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    MlpTcSmem<D>& s = *reinterpret_cast<MlpTcSmem<D>*>(base);
+    __nv_bfloat16* abuf = reinterpret_cast<__nv_bfloat16*>(base + Lay::ABUF);
+    __nv_bfloat16* hbuf = reinterpret_cast<__nv_bfloat16*>(base + Lay::HBUF);
+    uint64_t* slots = reinterpret_cast<uint64_t*>(base + Lay::SLOTS);
+    mlp_tc_stage_weights<D>(s, w);
+    TcState st;
+    tc_setup(st, slots);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int frow = (warp & 3) * 32 + lane, fslice = warp >> 2;
+    const long tiles = (n + TC_M - 1) / TC_M;
+    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long r = tile * TC_M + frow;
+        const float* x = X + (r < n ? r : n - 1) * K;
+        auto fill = [&](int cc, __nv_bfloat16* dst) {
+            const int k0 = cc * TC_KC + fslice * 16;
+            uint32_t wv[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                float v2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int kp = k0 + 2 * e + h;
+                    const int f = kp / PTS, j = kp - f * PTS;
+                    v2[h] = (kp < KP && j < NP) ? x[j * F + f] : 0.f;
+                }
+                wv[e] = pack_bf16(v2[0], v2[1]);
+            }
+            *reinterpret_cast<uint4*>(dst + canon_off(frow, fslice * 16, TC_KC)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            *reinterpret_cast<uint4*>(dst + canon_off(frow, fslice * 16 + 8, TC_KC)) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
         };
-        const float2 zz = mlp_tile<D>(s, feat);
-        if ((lane & 3) == 0) {
-            if (r0 < n) z[r0] = zz.x;
-            if (r1 < n) z[r1] = zz.y;
+        const float zz = mlp_tile_tc<D>(st, s, abuf, hbuf, fill);
+        if (!__syncthreads_and(st.ok ? 1 : 0)) {
+            if (threadIdx.x == 0) atomicOr(err, 1);
+            break;
+        }
+        if (warp < 4) {
+            const long ro = tile * TC_M + warp * 32 + lane;
+            if (ro < n) z[ro] = zz;
         }
     }
+    tc_teardown(st);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,16 +260,16 @@ int fwd_bwd(int D, const float* X, const int* idx, const float* y, int n, float 
 }
 
 template <int D>
-cudaError_t launch_infer(const float* X, long n, const float* w, float* z, cudaStream_t s) {
-    const size_t smem = sizeof(MlpSmem<D>);
+cudaError_t launch_infer(const float* X, long n, const float* w, float* z, int* err, cudaStream_t s) {
+    const size_t smem = InferLayout<D>::TOTAL;
     cudaError_t e = cudaFuncSetAttribute(k_infer<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long tiles = (n + 15) / 16;
-    const int grid = (int)std::min<long>(tiles / 8 + 1, (long)nsm * 2);
-    k_infer<D><<<grid, 256, smem, s>>>(X, n, w, z);
+    const long tiles = (n + TC_M - 1) / TC_M;
+    const int grid = (int)std::min<long>(tiles, (long)nsm);
+    k_infer<D><<<grid, 512, smem, s>>>(X, n, w, z, err);
     return cudaGetLastError();
 }
 
@@ -275,14 +305,20 @@ int amr_mlp_infer(int dim, const float* X, long n, const float* weights, float* 
     float* dx = dv.get<float>(n * K);
     float* dw = dv.get<float>(nw);
     float* dz = dv.get<float>(n);
-    if (!dx || !dw || !dz) return AMR_ERR_CUDA;
+    int* derr = dv.get<int>(1);
+    if (!dx || !dw || !dz || !derr) return AMR_ERR_CUDA;
     cudaMemcpyAsync(dx, X, n * K * sizeof(float), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dw, weights, nw * sizeof(float), cudaMemcpyHostToDevice, s);
-    cudaError_t e = dim == 1 ? launch_infer<1>(dx, n, dw, dz, s)
-                  : dim == 2 ? launch_infer<2>(dx, n, dw, dz, s) : launch_infer<3>(dx, n, dw, dz, s);
+    cudaMemsetAsync(dz, 0xFF, n * sizeof(float), s);           // NaN until written
+    cudaMemsetAsync(derr, 0, sizeof(int), s);
+    cudaError_t e = dim == 1 ? launch_infer<1>(dx, n, dw, dz, derr, s)
+                  : dim == 2 ? launch_infer<2>(dx, n, dw, dz, derr, s) : launch_infer<3>(dx, n, dw, dz, derr, s);
     if (e != cudaSuccess) return AMR_ERR_CUDA;
+    int herr = 0;
     cudaMemcpyAsync(logits, dz, n * sizeof(float), cudaMemcpyDeviceToHost, s);
-    return cudaStreamSynchronize(s) == cudaSuccess ? AMR_OK : AMR_ERR_CUDA;
+    cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return AMR_ERR_CUDA;
+    return herr ? AMR_ERR_TIMEOUT : AMR_OK;
 }
 
 int amr_mlp_grad(int dim, const float* X, const float* y, long n, float pw, const float* weights, float* grad,

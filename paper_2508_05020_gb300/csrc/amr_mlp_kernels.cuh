@@ -5,6 +5,7 @@
 #pragma once
 #include "amr_launch.cuh"
 #include "amr_mlp_core.cuh"
+#include "amr_mlp_tc.cuh"
 
 namespace amr {
 
@@ -106,53 +107,59 @@ template <int D, int N> struct MlpBand {
     static constexpr int CELLS = D == 1 ? B : (D == 2 ? B * B : B * B * DZ);
     static constexpr int F = D + 2;
     static constexpr int NTH = 512;                       // 16 warps
-    static constexpr int M = 256;                         // rows of a GEMM tile (16 per warp)
-    static constexpr int KC = 32;                         // K chunk
-    static constexpr int AP = KC + 8;                     // A row pitch (bf16): 80 B, conflict-free ldmatrix
+    static constexpr int M = TC_M;                        // rows of a tile (TMEM lanes)
     static constexpr int TILES = (CELLS + M - 1) / M;
 };
 
-template <int D, int N>
-constexpr size_t mlp_flag_smem() {
+template <int D, int N> struct MlpFlagLayout {
     using P = MlpBand<D, N>;
-    return (sizeof(MlpSmem<D>) + 15) / 16 * 16 + sizeof(int) * mlp_pts(D) + sizeof(float) * P::F * P::PLANE +
-           2 * sizeof(__nv_bfloat16) * P::M * P::AP + sizeof(int) * 8 * P::M + 64;
-}
+    static constexpr size_t W = 0;
+    static constexpr size_t KREL = (sizeof(MlpTcSmem<D>) + 127) / 128 * 128;
+    static constexpr size_t PRIM = KREL + sizeof(int) * mlp_pts(D);
+    static constexpr size_t ABUF = (PRIM + sizeof(float) * P::F * P::PLANE + 127) / 128 * 128;
+    static constexpr size_t HBUF = ABUF + 2 * sizeof(__nv_bfloat16) * TC_M * TC_KC;
+    static constexpr size_t ROWS = HBUF + sizeof(__nv_bfloat16) * TC_M * MLP_H;
+    static constexpr size_t SLOTS = ROWS + sizeof(int) * 8 * TC_M;
+    static constexpr size_t TOTAL = SLOTS + 4 * sizeof(uint64_t);
+};
+
+template <int D, int N>
+constexpr size_t mlp_flag_smem() { return MlpFlagLayout<D, N>::TOTAL + 128; }
 
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(512, 1) k_flag_mlp(Grid g, const T* __restrict__ U, const float* __restrict__ w,
                                                      int* anyflag, unsigned long long* stats) {
     using P = MlpBand<D, N>;
-    constexpr int K = mlp_kin(D), KP = mlp_kpad(D), F = P::F, M = P::M, KC = P::KC, AP = P::AP;
-    constexpr int NCHUNK = (KP + KC - 1) / KC;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MlpSmem<D>& ms = *reinterpret_cast<MlpSmem<D>*>(smem_raw);
-    constexpr int NP = mlp_npts(D), PTS = mlp_pts(D);
-    int* krel = reinterpret_cast<int*>(smem_raw + (sizeof(MlpSmem<D>) + 15) / 16 * 16);
-    float* prim = reinterpret_cast<float*>(krel + PTS);
-    __nv_bfloat16* abuf = reinterpret_cast<__nv_bfloat16*>(
-        (reinterpret_cast<uintptr_t>(prim + F * P::PLANE) + 15) & ~uintptr_t(15));
-    int* rcen = reinterpret_cast<int*>(abuf + 2 * M * AP);
+    using Lay = MlpFlagLayout<D, N>;
+    constexpr int F = P::F, M = P::M, NP = mlp_npts(D), PTS = mlp_pts(D), KP = mlp_kpad(D);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    MlpTcSmem<D>& ms = *reinterpret_cast<MlpTcSmem<D>*>(base + Lay::W);
+    int* krel = reinterpret_cast<int*>(base + Lay::KREL);
+    float* prim = reinterpret_cast<float*>(base + Lay::PRIM);
+    __nv_bfloat16* abuf = reinterpret_cast<__nv_bfloat16*>(base + Lay::ABUF);
+    __nv_bfloat16* hbuf = reinterpret_cast<__nv_bfloat16*>(base + Lay::HBUF);
+    int* rcen = reinterpret_cast<int*>(base + Lay::ROWS);
     float* rsc = reinterpret_cast<float*>(rcen + M);      // [3][M]: 1/rho0, 1/c0, 1/p0
     int* rval = reinterpret_cast<int*>(rsc + 3 * M);
     int* rlc = rval + M;                                  // [3][M]: local cell
+    uint64_t* slots = reinterpret_cast<uint64_t*>(base + Lay::SLOTS);
     __shared__ int skip;
-    mlp_stage_weights<D>(ms, w);
-    (void)K;
+    mlp_tc_stage_weights<D>(ms, w);
     // stencil point j -> offset of its cell from the centre cell (padding points: 0)
     for (int j = threadIdx.x; j < PTS; j += blockDim.x) {
         const int ox = j % 5 - 2, oy = D >= 2 ? (j / 5) % 5 - 2 : 0, oz = D == 3 ? j / 25 - 2 : 0;
         krel[j] = j < NP ? (oz * P::PY + oy) * P::PX + ox : 0;
     }
-    __syncthreads();
+    TcState st;
+    tc_setup(st, slots);                                   // includes a CTA barrier
     const T gm1 = T(g.gamma) - T(1);
     const int npatch = g.counts[1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gq = lane >> 2;
-    // feature-fill role: lane = row within a 32-row group, the warp picks the
-    // group and the half of the K chunk
-    const int frow = (warp & 7) * 32 + lane, fhalf = warp >> 3;
-    for (int item = blockIdx.x; item < npatch * P::NSLAB; item += gridDim.x) {
+    // feature-fill role: row of the tile and a 16-wide K slice of the chunk
+    const int frow = (warp & 3) * 32 + lane, fslice = warp >> 2;
+    bool alive = true;
+    for (int item = blockIdx.x; item < npatch * P::NSLAB && alive; item += gridDim.x) {
         const int pi = item / P::NSLAB, slab = item - pi * P::NSLAB;
         const int slot = g.leaf_list[pi];
         if (threadIdx.x == 0) skip = (!stats && *((volatile int*)&anyflag[slot])) ? 1 : 0;
@@ -177,8 +184,7 @@ __global__ void __launch_bounds__(512, 1) k_flag_mlp(Grid g, const T* __restrict
         }
         __syncthreads();
         for (int tile = 0; tile < P::TILES; ++tile) {
-            // per-row data of the tile
-            if (threadIdx.x < M) {
+            if (threadIdx.x < M) {                         // per-row data of the tile
                 const int r = tile * M + threadIdx.x;
                 const bool inb = r < P::CELLS;
                 const int rr = inb ? r : P::CELLS - 1;
@@ -208,62 +214,51 @@ __global__ void __launch_bounds__(512, 1) k_flag_mlp(Grid g, const T* __restrict
             __syncthreads();
             const int mcen = rcen[frow];
             const float sc0 = rsc[frow], sc1 = rsc[M + frow], sc2 = rsc[2 * M + frow];
-            // 16 features of chunk `cc` for this thread's row into buffer `b`: one
-            // field f and 16 consecutive stencil points (field-major K)
-            auto fill = [&](int cc, int b) {
-                __nv_bfloat16* dst = abuf + (size_t)b * M * AP + frow * AP + fhalf * 16;
-                const int k0 = cc * KC + fhalf * 16;
-                if (k0 >= KP) return;                    // past the padded K (1D): never multiplied
-                const int f = k0 / PTS, j0 = k0 - f * PTS;
-                const float sc = f == 0 ? sc0 : (f == F - 1 ? sc2 : sc1);
-                const float sh = (f == 0 || f == F - 1) ? -1.f : 0.f;
-                const float* pf = prim + f * P::PLANE + mcen;
+            // 16 features (one field, 16 consecutive stencil points) of chunk cc
+            auto fill = [&](int cc, __nv_bfloat16* dst) {
+                const int k0 = cc * TC_KC + fslice * 16;
                 uint32_t wv[8];
+                if (k0 < KP) {
+                    const int f = k0 / PTS, j0 = k0 - f * PTS;
+                    const float sc = f == 0 ? sc0 : (f == F - 1 ? sc2 : sc1);
+                    const float sh = (f == 0 || f == F - 1) ? -1.f : 0.f;
+                    const float* pf = prim + f * P::PLANE + mcen;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const float x0 = pf[krel[j0 + 2 * e]], x1 = pf[krel[j0 + 2 * e + 1]];
-                    wv[e] = pack_bf16(x0 * sc + sh, x1 * sc + sh);
+                    for (int e = 0; e < 8; ++e) {
+                        const float x0 = pf[krel[j0 + 2 * e]], x1 = pf[krel[j0 + 2 * e + 1]];
+                        wv[e] = pack_bf16(x0 * sc + sh, x1 * sc + sh);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) wv[e] = 0u;
                 }
-                *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-                *reinterpret_cast<uint4*>(dst + 8) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+                *reinterpret_cast<uint4*>(dst + canon_off(frow, fslice * 16, TC_KC)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                *reinterpret_cast<uint4*>(dst + canon_off(frow, fslice * 16 + 8, TC_KC)) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
             };
-            float acc[8][4];
-#pragma unroll
-            for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-            fill(0, 0);
-            __syncthreads();
-            for (int cc = 0; cc < NCHUNK; ++cc) {
-                if (cc + 1 < NCHUNK) fill(cc + 1, (cc + 1) & 1);
-                const __nv_bfloat16* arows = abuf + (size_t)(cc & 1) * M * AP + warp * 16 * AP;
-#pragma unroll
-                for (int kk = 0; kk < KC; kk += 16)
-                    if (cc * KC + kk < KP) mma_l1_step<D>(ms, arows, AP, kk, cc * KC + kk, acc);
-                __syncthreads();
+            const float z = mlp_tile_tc<D>(st, ms, abuf, hbuf, fill);
+            if (!__syncthreads_and(st.ok ? 1 : 0)) {       // a bounded wait gave up somewhere
+                if (threadIdx.x == 0) atomicOr(&g.time->err, ERR_TIMEOUT);
+                alive = false;
+                break;
             }
-            const float2 z = mlp_epilogue<D>(ms, acc);
-            const int row0 = warp * 16 + gq, row1 = row0 + 8;
-            const bool m0 = rval[row0] && z.x > 0.f, m1 = rval[row1] && z.y > 0.f;
-            const bool any = __any_sync(0xffffffffu, m0 || m1);
-            if (any && lane == 0) atomicOr(&anyflag[slot], 1);
-            if (stats) {
-                unsigned long long cnt[4] = {0, 0, 0, 0};
-                if ((lane & 3) == 0) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int row = h ? row1 : row0;
-                        if (!rval[row]) continue;
+            if (warp < 4) {
+                const int row = warp * 32 + lane;
+                const bool m = rval[row] && z > 0.f;
+                if (__any_sync(0xffffffffu, m) && lane == 0) atomicOr(&anyflag[slot], 1);
+                if (stats) {
+                    unsigned long long cnt[4] = {0, 0, 0, 0};
+                    if (rval[row]) {
                         const int lc[3] = {rlc[row], rlc[M + row], rlc[2 * M + row]};
                         const bool pf = plain_flag_cell<T, D, N>(g, U, slot, lc);
-                        const bool lf = h ? m1 : m0;
-                        cnt[pf ? (lf ? 0 : 2) : (lf ? 1 : 3)] += 1;
+                        cnt[pf ? (m ? 0 : 2) : (m ? 1 : 3)] += 1;
                     }
-                }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    unsigned long long v = cnt[q];
+                    for (int q = 0; q < 4; ++q) {
+                        unsigned long long v = cnt[q];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0 && v) atomicAdd(&stats[q], v);
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0 && v) atomicAdd(&stats[q], v);
+                    }
                 }
             }
             __syncthreads();
@@ -275,6 +270,7 @@ __global__ void __launch_bounds__(512, 1) k_flag_mlp(Grid g, const T* __restrict
         }
         __syncthreads();
     }
+    tc_teardown(st);
 }
 
 template <typename T, int D, int N>
