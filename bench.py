@@ -218,7 +218,7 @@ def main():
     ev0.record(stream)
     t0 = time.perf_counter()
     rhs_ms = []
-    kinds = np.zeros(8)
+    kinds = np.zeros(len(AMR.TIMING_SLOTS))
     flops_rhs = []
     flops = load_json(FLOPS_FILE, None)
     for _ in range(args.steps):
@@ -267,8 +267,7 @@ def main():
                 'l2': 'inputs larger than L2 (state arrays of several GB)',
                 'parallelism': 'replicas (dp%d, no data-path collective)' % world},
             'clocks': clk, 'gpu_launches': int(k1 - k0), 'roofline': roof,
-            'phase_ms_per_step': dict(zip(['ghost', 'rhs', 'reflux', 'restrict', 'cfl', 'flag', 'closure',
-                                           'upload_fill'], [float(x) / args.steps for x in kinds])),
+            'phase_ms_per_step': dict(zip(AMR.TIMING_SLOTS, [float(x) / args.steps for x in kinds])),
             'wall_s': wall}
 
     if rank == 0 and not args.no_e2e:

@@ -169,14 +169,18 @@ int amr_harvest(amr_ctx* ctx, long* n, double* samples, uint8_t* labels);
 /* Per-class device timing of the batched step, for profiling: enable (1) or
  * disable (0) CUDA events around each kernel class. While enabled, the step
  * is issued launch by launch instead of through the captured CUDA graph.
- * amr_get_timing synchronises and returns the last step's milliseconds:
- * ms[0] ghost fill, [1] fused RHS + stage, [2] reflux, [3] restriction,
- * [4] CFL reduction (0 if the step had a given dt), and of the last regrid
- * [5] flagging + request read-back (wall), [6] host closure (wall),
- * [7] table upload + new-patch fill (wall); launches (may be NULL) receives
- * the kernel launches behind each of [0..4]. */
+ * amr_get_timing synchronises and returns AMR_TIMING_SLOTS milliseconds.
+ * Of the last step (CUDA events): ms[0] ghost fill, [1] fused RHS + stage,
+ * [2] reflux, [3] restriction, [4] CFL reduction (0 if the step had a given
+ * dt). Of the last regrid: [5] the flag kernel (plain or learned; CUDA
+ * events), [6] host closure (wall), [7] table upload + new-patch fill (wall),
+ * [8] the ghost fill that precedes flagging (CUDA events), [9] the whole
+ * flagging phase: ghost fill, flag kernel, request compaction and read-back
+ * (wall). launches (may be NULL) receives the kernel launches behind each
+ * slot (0 for the wall-clock slots). */
+#define AMR_TIMING_SLOTS 10
 int amr_set_timing(amr_ctx* ctx, int enable);
-int amr_get_timing(amr_ctx* ctx, double ms[8], int launches[8]);
+int amr_get_timing(amr_ctx* ctx, double ms[AMR_TIMING_SLOTS], int launches[AMR_TIMING_SLOTS]);
 
 /* Counters since amr_init: host-to-device and device-to-host bytes copied,
  * kernels launched (graph launches count their kernels). */

@@ -270,10 +270,14 @@ class AMR:
     def set_timing(self, enable=True):
         self._check(self.lib.amr_set_timing(self.ctx, 1 if enable else 0))
 
+    TIMING_SLOTS = ('ghost', 'rhs', 'reflux', 'restrict', 'cfl', 'flag', 'closure', 'upload_fill',
+                    'regrid_ghost', 'flag_phase_wall')
+
     def timing(self):
-        """Last step: ms of (ghost, rhs, reflux, restrict, cfl, flag, closure, upload) and launches."""
-        ms = np.zeros(8)
-        n = np.zeros(8, dtype=np.int32)
+        """Milliseconds of the last step (slots 0-4) and regrid (5-9), named by
+        TIMING_SLOTS, and the kernel launches behind each slot."""
+        ms = np.zeros(len(self.TIMING_SLOTS))
+        n = np.zeros(len(self.TIMING_SLOTS), dtype=np.int32)
         self._check(self.lib.amr_get_timing(self.ctx, _ptr(ms), _ptr(n)))
         return ms, n
 

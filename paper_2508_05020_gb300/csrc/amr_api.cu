@@ -71,7 +71,10 @@ struct amr_ctx {
     bool timing = false;
     cudaEvent_t ev[3][5] = {};
     cudaEvent_t ev_cfl[2] = {};
-    double regrid_ms[3] = {0, 0, 0};      // flag (device), host closure, upload + new-patch fill
+    cudaEvent_t ev_rg[3] = {};            // regrid: before the ghost fill, before / after the flag kernel
+    double regrid_ms[3] = {0, 0, 0};      // flagging phase (wall), host closure, upload + new-patch fill
+    int regrid_fill_launches = 0;
+    bool regrid_timed = false;            // ev_rg hold a regrid issued while timing was on
     bool cfl_timed = false;
     // counters
     long long h2d = 0, d2h = 0, kernels = 0;
@@ -450,15 +453,21 @@ int step_impl(amr_ctx* c, double dt, double* dt_used) {
 // flags of the current state (ghosts filled first) -> compacted request lists on the host
 template <typename T>
 int compute_requests(amr_ctx* c, std::vector<Key>& refine, std::vector<Key>& coarsen) {
+    auto mark = [&](cudaEvent_t e) { return c->timing ? cudaEventRecord(e, c->stream) : cudaSuccess; };
+    CK(mark(c->ev_rg[0]), "event");
+    const long long k0 = c->kernels;
     int r = fill_all_levels<T>(c, St<T>(c, 0), 0.0);
     if (r) return r;
+    c->regrid_fill_launches = (int)(c->kernels - k0);
+    CK(mark(c->ev_rg[1]), "event");
     if (c->flagger == AMR_FLAG_MLP && (c->mlp_w || !c->initialising)) {
         if (!c->mlp_w) return fail(c, AMR_ERR_STATE, "learned indicator selected but no weights set");
-        CK(Kernels<T>::flag_mlp(c->grid, St<T>(c, 0), c->mlp_w, c->anyflag, grid_size(c, 2), c->stream),
+        CK(Kernels<T>::flag_mlp(c->grid, St<T>(c, 0), c->mlp_w, c->anyflag, grid_size(c, 1), c->stream),
            "flag (learned)");
     } else {
         CK(Kernels<T>::flag_plain(c->grid, St<T>(c, 0), c->anyflag, grid_size(c, 4), c->stream), "flag");
     }
+    CK(mark(c->ev_rg[2]), "event");
     CK(launch_requests(c->grid, c->anyflag, c->req_d + 2, c->req_d + 2 + c->cap, c->req_d, c->stream), "requests");
     c->kernels += 2;
     CK(cudaMemcpyAsync(c->req_h, c->req_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read requests");
@@ -489,6 +498,7 @@ int regrid_impl(amr_ctx* c, bool resample_ic) {
     if (r) return r;
     const auto t1 = std::chrono::steady_clock::now();
     c->regrid_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    c->regrid_timed = c->timing;
     c->regrid_ms[1] = c->regrid_ms[2] = 0.0;
     Mesh m2 = c->mesh;
     std::vector<Key> created = m2.refine(req);
@@ -759,7 +769,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     const MetaLayout ml(c->cap);
     c->meta_ints = ml.total;
     c->meta_d = (int*)dalloc(c, ml.total * sizeof(int));
-    c->anyflag = (int*)dalloc(c, c->cap * sizeof(int));
+    c->anyflag = (int*)dalloc(c, (c->cap + 32) * sizeof(int));     // flags + the learned flagger's work counter
     c->req_d = (int*)dalloc(c, (2 + 2 * (size_t)c->cap) * sizeof(int));
     c->cons_partial = (double*)dalloc(c, (size_t)c->cap * c->nv * sizeof(double));
     c->cons_d = (double*)dalloc(c, 8 * sizeof(double));
@@ -962,10 +972,10 @@ int amr_flag_stats(amr_ctx* c, long long counts[4]) {
     cudaError_t e;
     if (c->precision == 64) {
         if ((r = fill_all_levels<double>(c, St<double>(c, 0), 0.0))) return r;
-        e = Kernels<double>::flag_stats(c->grid, St<double>(c, 0), c->mlp_w, d, grid_size(c, 2), c->stream);
+        e = Kernels<double>::flag_stats(c->grid, St<double>(c, 0), c->mlp_w, d, grid_size(c, 1), c->stream);
     } else {
         if ((r = fill_all_levels<float>(c, St<float>(c, 0), 0.0))) return r;
-        e = Kernels<float>::flag_stats(c->grid, St<float>(c, 0), c->mlp_w, d, grid_size(c, 2), c->stream);
+        e = Kernels<float>::flag_stats(c->grid, St<float>(c, 0), c->mlp_w, d, grid_size(c, 1), c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "flag stats");
     unsigned long long hc[4];
@@ -1021,6 +1031,8 @@ int amr_set_timing(amr_ctx* c, int enable) {
             for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&c->ev[s][i]), "event");
         CK(cudaEventCreate(&c->ev_cfl[0]), "event");
         CK(cudaEventCreate(&c->ev_cfl[1]), "event");
+        for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&c->ev_rg[i]), "event");
+        c->regrid_timed = false;
     }
     // timed steps are issued launch by launch (events around each kernel
     // class); the captured graphs are used again once timing is off
@@ -1028,13 +1040,13 @@ int amr_set_timing(amr_ctx* c, int enable) {
     return AMR_OK;
 }
 
-int amr_get_timing(amr_ctx* c, double ms[8], int launches[8]) {
+int amr_get_timing(amr_ctx* c, double ms[AMR_TIMING_SLOTS], int launches[AMR_TIMING_SLOTS]) {
     GUARD(c);
     if (!ms) return AMR_ERR_ARG;
     if (!c->timing) return fail(c, AMR_ERR_STATE, "timing is not enabled");
     if (c->mode != AMR_MODE_BATCHED) return fail(c, AMR_ERR_STATE, "timing covers the batched mode");
     CK(cudaStreamSynchronize(c->stream), "timing");
-    for (int i = 0; i < 8; ++i) ms[i] = 0.0;
+    for (int i = 0; i < AMR_TIMING_SLOTS; ++i) ms[i] = 0.0;
     for (int s = 0; s < 3; ++s)
         for (int i = 0; i < 4; ++i) {
             float t = 0.f;
@@ -1046,12 +1058,21 @@ int amr_get_timing(amr_ctx* c, double ms[8], int launches[8]) {
         CK(cudaEventElapsedTime(&t, c->ev_cfl[0], c->ev_cfl[1]), "timing");
         ms[4] = t;
     }
-    ms[5] = c->regrid_ms[0];
+    if (c->regrid_timed) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->ev_rg[1], c->ev_rg[2]), "timing");
+        ms[5] = t;
+        CK(cudaEventElapsedTime(&t, c->ev_rg[0], c->ev_rg[1]), "timing");
+        ms[8] = t;
+    }
     ms[6] = c->regrid_ms[1];
     ms[7] = c->regrid_ms[2];
+    ms[9] = c->regrid_ms[0];
     if (launches) {
-        const int l[8] = {3 * c->L, 3, 3, 3 * (c->L - 1), c->cfl_timed ? 2 : 0, 0, 0, 0};
-        for (int i = 0; i < 8; ++i) launches[i] = l[i];
+        const int rt = c->regrid_timed ? 1 : 0;
+        const int l[AMR_TIMING_SLOTS] = {3 * c->L, 3, 3, 3 * (c->L - 1), c->cfl_timed ? 2 : 0, rt, 0, 0,
+                                         rt * c->regrid_fill_launches, 0};
+        for (int i = 0; i < AMR_TIMING_SLOTS; ++i) launches[i] = l[i];
     }
     return AMR_OK;
 }
@@ -1074,6 +1095,7 @@ void amr_destroy(amr_ctx* c) {
             for (int i = 0; i < 5; ++i) cudaEventDestroy(c->ev[s][i]);
         cudaEventDestroy(c->ev_cfl[0]);
         cudaEventDestroy(c->ev_cfl[1]);
+        for (int i = 0; i < 3; ++i) cudaEventDestroy(c->ev_rg[i]);
     }
     dfree_all(c);
     if (c->meta_h) cudaFreeHost(c->meta_h);

@@ -500,29 +500,61 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
         const int slot = one_slot >= 0 ? one_slot : g.all_list[pi];
         const int lev = g.level[slot];
         const int pf = g.pflag[slot];
-        // 1. stage the chunk and its halo as primitives
-        for (int idx = threadIdx.x; idx < C::QN; idx += NTH) {
-            int qx, qy, sz;
-            if (idx < C::QC) {                               // centre planes, full S x S
-                qx = idx % C::QX;
-                qy = (idx / C::QX) % C::QY;
-                sz = D == 3 ? z0 + G + idx / (C::QX * C::QY) : 0;
-            } else {                                         // 3D halo planes, interior N x N
-                const int h = idx - C::QC;
-                qx = h % N + G;
-                qy = (h / N) % N + G;
-                const int zh = h / (N * N);
-                sz = z0 + (zh < G ? zh : zh + DZ);
+        // 1. stage the chunk and its halo as primitives, loading 16-byte vectors
+        //    along x (slot rows are 16-byte aligned)
+        {
+            constexpr int VE = 16 / sizeof(T);
+            auto stage = [&](const T (&Uv)[NV][VE], int e, int qidx) {
+                T Uc[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Uc[v] = Uv[v][e];
+                T rho, u[D], p, Tt;
+                primitives<T, D>(Uc, gm1, rho, u, p, Tt);
+                q[qidx] = p;
+#pragma unroll
+                for (int d = 0; d < D; ++d) q[(1 + d) * C::QN + qidx] = u[d];
+                q[(D + 1) * C::QN + qidx] = Tt;
+            };
+            auto loadv = [&](T (&Uv)[NV][VE], int sz, int sy, int sx) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const T* src = Us + slot_index(g, slot, v, sz, sy, sx);
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(src);
+                        Uv[v][0] = t4.x; Uv[v][1] = t4.y; Uv[v][2] = t4.z; Uv[v][3] = t4.w;
+                    } else {
+                        const double2 t2 = *reinterpret_cast<const double2*>(src);
+                        Uv[v][0] = t2.x; Uv[v][1] = t2.y;
+                    }
+                }
+            };
+            // centre planes (3D) or the whole slot (1D/2D): full rows
+            constexpr int NXV = (C::QX + VE - 1) / VE;
+            for (int iv = threadIdx.x; iv < NXV * C::QY * C::QZ; iv += NTH) {
+                const int xv = iv % NXV, qy = (iv / NXV) % C::QY, qz = iv / (NXV * C::QY);
+                T Uv[NV][VE];
+                loadv(Uv, D == 3 ? z0 + G + qz : 0, qy, xv * VE);
+#pragma unroll
+                for (int e = 0; e < VE; ++e) {
+                    const int qx = xv * VE + e;
+                    if (qx < C::QX) stage(Uv, e, (qz * C::QY + qy) * C::QX + qx);
+                }
             }
-            T Uc[NV];
+            if constexpr (D == 3) {
+                // halo planes: interior x in [G, G + N) from aligned vectors
+                constexpr int HX0 = (G / VE) * VE;
+                constexpr int NHV = (G + N - HX0 + VE - 1) / VE;
+                for (int iv = threadIdx.x; iv < NHV * N * 2 * G; iv += NTH) {
+                    const int xv = iv % NHV, hy = (iv / NHV) % N, zh = iv / (NHV * N);
+                    T Uv[NV][VE];
+                    loadv(Uv, z0 + (zh < G ? zh : zh + DZ), hy + G, HX0 + xv * VE);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Uc[v] = Us[slot_index(g, slot, v, sz, qy, qx)];
-            T rho, u[D], p, Tt;
-            primitives<T, D>(Uc, gm1, rho, u, p, Tt);
-            q[idx] = p;
-#pragma unroll
-            for (int d = 0; d < D; ++d) q[(1 + d) * C::QN + idx] = u[d];
-            q[(D + 1) * C::QN + idx] = Tt;
+                    for (int e = 0; e < VE; ++e) {
+                        const int x = HX0 + xv * VE + e;
+                        if (x >= G && x < G + N) stage(Uv, e, C::QC + (zh * N + hy) * N + (x - G));
+                    }
+                }
+            }
         }
         __syncthreads();
         T R[CPT][NV];

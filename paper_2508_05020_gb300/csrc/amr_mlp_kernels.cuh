@@ -85,212 +85,494 @@ __device__ bool plain_flag_cell(const Grid& g, const T* U, int slot, const int* 
 }
 
 // ---------------------------------------------------------------------------
-// K10: learned indicator on the band [-1, N]^d of every leaf patch. One work
-// item is a leaf patch (1D/2D) or a slab of DZ band planes of it (3D). The
-// primitives (rho, u.., p) of the slab and its +-2 halo are staged in shared
-// memory in FP32. Band cells are taken 128 at a time (a GEMM tile, 16 rows per
-// warp): all threads write the centre-normalised 5^d stencil features of the
-// tile into a double-buffered 64-wide K chunk in shared memory (BF16, padded
-// rows), and each warp accumulates layer 1 on the tensor cores from that chunk
-// (ldmatrix + mma.sync). Layer 2 and the output follow in registers. A patch is
-// flagged if any in-domain band cell has a positive logit; items of an already
-// flagged patch are skipped. With `stats` the plain sensor of every band cell
-// is evaluated too and the agreement counts TP, FP, FN, TN accumulated.
+// K10: learned indicator on the band [-1, N]^d of every leaf patch. A work
+// item is a leaf patch (1D/2D) or a slab of DZ band planes of it (3D); items
+// are taken from a global counter in patch-major order, and items of a patch
+// that is already flagged are skipped. Band cells are evaluated 128 at a time
+// (a tile, one row per TMEM lane). Inside the kernel the K axis is ordered by
+// stencil plane (3D: the offset oz; 1D/2D: a single plane), then field, then
+// point of the plane, each plane padded to PK columns; a K chunk is one plane.
+// The CTA is warp-specialised:
+//  - 8 producer warps stage the primitives (rho, u.., p) of the item and its
+//    +-2 halo in shared memory (FP32), then compute the centre-normalised
+//    features of one stencil plane of a tile (each warp: 32 rows x PK/2
+//    columns; every column's cell offset and field are compile-time), convert
+//    them to BF16 and store them with tcgen05.st into a ring of NS chunk
+//    buffers in tensor memory (row = TMEM lane, two features per 32-bit
+//    column), then arrive on the buffer's `full` barrier;
+//  - one thread of the MMA warp waits for each chunk, issues the layer-1
+//    tcgen05.mma (M = 128, N = 64, K = 16 per slice, A from tensor memory, W1
+//    from shared memory) into the tile's accumulator and commits to the
+//    buffer's `empty` barrier; at the end of a tile it commits to `acc_full`
+//    and, once the epilogue has written the hidden layer (again into tensor
+//    memory), issues the layer-2 MMA (K = 64, into the same accumulator
+//    columns) and commits to `l2_full`;
+//  - 4 epilogue warps (TMEM lanes 0-127) turn the layer-1 accumulator into the
+//    BF16 hidden layer (bias + ReLU), then form the logit from the layer-2
+//    accumulator, and flag the patch if an in-domain band cell has a positive
+//    logit.
+// The accumulators are double-buffered, so the epilogue of one tile overlaps
+// the layer-1 MMAs of the next. Rows are ordered x fastest, then z, then y
+// (3D), and the staged primitives use padded x and plane pitches for which the
+// shared-memory words of 32 consecutive rows fall in 32 distinct banks, for
+// every stencil offset. With `stats` the plain sensor of every band cell is
+// evaluated too and the agreement counts TP, FP, FN, TN accumulated.
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pad_mod32(int n, int r) { return n + (((r - n) % 32) + 32) % 32; }
+
+// plane-major K order of the fused kernel
+template <int D> struct MlpPlanes {
+    static constexpr int F = D + 2;
+    static constexpr int NPL = D == 3 ? 5 : 1;            // stencil planes = K chunks per tile
+    static constexpr int PPL = D == 1 ? 5 : 25;           // stencil points per plane
+    static constexpr int PF = F * PPL;                    // features per plane
+    static constexpr int SG = 2;                          // producer warps per row group
+    static constexpr int PK = (PF + 16 * SG - 1) / (16 * SG) * (16 * SG);   // K per plane, padded
+    static constexpr int SPG = PK / (16 * SG);            // 16-wide slices per producer warp
+    static constexpr int KF = NPL * PK;
+};
+
+template <int D> struct MlpFlagW {
+    __nv_bfloat16 w1[MLP_H * MlpPlanes<D>::KF];           // canonical K-major, plane-major K
+    __nv_bfloat16 w2[MLP_H * MLP_H];
+    float b1[MLP_H], b2[MLP_H], w3[MLP_H];
+    float b3;
+};
+
+// flat float weights (W1 with k = j (d + 2) + f, stencil point j) -> shared memory
+template <int D>
+__device__ void mlp_flag_stage_weights(MlpFlagW<D>& s, const float* __restrict__ w) {
+    using PL = MlpPlanes<D>;
+    constexpr int K = mlp_kin(D), F = PL::F;
+    const float* W1 = w;
+    const float* B1 = W1 + MLP_H * K;
+    const float* W2 = B1 + MLP_H;
+    const float* B2 = W2 + MLP_H * MLP_H;
+    const float* W3 = B2 + MLP_H;
+    const float* B3 = W3 + MLP_H;
+    for (int i = threadIdx.x; i < MLP_H * PL::KF; i += blockDim.x) {
+        const int o = i / PL::KF, kf = i - o * PL::KF;
+        const int pl = kf / PL::PK, p = kf - pl * PL::PK;
+        float v = 0.f;
+        if (p < PL::PF) {
+            const int f = p / PL::PPL, j = pl * PL::PPL + p % PL::PPL;
+            v = W1[o * K + j * F + f];
+        }
+        s.w1[canon_off(o, kf, PL::KF)] = __float2bfloat16_rn(v);
+    }
+    for (int i = threadIdx.x; i < MLP_H * MLP_H; i += blockDim.x) {
+        const int o = i / MLP_H, k = i - o * MLP_H;
+        s.w2[canon_off(o, k, MLP_H)] = __float2bfloat16_rn(W2[i]);
+    }
+    for (int i = threadIdx.x; i < MLP_H; i += blockDim.x) {
+        s.b1[i] = B1[i];
+        s.b2[i] = B2[i];
+        s.w3[i] = W3[i];
+    }
+    if (threadIdx.x == 0) s.b3 = B3[0];
+}
+
 template <int D, int N> struct MlpBand {
+    using PL = MlpPlanes<D>;
     static constexpr int B = N + 2;                       // band cells per dimension
     static constexpr int S = N + 2 * G;                   // slot cells per dimension
-    static constexpr int DZ = D == 3 ? 3 : 1;
+    static constexpr int DZ = D == 3 ? (B % 3 == 0 ? 3 : 2) : 1;
     static constexpr int NSLAB = D == 3 ? B / DZ : 1;
-    static constexpr int PX = S, PY = D >= 2 ? S : 1, PZ = D == 3 ? DZ + 4 : 1;
-    static constexpr int PLANE = PX * PY * PZ;            // floats per primitive field
+    static_assert(D != 3 || B % DZ == 0, "the slabs tile the band");
+    // staged primitives: x pitch PX, plane pitch PP, PZ planes (3D)
+    static constexpr int PX = D == 1 ? S : (D == 2 ? pad_mod32(S, B % 32) : pad_mod32(S, (B * DZ) % 32));
+    static constexpr int PY = D >= 2 ? S : 1;
+    static constexpr int PP = D == 3 ? pad_mod32(PX * S, B % 32) : PX * PY;
+    static constexpr int PZ = D == 3 ? DZ + 4 : 1;
+    static constexpr int PLANE = PP * PZ;                 // floats per primitive field
     static constexpr int CELLS = D == 1 ? B : (D == 2 ? B * B : B * B * DZ);
     static constexpr int F = D + 2;
-    static constexpr int NTH = 512;                       // 16 warps
     static constexpr int M = TC_M;                        // rows of a tile (TMEM lanes)
     static constexpr int TILES = (CELLS + M - 1) / M;
+    static constexpr int NS = 5;                          // chunk ring depth (tensor memory)
+    static constexpr int EPI_WARPS = 4, MMA_WARP = 4, PROD_WARP0 = 5, PROD_WARPS = 4 * PL::SG;
+    static constexpr int NPROD = PROD_WARPS * 32;
+    static constexpr int NTH = (PROD_WARP0 + PROD_WARPS) * 32;
+    // tensor memory columns: accumulator of tile parity a at 64 a (layer 1,
+    // then layer 2), the hidden layer (layer-2 A), the chunk ring
+    static constexpr int TM_H = 2 * MLP_H, TM_RING = TM_H + MLP_H / 2, TMEM_COLS = 512;
+    static constexpr int STAGE_COLS = PL::PK / 2;
+    static_assert(TM_RING + NS * STAGE_COLS <= TMEM_COLS, "tensor memory budget");
+    // band cell of row r (1D: x; 2D: x, y; 3D: x, z, y)
+    __device__ static void cell(int r, int& bx, int& by, int& bz) {
+        bx = r % B;
+        if (D == 1) { by = 0; bz = 0; }
+        else if (D == 2) { by = r / B; bz = 0; }
+        else { bz = (r / B) % DZ; by = r / (B * DZ); }
+    }
 };
+
+// features of one stencil plane for producer group SGI: columns
+// SGI * SPG * 16 .. + SPG * 16 of the plane, packed two per word; `c` points at
+// the row's centre cell in the plane (field 0), scale/shift per field kind
+template <int D, int N, int SGI>
+__device__ __forceinline__ void plane_features(const float* c, float s_rho, float s_u, float s_p,
+                                               uint32_t (&wv)[MlpPlanes<D>::SPG * 8]) {
+    using PL = MlpPlanes<D>;
+    using P = MlpBand<D, N>;
+#pragma unroll
+    for (int i = 0; i < PL::SPG * 16; i += 2) {
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = SGI * PL::SPG * 16 + i + h;
+            if (p < PL::PF) {
+                const int f = p / PL::PPL, jj = p % PL::PPL;
+                const int off = f * P::PLANE + (D >= 2 ? (jj / 5 - 2) * P::PX : 0) + jj % 5 - 2;
+                const float x = c[off];
+                v[h] = f == 0 ? fmaf(x, s_rho, -1.f) : (f == PL::F - 1 ? fmaf(x, s_p, -1.f) : x * s_u);
+            } else {
+                v[h] = 0.f;
+            }
+        }
+        wv[i / 2] = pack_bf16(v[0], v[1]);
+    }
+}
 
 template <int D, int N> struct MlpFlagLayout {
     using P = MlpBand<D, N>;
+    static constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
     static constexpr size_t W = 0;
-    static constexpr size_t KREL = (sizeof(MlpTcSmem<D>) + 127) / 128 * 128;
-    static constexpr size_t PRIM = KREL + sizeof(int) * mlp_pts(D);
-    static constexpr size_t ABUF = (PRIM + sizeof(float) * P::F * P::PLANE + 127) / 128 * 128;
-    static constexpr size_t HBUF = ABUF + 2 * sizeof(__nv_bfloat16) * TC_M * TC_KC;
-    static constexpr size_t ROWS = HBUF + sizeof(__nv_bfloat16) * TC_M * MLP_H;
-    static constexpr size_t SLOTS = ROWS + sizeof(int) * 8 * TC_M;
-    static constexpr size_t TOTAL = SLOTS + 4 * sizeof(uint64_t);
+    static constexpr size_t PRIM = al(sizeof(MlpFlagW<D>));
+    static constexpr size_t CTL = al(PRIM + sizeof(float) * P::F * P::PLANE);     // int4 stage_ctl[NS], tile_ctl[2]
+    static constexpr size_t BARS = CTL + sizeof(int4) * (P::NS + 2);
+    // full[NS], empty[NS], acc_full[2], acc_empty[2], h_full, l2_full, fin
+    static constexpr int NBAR = 2 * P::NS + 7;
+    static constexpr size_t MISC = BARS + sizeof(uint64_t) * NBAR;                // tmem base, abort, item
+    static constexpr size_t TOTAL = MISC + 16;
 };
 
 template <int D, int N>
 constexpr size_t mlp_flag_smem() { return MlpFlagLayout<D, N>::TOTAL + 128; }
 
-template <typename T, int D, int N>
-__global__ void __launch_bounds__(512, 1) k_flag_mlp(Grid g, const T* __restrict__ U, const float* __restrict__ w,
-                                                     int* anyflag, unsigned long long* stats) {
+__device__ __forceinline__ void producer_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
+}
+
+template <typename T, int D, int N, bool STATS>
+__global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
+    k_flag_mlp(Grid g, const T* __restrict__ U, const float* __restrict__ w, int* anyflag,
+               unsigned long long* stats) {
     using P = MlpBand<D, N>;
+    using PL = MlpPlanes<D>;
     using Lay = MlpFlagLayout<D, N>;
-    constexpr int F = P::F, M = P::M, NP = mlp_npts(D), PTS = mlp_pts(D), KP = mlp_kpad(D);
+    constexpr int F = P::F, M = P::M, NS = P::NS, NPL = PL::NPL, PK = PL::PK, KF = PL::KF;
+    static_assert(Lay::TOTAL + 128 <= 232448, "shared memory of one CTA");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    MlpTcSmem<D>& ms = *reinterpret_cast<MlpTcSmem<D>*>(base + Lay::W);
-    int* krel = reinterpret_cast<int*>(base + Lay::KREL);
+    MlpFlagW<D>& ms = *reinterpret_cast<MlpFlagW<D>*>(base + Lay::W);
     float* prim = reinterpret_cast<float*>(base + Lay::PRIM);
-    __nv_bfloat16* abuf = reinterpret_cast<__nv_bfloat16*>(base + Lay::ABUF);
-    __nv_bfloat16* hbuf = reinterpret_cast<__nv_bfloat16*>(base + Lay::HBUF);
-    int* rcen = reinterpret_cast<int*>(base + Lay::ROWS);
-    float* rsc = reinterpret_cast<float*>(rcen + M);      // [3][M]: 1/rho0, 1/c0, 1/p0
-    int* rval = reinterpret_cast<int*>(rsc + 3 * M);
-    int* rlc = rval + M;                                  // [3][M]: local cell
-    uint64_t* slots = reinterpret_cast<uint64_t*>(base + Lay::SLOTS);
-    __shared__ int skip;
-    mlp_tc_stage_weights<D>(ms, w);
-    // stencil point j -> offset of its cell from the centre cell (padding points: 0)
-    for (int j = threadIdx.x; j < PTS; j += blockDim.x) {
-        const int ox = j % 5 - 2, oy = D >= 2 ? (j / 5) % 5 - 2 : 0, oz = D == 3 ? j / 25 - 2 : 0;
-        krel[j] = j < NP ? (oz * P::PY + oy) * P::PX + ox : 0;
-    }
-    TcState st;
-    tc_setup(st, slots);                                   // includes a CTA barrier
-    const T gm1 = T(g.gamma) - T(1);
-    const int npatch = g.counts[1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // feature-fill role: row of the tile and a 16-wide K slice of the chunk
-    const int frow = (warp & 3) * 32 + lane, fslice = warp >> 2;
-    bool alive = true;
-    for (int item = blockIdx.x; item < npatch * P::NSLAB && alive; item += gridDim.x) {
-        const int pi = item / P::NSLAB, slab = item - pi * P::NSLAB;
-        const int slot = g.leaf_list[pi];
-        if (threadIdx.x == 0) skip = (!stats && *((volatile int*)&anyflag[slot])) ? 1 : 0;
-        __syncthreads();
-        if (skip) continue;
-        const int lev = g.level[slot];
-        const int c[3] = {g.coord[slot * 3], g.coord[slot * 3 + 1], g.coord[slot * 3 + 2]};
-        const int zb0 = D == 3 ? slab * P::DZ - 1 : 0;            // first band plane (local z)
-        // primitives of the slab and its halo: local z in [zb0 - 2, zb0 + DZ + 2)
-        for (int idx = threadIdx.x; idx < P::PLANE; idx += blockDim.x) {
-            const int px = idx % P::PX, py = (idx / P::PX) % P::PY, pz = idx / (P::PX * P::PY);
-            const int sz = D == 3 ? zb0 - 2 + pz + G : 0;
-            T Uc[D + 2];
-#pragma unroll
-            for (int v = 0; v < D + 2; ++v) Uc[v] = U[slot_index(g, slot, v, sz, py, px)];
-            T rho, u[D], p, Tt;
-            primitives<T, D>(Uc, gm1, rho, u, p, Tt);
-            prim[idx] = (float)rho;
-#pragma unroll
-            for (int d = 0; d < D; ++d) prim[(1 + d) * P::PLANE + idx] = (float)u[d];
-            prim[(F - 1) * P::PLANE + idx] = (float)p;
+    int4* stage_ctl = reinterpret_cast<int4*>(base + Lay::CTL);
+    int4* tile_ctl = stage_ctl + NS;
+    uint32_t* misc = reinterpret_cast<uint32_t*>(base + Lay::MISC);
+    volatile int* abort_f = reinterpret_cast<volatile int*>(misc + 1);
+    volatile int* s_item = reinterpret_cast<volatile int*>(misc + 2);
+    const uint32_t b_full = smem_u32(base + Lay::BARS), b_empty = b_full + 8 * NS, b_accf = b_empty + 8 * NS;
+    const uint32_t b_acce = b_accf + 16, b_h = b_acce + 16, b_l2 = b_h + 8, b_fin = b_l2 + 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    mlp_flag_stage_weights<D>(ms, w);
+    if (warp == 0) tmem_alloc(smem_u32(misc), P::TMEM_COLS);
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(b_full + 8 * s, P::PROD_WARPS);
+            mbar_init(b_empty + 8 * s, 1);
         }
-        __syncthreads();
-        for (int tile = 0; tile < P::TILES; ++tile) {
-            if (threadIdx.x < M) {                         // per-row data of the tile
-                const int r = tile * M + threadIdx.x;
-                const bool inb = r < P::CELLS;
-                const int rr = inb ? r : P::CELLS - 1;
-                const int bx = rr % P::B, by = D >= 2 ? (rr / P::B) % P::B : 0, bz = D == 3 ? rr / (P::B * P::B) : 0;
-                const int l0 = bx - 1, l1 = D >= 2 ? by - 1 : 0, l2 = D == 3 ? zb0 + bz : 0;
-                const int qx = l0 + G, qy = D >= 2 ? l1 + G : 0, qz = D == 3 ? bz + 2 : 0;
-                const int cen = (qz * P::PY + qy) * P::PX + qx;
-                const float r0 = prim[cen], p0 = prim[(F - 1) * P::PLANE + cen];
-                const float ir = 1.f / r0;
-                bool indom = inb;
-                const int lcv[3] = {l0, l1, l2};
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    if (g.periodic[d]) continue;
-                    const int Gd = c[d] * N + lcv[d];
-                    indom = indom && Gd >= 0 && Gd < g.ext[lev][d] * N;
-                }
-                rcen[threadIdx.x] = cen;
-                rsc[threadIdx.x] = ir;
-                rsc[M + threadIdx.x] = rsqrtf((float)g.gamma * p0 * ir);
-                rsc[2 * M + threadIdx.x] = 1.f / p0;
-                rval[threadIdx.x] = indom ? 1 : 0;
-                rlc[threadIdx.x] = l0;
-                rlc[M + threadIdx.x] = l1;
-                rlc[2 * M + threadIdx.x] = l2;
-            }
-            __syncthreads();
-            const int mcen = rcen[frow];
-            const float sc0 = rsc[frow], sc1 = rsc[M + frow], sc2 = rsc[2 * M + frow];
-            // 16 features (one field, 16 consecutive stencil points) of chunk cc
-            auto fill = [&](int cc, __nv_bfloat16* dst) {
-                const int k0 = cc * TC_KC + fslice * 16;
-                uint32_t wv[8];
-                if (k0 < KP) {
-                    const int f = k0 / PTS, j0 = k0 - f * PTS;
-                    const float sc = f == 0 ? sc0 : (f == F - 1 ? sc2 : sc1);
-                    const float sh = (f == 0 || f == F - 1) ? -1.f : 0.f;
-                    const float* pf = prim + f * P::PLANE + mcen;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float x0 = pf[krel[j0 + 2 * e]], x1 = pf[krel[j0 + 2 * e + 1]];
-                        wv[e] = pack_bf16(x0 * sc + sh, x1 * sc + sh);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(b_accf + 8 * a, 2);                 // the MMAs' commit + the tile record
+            mbar_init(b_acce + 8 * a, P::EPI_WARPS);
+        }
+        mbar_init(b_h, P::EPI_WARPS);
+        mbar_init(b_l2, 1);
+        mbar_init(b_fin, 1);
+        *abort_f = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(misc);
+    const int total = g.counts[1] * P::NSLAB;
+    int* counter = anyflag + g.cap;                        // zeroed with the flags by the launcher
+
+    if (warp >= P::PROD_WARP0) {
+        // ---------------- producers ----------------
+        // TMEM lane quarter of a warp is warp % 4: the row group follows it
+        const int ptid = threadIdx.x - P::PROD_WARP0 * 32;
+        const int frow = (warp & 3) * 32 + lane, sg = (warp - P::PROD_WARP0) >> 2;
+        const uint32_t tm_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + P::TM_RING + sg * PL::SPG * 8;
+        const T gm1 = T(g.gamma) - T(1);
+        int s = 0;
+        uint32_t ph = 0;                                   // ring position and pass parity
+        for (;;) {
+            producer_sync(P::NPROD);                       // the previous item's primitives are no longer read
+            if (ptid == 0) {
+                int it;
+                for (;;) {
+                    it = atomicAdd(counter, 1);
+                    if (it >= total || *abort_f) {
+                        it = -1;
+                        break;
                     }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) wv[e] = 0u;
+                    if constexpr (STATS) break;
+                    if (!*((volatile int*)&anyflag[g.leaf_list[it / P::NSLAB]])) break;
                 }
-                *reinterpret_cast<uint4*>(dst + canon_off(frow, fslice * 16, TC_KC)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-                *reinterpret_cast<uint4*>(dst + canon_off(frow, fslice * 16 + 8, TC_KC)) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
-            };
-            const float z = mlp_tile_tc<D>(st, ms, abuf, hbuf, fill);
-            if (!__syncthreads_and(st.ok ? 1 : 0)) {       // a bounded wait gave up somewhere
-                if (threadIdx.x == 0) atomicOr(&g.time->err, ERR_TIMEOUT);
-                alive = false;
+                *s_item = it;
+            }
+            producer_sync(P::NPROD);
+            const int item = *s_item;
+            if (item < 0) {                                // end record in the next chunk buffer
+                mbar_wait_ab(b_empty + 8 * s, ph ^ 1, abort_f);
+                if (ptid == 0) stage_ctl[s] = make_int4(-1, 0, 0, 0);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_full + 8 * s);
                 break;
             }
-            if (warp < 4) {
-                const int row = warp * 32 + lane;
-                const bool m = rval[row] && z > 0.f;
-                if (__any_sync(0xffffffffu, m) && lane == 0) atomicOr(&anyflag[slot], 1);
-                if (stats) {
-                    unsigned long long cnt[4] = {0, 0, 0, 0};
-                    if (rval[row]) {
-                        const int lc[3] = {rlc[row], rlc[M + row], rlc[2 * M + row]};
-                        const bool pf = plain_flag_cell<T, D, N>(g, U, slot, lc);
-                        cnt[pf ? (m ? 0 : 2) : (m ? 1 : 3)] += 1;
+            const int pi = item / P::NSLAB, slab = item - pi * P::NSLAB;
+            const int slot = g.leaf_list[pi];
+            const int zb0 = D == 3 ? slab * P::DZ - 1 : 0;  // first band plane (local z)
+            // primitives of the slab and its halo: local z in [zb0 - 2, zb0 + DZ + 2),
+            // loaded as 16-byte vectors along x (slot rows are 16-byte aligned)
+            {
+                constexpr int VE = 16 / sizeof(T);
+                constexpr int NXV = (P::S + VE - 1) / VE;
+                constexpr int NVEC = NXV * P::PY * P::PZ;
+                for (int iv = ptid; iv < NVEC; iv += P::NPROD) {
+                    const int xv = iv % NXV, py = (iv / NXV) % P::PY, pz = iv / (NXV * P::PY);
+                    const int sz = D == 3 ? zb0 - 2 + pz + G : 0;
+                    T Uv[D + 2][VE];
+#pragma unroll
+                    for (int v = 0; v < D + 2; ++v) {
+                        const T* src = U + slot_index(g, slot, v, sz, py, xv * VE);
+                        if constexpr (sizeof(T) == 4) {
+                            const float4 q = *reinterpret_cast<const float4*>(src);
+                            Uv[v][0] = q.x; Uv[v][1] = q.y; Uv[v][2] = q.z; Uv[v][3] = q.w;
+                        } else {
+                            const double2 q = *reinterpret_cast<const double2*>(src);
+                            Uv[v][0] = q.x; Uv[v][1] = q.y;
+                        }
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        unsigned long long v = cnt[q];
+                    for (int e = 0; e < VE; ++e) {
+                        const int px = xv * VE + e;
+                        if (px >= P::S) break;
+                        T Uc[D + 2];
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        if (lane == 0 && v) atomicAdd(&stats[q], v);
+                        for (int v = 0; v < D + 2; ++v) Uc[v] = Uv[v][e];
+                        T rho, u[D], p, Tt;
+                        primitives<T, D>(Uc, gm1, rho, u, p, Tt);
+                        const int idx = pz * P::PP + py * P::PX + px;
+                        prim[idx] = (float)rho;
+#pragma unroll
+                        for (int d = 0; d < D; ++d) prim[(1 + d) * P::PLANE + idx] = (float)u[d];
+                        prim[(F - 1) * P::PLANE + idx] = (float)p;
                     }
                 }
             }
-            __syncthreads();
-            if (!stats) {                                    // the rest of a flagged patch is skipped
-                if (threadIdx.x == 0) skip = *((volatile int*)&anyflag[slot]);
-                __syncthreads();
-                if (skip) break;
+            producer_sync(P::NPROD);
+            for (int tile = 0; tile < P::TILES; ++tile) {
+                // the row's centre cell and its normalisation: 1/rho0, 1/c0, 1/p0
+                const int r = tile * M + frow;
+                int bx, by, bz;
+                P::cell(r < P::CELLS ? r : P::CELLS - 1, bx, by, bz);
+                const int mcen = (D == 3 ? (bz + 2) * P::PP : 0) + (D >= 2 ? (by - 1 + G) * P::PX : 0) + bx - 1 + G;
+                const float r0 = prim[mcen], p0 = prim[(F - 1) * P::PLANE + mcen];
+                const float s_rho = 1.f / r0;
+                const float s_u = rsqrtf((float)g.gamma * p0 * s_rho), s_p = 1.f / p0;
+#pragma unroll 1
+                for (int pl = 0; pl < NPL; ++pl) {
+                    uint32_t wv[PL::SPG * 8];
+                    const float* c = prim + mcen + (D == 3 ? (pl - 2) * P::PP : 0);
+                    if (sg == 0) plane_features<D, N, 0>(c, s_rho, s_u, s_p, wv);
+                    else plane_features<D, N, 1>(c, s_rho, s_u, s_p, wv);
+                    mbar_wait_ab(b_empty + 8 * s, ph ^ 1, abort_f);
+                    tc_fence_after();
+                    if (pl == 0 && ptid == 0) stage_ctl[s] = make_int4(slot, zb0, tile, 0);
+                    const uint32_t ta = tm_lane + s * P::STAGE_COLS;
+                    if constexpr (PL::SPG == 4) {
+                        tmem_st32(ta, wv);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PL::SPG; ++q) {
+                            uint32_t w8[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) w8[e] = wv[q * 8 + e];
+                            tmem_st8(ta + q * 8, w8);
+                        }
+                    }
+                    tmem_wait_st();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(b_full + 8 * s);
+                    if (++s == NS) { s = 0; ph ^= 1; }
+                }
             }
         }
-        __syncthreads();
+    } else if (warp == P::MMA_WARP) {
+        // ---------------- MMA issue (one thread) ----------------
+        if (lane == 0) {
+            constexpr uint32_t IDESC = umma_idesc_bf16(TC_M, MLP_H);
+            // descriptors advance by k 16-byte units per k columns (canonical K-major)
+            const uint64_t bd1 = umma_desc(smem_u32(ms.w1), 128, (KF >> 3) * 128);
+            const uint64_t bd2 = umma_desc(smem_u32(ms.w2), 128, (MLP_H >> 3) * 128);
+            auto layer2 = [&](int tt) -> bool {           // hidden layer of tile tt written -> its layer-2 MMA
+                if (!mbar_wait_ab(b_h, tt & 1, abort_f)) return false;
+                tc_fence_after();
+                const uint32_t d = tmem + (tt & 1) * MLP_H;
+#pragma unroll
+                for (int kk = 0; kk < MLP_H; kk += 16)
+                    umma_bf16_ts(d, tmem + P::TM_H + kk / 2, bd2 + (uint64_t)kk, IDESC, kk > 0 ? 1u : 0u);
+                umma_commit(b_l2);
+                return true;
+            };
+            int s = 0, t = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (;;) {
+                if (!mbar_wait_ab(b_full + 8 * s, ph, abort_f)) { ok = false; break; }
+                const int4 info = stage_ctl[s];
+                if (info.x < 0) break;                     // no more items
+                const int a = t & 1;
+                if (t >= 2 && !mbar_wait_ab(b_acce + 8 * a, ((t >> 1) - 1) & 1, abort_f)) { ok = false; break; }
+                const uint32_t d = tmem + a * MLP_H;
+#pragma unroll 1
+                for (int pl = 0; pl < NPL; ++pl) {
+                    if (pl > 0 && !mbar_wait_ab(b_full + 8 * s, ph, abort_f)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t aa = tmem + P::TM_RING + s * P::STAGE_COLS;
+                    const uint64_t bb = bd1 + (uint64_t)(pl * PK);
+#pragma unroll
+                    for (int q = 0; q < PK / 16; ++q)
+                        umma_bf16_ts(d, aa + q * 8, bb + (uint64_t)(q * 16), IDESC, (pl | q) ? 1u : 0u);
+                    umma_commit(b_empty + 8 * s);
+                    if (++s == NS) { s = 0; ph ^= 1; }
+                }
+                if (!ok) break;
+                umma_commit(b_accf + 8 * a);
+                tile_ctl[a] = info;
+                mbar_arrive(b_accf + 8 * a);
+                if (t > 0 && !layer2(t - 1)) { ok = false; break; }
+                ++t;
+            }
+            if (ok && t > 0) ok = layer2(t - 1);
+            if (ok) {                                      // end record for the epilogue
+                const int a = t & 1;
+                if (t < 2 || mbar_wait_ab(b_acce + 8 * a, ((t >> 1) - 1) & 1, abort_f)) {
+                    tile_ctl[a] = make_int4(-1, 0, 0, 0);
+                    mbar_arrive_n(b_accf + 8 * a, 2);
+                }
+            }
+            umma_commit(b_fin);                            // every MMA issued has completed
+            if (!mbar_wait_cycles(b_fin, 0)) *abort_f = 1;
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (TMEM lanes 0-127) ----------------
+        const int row = warp * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        for (int t = 0;; ++t) {
+            const int a = t & 1;
+            if (!mbar_wait_ab(b_accf + 8 * a, (t >> 1) & 1, abort_f)) break;
+            const int4 info = tile_ctl[a];
+            if (info.x < 0) break;
+            tc_fence_after();
+            const uint32_t d = tmem + lane_base + a * MLP_H;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v[16];
+                tmem_ld16(d + q * 16, v);
+                uint32_t pk[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int cc = q * 16 + 2 * e;
+                    pk[e] = pack_bf16(fmaxf(v[2 * e] + ms.b1[cc], 0.f), fmaxf(v[2 * e + 1] + ms.b1[cc + 1], 0.f));
+                }
+                tmem_st8(tmem + lane_base + P::TM_H + q * 8, pk);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_h);
+            if (!mbar_wait_ab(b_l2, t & 1, abort_f)) break;
+            tc_fence_after();
+            float z = ms.b3;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v[16];
+                tmem_ld16(d + q * 16, v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) z += fmaxf(v[e] + ms.b2[q * 16 + e], 0.f) * ms.w3[q * 16 + e];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_acce + 8 * a);
+            // the row's band cell, in-domain test, flag
+            const int slot = info.x, zb0 = info.y, r = info.z * M + row;
+            const bool inb = r < P::CELLS;
+            int bx, by, bz;
+            P::cell(inb ? r : P::CELLS - 1, bx, by, bz);
+            const int lc[3] = {bx - 1, D >= 2 ? by - 1 : 0, D == 3 ? zb0 + bz : 0};
+            const int lev = g.level[slot];
+            bool indom = inb;
+#pragma unroll
+            for (int dd = 0; dd < D; ++dd) {
+                if (g.periodic[dd]) continue;
+                const int Gd = g.coord[slot * 3 + dd] * N + lc[dd];
+                indom = indom && Gd >= 0 && Gd < g.ext[lev][dd] * N;
+            }
+            const bool m = indom && z > 0.f;
+            if (__any_sync(0xffffffffu, m) && lane == 0) atomicOr(&anyflag[slot], 1);
+            if constexpr (STATS) {
+                unsigned long long cnt[4] = {0, 0, 0, 0};
+                if (indom) {
+                    const bool pf = plain_flag_cell<T, D, N>(g, U, slot, lc);
+                    cnt[pf ? (m ? 0 : 2) : (m ? 1 : 3)] += 1;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    unsigned long long v = cnt[q];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0 && v) atomicAdd(&stats[q], v);
+                }
+            }
+        }
     }
-    tc_teardown(st);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, P::TMEM_COLS);
+    if (threadIdx.x == 0 && *abort_f) atomicOr(&g.time->err, ERR_TIMEOUT);
 }
 
 template <typename T, int D, int N>
 static cudaError_t flag_mlp_launch(const Grid& g, const T* U, const float* w, int* anyflag,
                                    unsigned long long* stats, int grid, cudaStream_t s) {
     constexpr size_t smem = mlp_flag_smem<D, N>();
-    k_flag_mlp<T, D, N><<<grid, MlpBand<D, N>::NTH, smem, s>>>(g, U, w, anyflag, stats);
+    if (stats) k_flag_mlp<T, D, N, true><<<grid, MlpBand<D, N>::NTH, smem, s>>>(g, U, w, anyflag, stats);
+    else k_flag_mlp<T, D, N, false><<<grid, MlpBand<D, N>::NTH, smem, s>>>(g, U, w, anyflag, stats);
     return cudaGetLastError();
 }
 
 template <typename T, int D, int N>
 static cudaError_t flag_mlp_prepare() {
     constexpr size_t smem = mlp_flag_smem<D, N>();
-    return cudaFuncSetAttribute(k_flag_mlp<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_flag_mlp<T, D, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_flag_mlp<T, D, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T>
 cudaError_t Kernels<T>::flag_mlp(const Grid& g, const T* U, const float* w, int* anyflag, int grid,
                                  cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(anyflag, 0, sizeof(int) * (size_t)g.cap, s);
+    // per-slot flags and, after them, the work-item counter
+    cudaError_t e = cudaMemsetAsync(anyflag, 0, sizeof(int) * ((size_t)g.cap + 1), s);
     if (e != cudaSuccess) return e;
     AMR_DISPATCH(g, return (flag_mlp_launch<T, D, N>(g, U, w, anyflag, nullptr, grid, s)));
     return cudaSuccess;
@@ -299,9 +581,10 @@ cudaError_t Kernels<T>::flag_mlp(const Grid& g, const T* U, const float* w, int*
 template <typename T>
 cudaError_t Kernels<T>::flag_stats(const Grid& g, const T* U, const float* w, unsigned long long* counts,
                                    int grid, cudaStream_t s) {
-    // the per-patch flags land in a scratch area after the four counters
+    // the per-patch flags and the work-item counter land in a scratch area
+    // after the four counters
     int* scratch = reinterpret_cast<int*>(counts + 4);
-    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * (size_t)g.cap, s);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * ((size_t)g.cap + 1), s);
     if (e != cudaSuccess) return e;
     AMR_DISPATCH(g, return (flag_mlp_launch<T, D, N>(g, U, w, scratch, counts, grid, s)));
     return cudaSuccess;

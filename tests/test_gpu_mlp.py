@@ -158,3 +158,75 @@ def test_fused_flags_agree_with_oracle_flagger():
     counts = g.flag_stats()
     assert counts.sum() > 0
     g.close()
+
+
+def oracle_cell_counts(r, wf, margin):
+    """Per-cell agreement of the network with the plain sensor over the
+    in-domain band cells [-1, N]^d of every leaf: (TP, FP, FN, TN), and the
+    number of cells whose logit lies within `margin` of zero. The network is
+    the oracle's, evaluated in FP64 on the BF16-rounded weights, features and
+    hidden activations the tensor-core kernel uses."""
+    from oracle import mlp
+    dim = r.dim
+    q = mlp.unflatten(wf.astype(np.float64), mlp.k_in(dim))
+    r.fill_ghosts(r.U, r.t)
+    offs = mlp.stencil_offsets(dim)
+    c0 = offs.index((0, 0, 0))
+    cnt = np.zeros(4, dtype=np.int64)
+    near = 0
+    for k in r.mesh.canonical():
+        if not r.mesh.is_leaf(k):
+            continue
+        R, Us, P, cells = mlp.cell_stencils(r, k)
+        X = mlp.features(R, Us, P, r.gamma)
+        h1 = bf16(np.maximum(bf16(X) @ bf16(q['W1']).T + q['b1'], 0.0))
+        z = np.maximum(h1 @ bf16(q['W2']).T + q['b2'], 0.0) @ q['W3'][0] + q['b3'][0]
+        plain = np.zeros(len(z), dtype=bool)
+        for phi, th in ((R, r.w['theta_rho']), (P, r.w['theta_p'])):
+            for d in range(dim):
+                e = [0, 0, 0]
+                e[d] = 1
+                ip, im = offs.index(tuple(e)), offs.index(tuple(-x for x in e))
+                plain |= np.abs(phi[:, ip] - phi[:, im]) > th * (phi[:, ip] + 2.0 * phi[:, c0] + phi[:, im])
+        ok = np.ones(len(z), dtype=bool)
+        for d in range(dim):
+            if r.periodic[d]:
+                continue
+            gi = k[1][d] * r.N + cells[:, d]
+            ok &= (gi >= 0) & (gi < r.mesh.extent(k[0])[d] * r.N)
+        m = z > 0.0
+        cnt += [np.sum(ok & plain & m), np.sum(ok & ~plain & m), np.sum(ok & plain & ~m), np.sum(ok & ~plain & ~m)]
+        near += int(np.sum(ok & (np.abs(z) < margin)))
+    return cnt, near
+
+
+@pytest.mark.parametrize('name,base,patch', [('sod', (64, 1, 1), 16), ('shu_osher', (64, 1, 1), 8),
+                                             ('riemann2d', (32, 32, 1), 8), ('riemann2d', (32, 32, 1), 16),
+                                             ('blast3d', (16, 16, 16), 8), ('blast3d', (16, 16, 16), 16)])
+def test_fused_cell_counts_match_oracle(name, base, patch):
+    # every band cell's learned decision (fused kernel: features in shared
+    # memory, BF16 operands in tensor memory, row <-> cell maps of the
+    # producer and epilogue roles) against the FP64 oracle network, cell by
+    # cell through the agreement counts with the plain sensor; FP64 state so
+    # that the plain flags coincide bit for bit
+    import os
+    from oracle.amr import Oracle
+    from paper_2508_05020_gb300.amr import AMR
+    w = workload(name, base_cells=base, patch=patch, levels=2)
+    dim = w['dim']
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    wf = np.load(os.path.join(here, 'paper_2508_05020_gb300', 'weights', 'indicator_d%d.npy' % dim)).astype(np.float32)
+    r = Oracle(w)
+    ref, near = oracle_cell_counts(r, wf, margin=0.02)
+    assert ref[0] + ref[1] > 0 and ref[2] + ref[3] > 0
+    g = AMR(w, precision=64, flagger='mlp', mlp_weights=wf)
+    keys = r.mesh.canonical()
+    shape = (w['dim'] + 2,) + (patch,) * dim
+    g.set_state(np.array([k[0] for k in keys]), np.array([list(k[1][:dim]) for k in keys]),
+                np.stack([r.U[k][r.inner()].reshape(shape) for k in keys]), t=r.t)
+    got = g.flag_stats()
+    g.close()
+    # plain positives and negatives are the same cells on both sides
+    assert got[0] + got[2] == ref[0] + ref[2] and got[1] + got[3] == ref[1] + ref[3], (got, ref)
+    # learned decisions may differ only where the logit is within the rounding margin
+    assert np.all(np.abs(got - ref) <= near), (got, ref, near)
