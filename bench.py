@@ -32,6 +32,23 @@ UNIT = 'cell-updates/s'
 PEAKS_FILE = os.path.join(ROOT, 'MEASURED_PEAKS.json')
 FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 
+# DRAM bytes (read + write) of one k_rhs launch (SSP-RK3 stage 1, 1536 patches) from the ncu capture
+# summarised in profiles/k_rhs_blast3d_128_fp32.md, valid while the kernel sources hash as they did then
+RHS_TRAFFIC = {'bytes': 452502272 + 170149120, 'workload': 'blast3d', 'base': 128,
+               'sources': {'paper_2508_05020_gb300/csrc/amr_kernels.cuh': 'f6596d8592ca8f4f',
+                           'paper_2508_05020_gb300/csrc/amr_launch.cuh': '187a014027af0415'}}
+
+
+def rhs_traffic(workload_name, base):
+    import hashlib
+    if workload_name != RHS_TRAFFIC['workload'] or base not in (0, RHS_TRAFFIC['base']):
+        return None
+    for f, h in RHS_TRAFFIC['sources'].items():
+        with open(os.path.join(ROOT, f), 'rb') as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != h:
+                return None
+    return RHS_TRAFFIC['bytes']
+
 
 def load_json(path, default):
     try:
@@ -57,7 +74,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(['nvidia-smi', '-i', self.gpu, '--query-gpu=' + self.QUERY,
-                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                          '--format=csv,noheader,nounits', '-lms', '50'],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -159,17 +176,19 @@ def rhs_flops_per_launch(amr, w, flops):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
-    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--steps', type=int, default=40)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--workload', default='blast3d')
     ap.add_argument('--base', type=int, default=0, help='override base cells per dimension')
     ap.add_argument('--precision', type=int, default=32)
-    ap.add_argument('--flagger', default='plain', choices=['plain', 'mlp'])
+    ap.add_argument('--flagger', default='mlp', choices=['plain', 'mlp'])
     ap.add_argument('--weights', default=None, help='float32 .npy weights of the learned indicator')
     ap.add_argument('--max-patches', type=int, default=0, help='pool capacity (0: every level fully refined)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--no-compare', action='store_true',
+                    help='skip the plain FP64 per-patch path and the L1(rho) comparison')
     args = ap.parse_args()
 
     rank = int(os.environ.get('RANK', '0'))
@@ -253,7 +272,8 @@ def main():
         achieved = float(np.mean(flops_rhs)) / (avg_ms / 1000.0) / 1e12
         roof = {'bound': 'alu', 'kernel': 'k_rhs (fused WENO5 + Rusanov + SSP-RK3 stage)',
                 'achieved': achieved, 'peak': fp32_peak, 'unit': 'TFLOP/s', 'frac': achieved / fp32_peak,
-                'traffic': None, 'avg_launch_ms': avg_ms,
+                'traffic': rhs_traffic(args.workload, args.base), 'traffic_unit': 'bytes per launch (stage 1)',
+                'avg_launch_ms': avg_ms,
                 'peak_basis': 'FP32 ALU: 152 SMs x 128 lanes x 2 FLOP x %.0f MHz' % sm_max}
 
     line = {'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
@@ -270,17 +290,86 @@ def main():
             'phase_ms_per_step': dict(zip(AMR.TIMING_SLOTS, [float(x) / args.steps for x in kinds])),
             'wall_s': wall}
 
+    if args.flagger == 'mlp':
+        c = amr.flag_stats()                      # learned vs plain sensor on the final state, per band cell
+        line['learned_indicator'] = {'tp': int(c[0]), 'fp': int(c[1]), 'fn': int(c[2]), 'tn': int(c[3]),
+                                     'recall': float(c[0] / max(1, c[0] + c[2])),
+                                     'precision': float(c[0] / max(1, c[0] + c[1])),
+                                     'state': 'after the timed steps'}
+    amr.close()
+    if rank == 0 and not args.no_compare:
+        line['compare'] = compare_fp64_plain(AMR, w, args, fe, weights, value)
     if rank == 0 and not args.no_e2e:
         line['e2e'] = e2e_measure(AMR, w, args, fe, weights)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, desc = oracle_sample(1)
         line['cpu_baseline'] = {'value': v, 'unit': UNIT, 'cores': 1, 'kind': 'oracle', 'sample': desc}
-    amr.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def level0_rho(amr):
+    _, x = amr.get_level(0)
+    return x[:, 0]
+
+
+def compare_fp64_plain(AMR, w, args, fe, weights, value):
+    """The plain per-patch FP64 GPU path beside the batched one: its
+    throughput on the same workload (one launch per patch and kernel class,
+    plain sensor, FP64 fields), and L1(rho) on level 0 (the conservative
+    average of the whole hierarchy) of the batched FP32 runs, with learned and
+    with plain flags, against it after the same steps with the same dt."""
+    import numpy as np
+    import torch
+    steps = max(2, min(args.steps, 5))
+    ref = AMR(w, precision=64, flagger='plain', mode='per_patch')
+    dts = []
+    for _ in range(1):                             # warm-up (launch paths, allocator)
+        dts.append(ref.step(sync=True))
+        ref.regrid()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dts.append(ref.step(sync=True))
+        ref.regrid()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    rho64 = level0_rho(ref)
+    ref.close()
+    out = {'plain_fp64_per_patch': {'value': fe * steps / el, 'unit': UNIT, 'ms_per_step': 1000.0 * el / steps,
+                                    'steps': steps, 'timing': 'host wall clock around steps + regrids (dt read '
+                                    'back every step)'},
+           'speedup_batched_fp32_learned': value / (fe * steps / el)}
+    # the batched FP64 plain path, for the share of the gain that batching alone gives
+    b64 = AMR(w, precision=64, flagger='plain')
+    b64.step(sync=True)
+    b64.regrid()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b64.step(sync=False)
+        b64.regrid()
+    torch.cuda.synchronize()
+    el64 = time.perf_counter() - t0
+    b64.close()
+    out['plain_fp64_batched'] = {'value': fe * steps / el64, 'unit': UNIT, 'ms_per_step': 1000.0 * el64 / steps,
+                                 'steps': steps, 'timing': 'host wall clock around steps + regrids'}
+    l1 = {}
+    for name, prec, flagger in (('fp32_learned', 32, 'mlp'), ('fp32_plain', 32, 'plain'), ('fp64_batched_plain', 64, 'plain')):
+        a = AMR(w, precision=prec, flagger=flagger, mlp_weights=weights if flagger == 'mlp' else None)
+        for dt in dts:
+            a.step(dt=dt)
+            a.regrid()
+        r = level0_rho(a)
+        a.close()
+        l1[name] = float(np.sum(np.abs(r - rho64)) / np.sum(np.abs(rho64)))
+    out['l1_rho_vs_plain_fp64'] = l1
+    out['l1_rho_note'] = ('relative L1 of rho on level 0 after %d steps (t = %.4g) with the per-patch FP64 '
+                          "plain run's dt sequence" % (len(dts), float(sum(dts))))
+    return out
 
 
 def e2e_measure(AMR, w, args, fe, weights=None):

@@ -167,8 +167,9 @@ int amr_flag_stats(amr_ctx* ctx, long long counts[4]);
 int amr_harvest(amr_ctx* ctx, long* n, double* samples, uint8_t* labels);
 
 /* Per-class device timing of the batched step, for profiling: enable (1) or
- * disable (0) CUDA events around each kernel class. While enabled, the step
- * is issued launch by launch instead of through the captured CUDA graph.
+ * disable (0) CUDA events around each kernel class. The step is still issued
+ * through its captured CUDA graph (the events are event-record nodes of it),
+ * or launch by launch when the context was created without graphs.
  * amr_get_timing synchronises and returns AMR_TIMING_SLOTS milliseconds.
  * Of the last step (CUDA events): ms[0] ghost fill, [1] fused RHS + stage,
  * [2] reflux, [3] restriction, [4] CFL reduction (0 if the step had a given

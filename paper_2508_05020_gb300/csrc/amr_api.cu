@@ -67,8 +67,10 @@ struct amr_ctx {
     // graph
     cudaGraphExec_t graph_cfl = nullptr, graph_fixed = nullptr;
     long long graph_kernels_cfl = 0, graph_kernels_fixed = 0;
-    // per-class CUDA-event timing of the last step (ghost, rhs, reflux, restrict, cfl)
+    // per-class CUDA-event timing of the last step (ghost, rhs, reflux, restrict, cfl);
+    // inside a graph capture the events become external event-record nodes
     bool timing = false;
+    bool capturing = false;
     cudaEvent_t ev[3][5] = {};
     cudaEvent_t ev_cfl[2] = {};
     cudaEvent_t ev_rg[3] = {};            // regrid: before the ghost fill, before / after the flag kernel
@@ -310,7 +312,11 @@ template <typename T>
 int enqueue_step(amr_ctx* c, bool with_cfl, long long* nk) {
     const Grid& g = c->grid;
     long long k = 0;
-    auto mark = [&](cudaEvent_t e) { return c->timing ? cudaEventRecord(e, c->stream) : cudaSuccess; };
+    auto mark = [&](cudaEvent_t e) {
+        if (!c->timing) return cudaSuccess;
+        return c->capturing ? cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal)
+                            : cudaEventRecord(e, c->stream);
+    };
     if (with_cfl) {
         CK(mark(c->ev_cfl[0]), "event");
         CK(Kernels<T>::cfl(g, St<T>(c, 0), grid_size(c, 8), c->stream, -1), "cfl");
@@ -420,13 +426,15 @@ int step_impl(amr_ctx* c, double dt, double* dt_used) {
     if (c->mode == AMR_MODE_PER_PATCH) {
         int r = per_patch_step<T>(c, with_cfl);
         if (r) return r;
-    } else if (c->use_graph && !c->timing) {
+    } else if (c->use_graph) {
         cudaGraphExec_t& ex = with_cfl ? c->graph_cfl : c->graph_fixed;
         long long& nk = with_cfl ? c->graph_kernels_cfl : c->graph_kernels_fixed;
         if (!ex) {
             cudaGraph_t gr;
             CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            c->capturing = true;
             int r = enqueue_step<T>(c, with_cfl, &nk);
+            c->capturing = false;
             cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
             if (r) return r;
             if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
@@ -1034,8 +1042,10 @@ int amr_set_timing(amr_ctx* c, int enable) {
         for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&c->ev_rg[i]), "event");
         c->regrid_timed = false;
     }
-    // timed steps are issued launch by launch (events around each kernel
-    // class); the captured graphs are used again once timing is off
+    // the captured step graphs carry the event-record nodes or not: capture again
+    if (c->graph_cfl) cudaGraphExecDestroy(c->graph_cfl);
+    if (c->graph_fixed) cudaGraphExecDestroy(c->graph_fixed);
+    c->graph_cfl = c->graph_fixed = nullptr;
     c->timing = en;
     return AMR_OK;
 }

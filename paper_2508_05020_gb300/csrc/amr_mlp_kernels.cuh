@@ -87,8 +87,9 @@ __device__ bool plain_flag_cell(const Grid& g, const T* U, int slot, const int* 
 // ---------------------------------------------------------------------------
 // K10: learned indicator on the band [-1, N]^d of every leaf patch. A work
 // item is a leaf patch (1D/2D) or a slab of DZ band planes of it (3D); items
-// are taken from a global counter in patch-major order, and items of a patch
-// that is already flagged are skipped. Band cells are evaluated 128 at a time
+// are taken from a global counter in slab-major order, items of a patch that
+// is already flagged are skipped, and the next item's state is prefetched into
+// L2 while the current one is evaluated. Band cells are evaluated 128 at a time
 // (a tile, one row per TMEM lane). Inside the kernel the K axis is ordered by
 // stencil plane (3D: the offset oz; 1D/2D: a single plane), then field, then
 // point of the plane, each plane padded to PK columns; a K chunk is one plane.
@@ -243,7 +244,7 @@ template <int D, int N> struct MlpFlagLayout {
     static constexpr size_t BARS = CTL + sizeof(int4) * (P::NS + 2);
     // full[NS], empty[NS], acc_full[2], acc_empty[2], h_full, l2_full, fin
     static constexpr int NBAR = 2 * P::NS + 7;
-    static constexpr size_t MISC = BARS + sizeof(uint64_t) * NBAR;                // tmem base, abort, item
+    static constexpr size_t MISC = BARS + sizeof(uint64_t) * NBAR;                // tmem base, abort, items
     static constexpr size_t TOTAL = MISC + 16;
 };
 
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
     int4* tile_ctl = stage_ctl + NS;
     uint32_t* misc = reinterpret_cast<uint32_t*>(base + Lay::MISC);
     volatile int* abort_f = reinterpret_cast<volatile int*>(misc + 1);
-    volatile int* s_item = reinterpret_cast<volatile int*>(misc + 2);
+    volatile int* s_item = reinterpret_cast<volatile int*>(misc + 2);      // current, next item
     const uint32_t b_full = smem_u32(base + Lay::BARS), b_empty = b_full + 8 * NS, b_accf = b_empty + 8 * NS;
     const uint32_t b_acce = b_accf + 16, b_h = b_acce + 16, b_l2 = b_h + 8, b_fin = b_l2 + 8;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -307,25 +308,33 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
         const int frow = (warp & 3) * 32 + lane, sg = (warp - P::PROD_WARP0) >> 2;
         const uint32_t tm_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + P::TM_RING + sg * PL::SPG * 8;
         const T gm1 = T(g.gamma) - T(1);
-        int s = 0;
+        const int npatch = g.counts[1];
+        // items are slab-major (slab = item / npatch): the slabs of a patch are
+        // far apart in the order, so a patch flagged by an earlier slab is
+        // seen as flagged when its later slabs come up and they are skipped
+        auto grab = [&]() -> int {
+            for (;;) {
+                const int it = atomicAdd(counter, 1);
+                if (it >= total || *abort_f) return -1;
+                if constexpr (STATS) return it;
+                if (!*((volatile int*)&anyflag[g.leaf_list[it % npatch]])) return it;
+            }
+        };
+        int s = 0, nxt = -2;                               // nxt: the item prefetched (-2: none taken yet)
         uint32_t ph = 0;                                   // ring position and pass parity
         for (;;) {
             producer_sync(P::NPROD);                       // the previous item's primitives are no longer read
             if (ptid == 0) {
-                int it;
-                for (;;) {
-                    it = atomicAdd(counter, 1);
-                    if (it >= total || *abort_f) {
-                        it = -1;
-                        break;
-                    }
-                    if constexpr (STATS) break;
-                    if (!*((volatile int*)&anyflag[g.leaf_list[it / P::NSLAB]])) break;
+                int it = nxt == -2 ? grab() : nxt;
+                if constexpr (!STATS) {                    // flagged since it was taken: skip it
+                    if (it >= 0 && *((volatile int*)&anyflag[g.leaf_list[it % npatch]])) it = grab();
                 }
-                *s_item = it;
+                s_item[0] = it;
+                s_item[1] = it >= 0 ? grab() : -1;
             }
             producer_sync(P::NPROD);
-            const int item = *s_item;
+            const int item = s_item[0];
+            nxt = s_item[1];
             if (item < 0) {                                // end record in the next chunk buffer
                 mbar_wait_ab(b_empty + 8 * s, ph ^ 1, abort_f);
                 if (ptid == 0) stage_ctl[s] = make_int4(-1, 0, 0, 0);
@@ -333,7 +342,19 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
                 if (lane == 0) mbar_arrive(b_full + 8 * s);
                 break;
             }
-            const int pi = item / P::NSLAB, slab = item - pi * P::NSLAB;
+            if (nxt >= 0) {                                // the next item's state into L2 meanwhile
+                const int nslot = g.leaf_list[nxt % npatch], nslab = nxt / npatch;
+                const int nz0 = D == 3 ? nslab * P::DZ - 3 + G : 0;
+                constexpr int LINE_ELEMS = 128 / sizeof(T);
+                const long long span = (long long)P::PZ * g.SY * g.SX;
+                const int lines = (int)((span + LINE_ELEMS - 1) / LINE_ELEMS);
+                for (int i = ptid; i < F * lines; i += P::NPROD) {
+                    const int v = i / lines, ln = i - v * lines;
+                    const T* a = U + slot_index(g, nslot, v, nz0, 0, 0) + (long long)ln * LINE_ELEMS;
+                    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
+                }
+            }
+            const int pi = item % npatch, slab = item / npatch;
             const int slot = g.leaf_list[pi];
             const int zb0 = D == 3 ? slab * P::DZ - 1 : 0;  // first band plane (local z)
             // primitives of the slab and its halo: local z in [zb0 - 2, zb0 + DZ + 2),
