@@ -187,6 +187,7 @@ def main():
     ap.add_argument('--max-patches', type=int, default=0, help='pool capacity (0: every level fully refined)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--no-autotune', action='store_true', help='default launch parameters instead of tuned ones')
     ap.add_argument('--no-compare', action='store_true',
                     help='skip the plain FP64 per-patch path and the L1(rho) comparison')
     args = ap.parse_args()
@@ -215,7 +216,9 @@ def main():
     if args.flagger == 'mlp':
         path = args.weights or os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights', 'indicator_d%d.npy' % w['dim'])
         weights = np.load(path).astype(np.float32)
-    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights, max_patches=args.max_patches)
+    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights, max_patches=args.max_patches,
+              autotune=not args.no_autotune)
+    tuned, tuned_ms = amr.tuning()
     stream = amr._keep[1]
     amr.set_timing(True)
 
@@ -285,7 +288,9 @@ def main():
                 w['dim'], args.precision, args.flagger),
                 'fine_equivalent_cells': fe, 'patches_per_level': [int(x) for x in ppl],
                 'l2': 'inputs larger than L2 (state arrays of several GB)',
-                'parallelism': 'replicas (dp%d, no data-path collective)' % world},
+                'parallelism': 'replicas (dp%d, no data-path collective)' % world,
+                'launch_parameters': tuned, 'autotuned': not args.no_autotune,
+                'cells_per_step': cell_counts(w, ppl)},
             'clocks': clk, 'gpu_launches': int(k1 - k0), 'roofline': roof,
             'phase_ms_per_step': dict(zip(AMR.TIMING_SLOTS, [float(x) / args.steps for x in kinds])),
             'wall_s': wall}
@@ -309,6 +314,15 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def cell_counts(w, ppl):
+    """Cells one step updates: every patch of every level (and, of those, the leaves
+    need the learned or plain flags), against the fine-equivalent count."""
+    n = w['patch'] ** w['dim']
+    total = int(sum(ppl)) * n
+    return {'all_patches': total, 'fine_equivalent': int(fine_equivalent_cells(w)),
+            'stage_updates_per_step': 3 * total}
 
 
 def level0_rho(amr):
@@ -344,7 +358,7 @@ def compare_fp64_plain(AMR, w, args, fe, weights, value):
                                     'back every step)'},
            'speedup_batched_fp32_learned': value / (fe * steps / el)}
     # the batched FP64 plain path, for the share of the gain that batching alone gives
-    b64 = AMR(w, precision=64, flagger='plain')
+    b64 = AMR(w, precision=64, flagger='plain', autotune=True)
     b64.step(sync=True)
     b64.regrid()
     torch.cuda.synchronize()

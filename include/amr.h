@@ -84,8 +84,9 @@ typedef struct {
 /* Options. Zero-initialise and set what you need; amr_default_options fills
  * the defaults (FP64, CFL 0.5, plain flags, thresholds 0.05, batched). */
 typedef struct {
-    int precision;        /* 64 (FP64 storage and arithmetic) or 32 (FP32 storage and
-                             stencil arithmetic; FP64 restriction sums, CFL and flag tests) */
+    int precision;        /* 64 (FP64 storage and arithmetic) or 32 (FP32 storage, stencil
+                             arithmetic, CFL and flag tests; FP64 restriction and conservation
+                             sums and the CFL maximum) */
     double cfl;           /* CFL number of the step (Sec. 3.1: c sets the step size) */
     double t_end;         /* > 0: the step is clipped so t never exceeds t_end */
     int flagger;          /* AMR_FLAG_PLAIN or AMR_FLAG_MLP */
@@ -104,7 +105,21 @@ typedef struct {
                                   at init; NULL: the initial hierarchy uses the plain sensor and
                                   amr_set_mlp must precede the first amr_regrid */
     long mlp_n_weights;
+    int autotune;         /* 1: amr_init ends with amr_autotune on the initial hierarchy */
 } amr_options_t;
+
+/* Launch parameters of the batched step (amr_get_tuning), in this order:
+ * CTAs per SM of the ghost fill, ghost cells per ghost-fill work item, CTAs per
+ * SM of the fused RHS, the reflux, the restriction, the CFL reduction and the
+ * plain flagging. */
+#define AMR_TUNE_GHOST_GRID 0
+#define AMR_TUNE_GHOST_CHUNK 1
+#define AMR_TUNE_RHS_GRID 2
+#define AMR_TUNE_REFLUX_GRID 3
+#define AMR_TUNE_RESTRICT_GRID 4
+#define AMR_TUNE_CFL_GRID 5
+#define AMR_TUNE_FLAG_GRID 6
+#define AMR_TUNE_N 7
 
 void amr_default_options(amr_options_t* opt);
 
@@ -181,6 +196,20 @@ int amr_harvest(amr_ctx* ctx, long* n, double* samples, uint8_t* labels);
  * slot (0 for the wall-clock slots). */
 #define AMR_TIMING_SLOTS 10
 int amr_set_timing(amr_ctx* ctx, int enable);
+
+/* Autotuner of the batched step's launch parameters (the tile-free kernels'
+ * grids and the ghost-fill work-item size): on the current hierarchy, every
+ * candidate of each kernel class is timed with CUDA events (best of 3 after a
+ * warm-up) on scratch copies of the state (the stage arrays), and the fastest
+ * is kept; the captured step graphs are dropped so that the next step uses
+ * the choice. The state, time, dt and error word are left as they were (the
+ * results of later steps do not depend on the choice). Synchronises. Not in
+ * the paper (its tasks are scheduled by the Legion runtime). */
+int amr_autotune(amr_ctx* ctx);
+/* The launch parameters in use (AMR_TUNE_N ints, AMR_TUNE_* order) and, if
+ * ms is not NULL, the best time in milliseconds the last autotune measured
+ * for each (0: not measured; the two ghost-fill entries share one time). */
+int amr_get_tuning(amr_ctx* ctx, int params[AMR_TUNE_N], float ms[AMR_TUNE_N]);
 int amr_get_timing(amr_ctx* ctx, double ms[AMR_TIMING_SLOTS], int launches[AMR_TIMING_SLOTS]);
 
 /* Counters since amr_init: host-to-device and device-to-host bytes copied,

@@ -38,7 +38,11 @@ class Options(C.Structure):
                 ('max_patches', C.c_int), ('seed', C.c_uint64), ('amp', C.c_double),
                 ('mode', C.c_int), ('use_graph', C.c_int),
                 ('dev_alloc', ALLOC_FN), ('dev_free', FREE_FN), ('user', C.c_void_p),
-                ('stream', C.c_void_p), ('mlp_weights', C.c_void_p), ('mlp_n_weights', C.c_long)]
+                ('stream', C.c_void_p), ('mlp_weights', C.c_void_p), ('mlp_n_weights', C.c_long),
+                ('autotune', C.c_int)]
+
+TUNE_NAMES = ('ghost_ctas_per_sm', 'ghost_cells_per_item', 'rhs_ctas_per_sm', 'reflux_ctas_per_sm',
+              'restrict_ctas_per_sm', 'cfl_ctas_per_sm', 'flag_ctas_per_sm')
 
 
 class AMRError(RuntimeError):
@@ -67,6 +71,8 @@ SIGNATURES = [
     ('amr_get_counters', C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_longlong)]),
     ('amr_set_timing', C.c_int, [C.c_void_p, C.c_int]),
+    ('amr_autotune', C.c_int, [C.c_void_p]),
+    ('amr_get_tuning', C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ('amr_get_timing', C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ('amr_destroy', None, [C.c_void_p]),
     ('amr_last_error', C.c_char_p, [C.c_void_p]),
@@ -125,7 +131,8 @@ class _TorchMemory:
 
 
 def make_options(precision=64, cfl=0.5, t_end=0.0, flagger='plain', theta_rho=0.05, theta_p=0.05,
-                 max_patches=0, seed=0, amp=0.01, mode='batched', use_graph=True, torch_memory=True):
+                 max_patches=0, seed=0, amp=0.01, mode='batched', use_graph=True, torch_memory=True,
+                 autotune=False):
     """Options struct plus the objects that must outlive it."""
     lib = load()
     o = Options()
@@ -141,6 +148,7 @@ def make_options(precision=64, cfl=0.5, t_end=0.0, flagger='plain', theta_rho=0.
     o.amp = amp
     o.mode = MODE[mode]
     o.use_graph = 1 if use_graph else 0
+    o.autotune = 1 if autotune else 0
     keep = []
     if torch_memory:
         import torch
@@ -157,7 +165,7 @@ class AMR:
     """One hierarchy on the current CUDA device (see include/amr.h)."""
 
     def __init__(self, w, precision=64, flagger='plain', mode='batched', use_graph=True,
-                 max_patches=0, torch_memory=True, mlp_weights=None):
+                 max_patches=0, torch_memory=True, mlp_weights=None, autotune=False):
         self.lib = load()
         self.w = dict(w)
         self.dim = w['dim']
@@ -173,7 +181,7 @@ class AMR:
             dom.bc_hi[d] = BC[w['bc'][d][1]]
         self.opt, self._keep = make_options(precision, w['cfl'], w['t_end'], flagger, w['theta_rho'],
                                             w['theta_p'], max_patches, w.get('seed', 0), w.get('amp', 0.01),
-                                            mode, use_graph, torch_memory)
+                                            mode, use_graph, torch_memory, autotune)
         if mlp_weights is not None:
             self._w_host = np.ascontiguousarray(mlp_weights, dtype=np.float32)
             self.opt.mlp_weights = _ptr(self._w_host)
@@ -266,6 +274,16 @@ class AMR:
         a, b, k = C.c_longlong(), C.c_longlong(), C.c_longlong()
         self._check(self.lib.amr_get_counters(self.ctx, C.byref(a), C.byref(b), C.byref(k)))
         return a.value, b.value, k.value
+
+    def autotune(self):
+        self._check(self.lib.amr_autotune(self.ctx))
+
+    def tuning(self):
+        """Launch parameters in use and the autotuner's best times (ms), by TUNE_NAMES."""
+        p = np.zeros(len(TUNE_NAMES), dtype=np.int32)
+        ms = np.zeros(len(TUNE_NAMES), dtype=np.float32)
+        self._check(self.lib.amr_get_tuning(self.ctx, _ptr(p), _ptr(ms)))
+        return dict(zip(TUNE_NAMES, p.tolist())), dict(zip(TUNE_NAMES, ms.tolist()))
 
     def set_timing(self, enable=True):
         self._check(self.lib.amr_set_timing(self.ctx, 1 if enable else 0))

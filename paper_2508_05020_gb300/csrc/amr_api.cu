@@ -29,6 +29,10 @@ struct amr_ctx {
     int base_cells[3] = {1, 1, 1};
     int cap = 0;
     int nsm = 1;
+    // launch parameters of the batched step (CTAs per SM; ghost cells per work
+    // item), the defaults or the autotuner's choice (AMR_TUNE_* order)
+    int tune[AMR_TUNE_N] = {16, 512, 2, 4, 8, 8, 4};
+    float tune_ms[AMR_TUNE_N] = {0, 0, 0, 0, 0, 0, 0};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     // hierarchy
@@ -65,8 +69,12 @@ struct amr_ctx {
     int n_ghost = 0;
     Grid grid{};
     // graph
-    cudaGraphExec_t graph_cfl = nullptr, graph_fixed = nullptr;
-    long long graph_kernels_cfl = 0, graph_kernels_fixed = 0;
+    // captured step graphs by [CFL step][stage-1 ghost fill skipped]
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    long long graph_kernels[2][2] = {{0, 0}, {0, 0}};
+    // the ghosts of U0 hold the values the first stage's ghost fill would
+    // write (a regrid filled them at the current time and left the mesh as it was)
+    bool ghosts_valid = false;
     // per-class CUDA-event timing of the last step (ghost, rhs, reflux, restrict, cfl);
     // inside a graph capture the events become external event-record nodes
     bool timing = false;
@@ -295,13 +303,23 @@ void assign_slots(amr_ctx* c, const std::vector<Key>& created, const std::vector
 
 int grid_size(const amr_ctx* c, int per_sm) { return c->nsm * per_sm; }
 
+void drop_graphs(amr_ctx* c) {
+    for (auto& row : c->graph)
+        for (auto& ex : row) {
+            if (ex) cudaGraphExecDestroy(ex);
+            ex = nullptr;
+        }
+}
+
 template <typename T>
 T* St(amr_ctx* c, int i) { return reinterpret_cast<T*>(c->U[i]); }
 
 template <typename T>
 int fill_all_levels(amr_ctx* c, T* U, double tfrac) {
     for (int l = 0; l < c->L; ++l) {
-        CK(Kernels<T>::ghost_fill(c->grid, U, l, tfrac, grid_size(c, 16), c->stream, -1), "ghost fill");
+        CK(Kernels<T>::ghost_fill(c->grid, U, l, tfrac, grid_size(c, c->tune[AMR_TUNE_GHOST_GRID]), c->stream, -1,
+                                  c->tune[AMR_TUNE_GHOST_CHUNK]),
+           "ghost fill");
         ++c->kernels;
     }
     return AMR_OK;
@@ -309,7 +327,7 @@ int fill_all_levels(amr_ctx* c, T* U, double tfrac) {
 
 // Enqueue one SSP-RK3 step of the batched mode (optionally with the CFL step).
 template <typename T>
-int enqueue_step(amr_ctx* c, bool with_cfl, long long* nk) {
+int enqueue_step(amr_ctx* c, bool with_cfl, bool skip_fill0, long long* nk) {
     const Grid& g = c->grid;
     long long k = 0;
     auto mark = [&](cudaEvent_t e) {
@@ -319,7 +337,7 @@ int enqueue_step(amr_ctx* c, bool with_cfl, long long* nk) {
     };
     if (with_cfl) {
         CK(mark(c->ev_cfl[0]), "event");
-        CK(Kernels<T>::cfl(g, St<T>(c, 0), grid_size(c, 8), c->stream, -1), "cfl");
+        CK(Kernels<T>::cfl(g, St<T>(c, 0), grid_size(c, c->tune[AMR_TUNE_CFL_GRID]), c->stream, -1), "cfl");
         CK(launch_finalize_dt(g, c->stream), "finalize dt");
         CK(mark(c->ev_cfl[1]), "event");
         k += 2;
@@ -329,20 +347,26 @@ int enqueue_step(amr_ctx* c, bool with_cfl, long long* nk) {
         T* src = St<T>(c, s == 0 ? 0 : s);
         T* dst = St<T>(c, s == 0 ? 1 : (s == 1 ? 2 : 0));
         CK(mark(c->ev[s][0]), "event");
-        for (int l = 0; l < c->L; ++l) {
-            CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], grid_size(c, 16), c->stream, -1), "ghost fill");
+        for (int l = 0; l < c->L && !(s == 0 && skip_fill0); ++l) {
+            CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], grid_size(c, c->tune[AMR_TUNE_GHOST_GRID]), c->stream, -1,
+                                      c->tune[AMR_TUNE_GHOST_CHUNK]),
+               "ghost fill");
             ++k;
         }
         CK(mark(c->ev[s][1]), "event");
-        CK(Kernels<T>::rhs_stage(g, src, St<T>(c, 0), dst, reinterpret_cast<T*>(c->faces), s, grid_size(c, 2),
+        CK(Kernels<T>::rhs_stage(g, src, St<T>(c, 0), dst, reinterpret_cast<T*>(c->faces), s,
+                                 grid_size(c, c->tune[AMR_TUNE_RHS_GRID]),
                                  c->stream, -1),
            "rhs stage");
         CK(mark(c->ev[s][2]), "event");
-        CK(Kernels<T>::reflux(g, dst, reinterpret_cast<T*>(c->faces), s, grid_size(c, 4), c->stream, -1), "reflux");
+        CK(Kernels<T>::reflux(g, dst, reinterpret_cast<T*>(c->faces), s, grid_size(c, c->tune[AMR_TUNE_REFLUX_GRID]),
+                              c->stream, -1),
+           "reflux");
         CK(mark(c->ev[s][3]), "event");
         k += 2;
         for (int l = c->L - 1; l >= 1; --l) {
-            CK(Kernels<T>::restrict_level(g, dst, l, grid_size(c, 8), c->stream, -1), "restrict");
+            CK(Kernels<T>::restrict_level(g, dst, l, grid_size(c, c->tune[AMR_TUNE_RESTRICT_GRID]), c->stream, -1),
+               "restrict");
             ++k;
         }
         CK(mark(c->ev[s][4]), "event");
@@ -427,13 +451,14 @@ int step_impl(amr_ctx* c, double dt, double* dt_used) {
         int r = per_patch_step<T>(c, with_cfl);
         if (r) return r;
     } else if (c->use_graph) {
-        cudaGraphExec_t& ex = with_cfl ? c->graph_cfl : c->graph_fixed;
-        long long& nk = with_cfl ? c->graph_kernels_cfl : c->graph_kernels_fixed;
+        const bool skip = c->ghosts_valid;
+        cudaGraphExec_t& ex = c->graph[with_cfl][skip];
+        long long& nk = c->graph_kernels[with_cfl][skip];
         if (!ex) {
             cudaGraph_t gr;
             CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
             c->capturing = true;
-            int r = enqueue_step<T>(c, with_cfl, &nk);
+            int r = enqueue_step<T>(c, with_cfl, skip, &nk);
             c->capturing = false;
             cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
             if (r) return r;
@@ -446,10 +471,11 @@ int step_impl(amr_ctx* c, double dt, double* dt_used) {
         c->kernels += nk;
     } else {
         long long nk = 0;
-        int r = enqueue_step<T>(c, with_cfl, &nk);
+        int r = enqueue_step<T>(c, with_cfl, c->ghosts_valid, &nk);
         if (r) return r;
         c->kernels += nk;
     }
+    c->ghosts_valid = false;                               // U0 has advanced
     if (dt_used) {
         int r = read_time(c);
         if (r) return r;
@@ -473,7 +499,9 @@ int compute_requests(amr_ctx* c, std::vector<Key>& refine, std::vector<Key>& coa
         CK(Kernels<T>::flag_mlp(c->grid, St<T>(c, 0), c->mlp_w, c->anyflag, grid_size(c, 1), c->stream),
            "flag (learned)");
     } else {
-        CK(Kernels<T>::flag_plain(c->grid, St<T>(c, 0), c->anyflag, grid_size(c, 4), c->stream), "flag");
+        CK(Kernels<T>::flag_plain(c->grid, St<T>(c, 0), c->anyflag, grid_size(c, c->tune[AMR_TUNE_FLAG_GRID]),
+                                  c->stream),
+           "flag");
     }
     CK(mark(c->ev_rg[2]), "event");
     CK(launch_requests(c->grid, c->anyflag, c->req_d + 2, c->req_d + 2 + c->cap, c->req_d, c->stream), "requests");
@@ -504,6 +532,7 @@ int regrid_impl(amr_ctx* c, bool resample_ic) {
     const auto t0 = std::chrono::steady_clock::now();
     int r = compute_requests<T>(c, req, cand);
     if (r) return r;
+    c->ghosts_valid = true;                                // filled at the current time for the flags
     const auto t1 = std::chrono::steady_clock::now();
     c->regrid_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
     c->regrid_timed = c->timing;
@@ -516,6 +545,7 @@ int regrid_impl(amr_ctx* c, bool resample_ic) {
     if (created.empty() && deleted.empty()) return AMR_OK;
     if ((long long)m2.patches.size() > c->cap)
         return fail(c, AMR_ERR_POOL, "patch pool capacity exceeded; hierarchy left unchanged");
+    c->ghosts_valid = false;                               // new and removed patches: neighbours' ghosts stale
     c->mesh.patches.swap(m2.patches);
     assign_slots(c, created, deleted);
     const auto t2 = std::chrono::steady_clock::now();
@@ -594,6 +624,7 @@ int set_state_impl(amr_ctx* c, int n, const int* levels, const int* coords, cons
     }
     std::vector<Key> all = c->mesh.canonical();
     assign_slots(c, all, {});
+    c->ghosts_valid = false;
     int r = rebuild_tables(c, {});
     if (r) return r;
     long long ncell = 1;
@@ -637,6 +668,129 @@ bool valid_bc(int b) { return b >= AMR_BC_OUTFLOW && b <= AMR_BC_DMR_TOP; }
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Autotuner of the batched step's launch parameters: each candidate timed
+// with CUDA events (best of 3 after a warm-up) on the stage arrays, which hold
+// a copy of the state; the device time record is saved and put back.
+template <typename T>
+int autotune_impl(amr_ctx* c) {
+    const Grid& g = c->grid;
+    const size_t state_bytes = (size_t)c->cap * g.patch_elems * sizeof(T);
+    T* A = St<T>(c, 1);
+    T* B = St<T>(c, 2);
+    T* faces = reinterpret_cast<T*>(c->faces);
+    CK(cudaMemcpyAsync(A, St<T>(c, 0), state_bytes, cudaMemcpyDeviceToDevice, c->stream), "autotune copy");
+    DevTime saved;
+    CK(cudaMemcpyAsync(&saved, c->time_d, sizeof(DevTime), cudaMemcpyDeviceToHost, c->stream), "autotune");
+    CK(cudaStreamSynchronize(c->stream), "autotune");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "autotune");
+    cudaError_t err = cudaEventCreate(&e1);
+    long long nk = 0;
+    // best-of-3 device time of launch() after one warm-up call
+    auto timed = [&](auto&& launch, float& best) -> cudaError_t {
+        cudaError_t e = launch();
+        if (e != cudaSuccess) return e;
+        best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) return e;
+            if ((e = launch()) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) return e;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+            float ms = 0.f;
+            if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
+            best = ms < best ? ms : best;
+        }
+        return cudaSuccess;
+    };
+    // pick the fastest of `cands` for parameter `slot`: launch(candidate)
+    auto tune_one = [&](int slot, const int* cands, int n, auto&& launch) -> cudaError_t {
+        float bestv = 1e30f;
+        int pick = c->tune[slot];
+        for (int i = 0; i < n; ++i) {
+            float t = 0.f;
+            const cudaError_t e = timed([&]() { return launch(cands[i]); }, t);
+            if (e != cudaSuccess) return e;
+            if (t < bestv) {
+                bestv = t;
+                pick = cands[i];
+            }
+        }
+        c->tune[slot] = pick;
+        c->tune_ms[slot] = bestv;
+        return cudaSuccess;
+    };
+    if (err == cudaSuccess) {                            // ghost fill of every level: grid x work-item size
+        const int grids[] = {4, 8, 16, 32}, chunks[] = {256, 512, 1024, 2048, 4096};
+        float bestv = 1e30f;
+        for (int gr : grids)
+            for (int ch : chunks) {
+                float t = 0.f;
+                err = timed([&]() {
+                    for (int l = 0; l < c->L; ++l) {
+                        const cudaError_t e = Kernels<T>::ghost_fill(g, A, l, 0.0, grid_size(c, gr), c->stream, -1, ch);
+                        ++nk;
+                        if (e != cudaSuccess) return e;
+                    }
+                    return cudaSuccess;
+                }, t);
+                if (err != cudaSuccess) break;
+                if (t < bestv) {
+                    bestv = t;
+                    c->tune[AMR_TUNE_GHOST_GRID] = gr;
+                    c->tune[AMR_TUNE_GHOST_CHUNK] = ch;
+                }
+            }
+        c->tune_ms[AMR_TUNE_GHOST_GRID] = c->tune_ms[AMR_TUNE_GHOST_CHUNK] = bestv;
+    }
+    if (err == cudaSuccess) {                            // fused RHS, stage 1: A -> B
+        const int cands[] = {1, 2, 3, 4};
+        err = tune_one(AMR_TUNE_RHS_GRID, cands, 4, [&](int gr) {
+            ++nk;
+            return Kernels<T>::rhs_stage(g, A, St<T>(c, 0), B, faces, 0, grid_size(c, gr), c->stream, -1);
+        });
+    }
+    if (err == cudaSuccess) {                            // reflux of stage 1 into B
+        const int cands[] = {1, 2, 4, 8, 16};
+        err = tune_one(AMR_TUNE_REFLUX_GRID, cands, 5, [&](int gr) {
+            ++nk;
+            return Kernels<T>::reflux(g, B, faces, 0, grid_size(c, gr), c->stream, -1);
+        });
+    }
+    if (err == cudaSuccess) {                            // restriction of every level of A
+        const int cands[] = {2, 4, 8, 16, 32};
+        err = tune_one(AMR_TUNE_RESTRICT_GRID, cands, 5, [&](int gr) {
+            for (int l = c->L - 1; l >= 1; --l) {
+                ++nk;
+                const cudaError_t e = Kernels<T>::restrict_level(g, A, l, grid_size(c, gr), c->stream, -1);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        });
+    }
+    if (err == cudaSuccess) {                            // CFL reduction over the leaves of A
+        const int cands[] = {2, 4, 8, 16, 32};
+        err = tune_one(AMR_TUNE_CFL_GRID, cands, 5, [&](int gr) {
+            ++nk;
+            return Kernels<T>::cfl(g, A, grid_size(c, gr), c->stream, -1);
+        });
+    }
+    if (err == cudaSuccess) {                            // plain flagging of A (scratch flags)
+        const int cands[] = {1, 2, 4, 8, 16};
+        err = tune_one(AMR_TUNE_FLAG_GRID, cands, 5, [&](int gr) {
+            ++nk;
+            return Kernels<T>::flag_plain(g, A, c->anyflag, grid_size(c, gr), c->stream);
+        });
+    }
+    c->kernels += nk;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(c, err, "autotune");
+    CK(cudaMemcpyAsync(c->time_d, &saved, sizeof(DevTime), cudaMemcpyHostToDevice, c->stream), "autotune");
+    CK(cudaStreamSynchronize(c->stream), "autotune");
+    drop_graphs(c);
+    return AMR_OK;
+}
+
 extern "C" {
 
 void amr_default_options(amr_options_t* opt) {
@@ -871,6 +1025,10 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     ++c->kernels;
     CK(cudaStreamSynchronize(c->stream), "init");
     c->initialising = false;
+    if (c->opt.autotune) {
+        r = c->precision == 64 ? autotune_impl<double>(c) : autotune_impl<float>(c);
+        if (r) return r;
+    }
     return AMR_OK;
 }
 
@@ -1030,6 +1188,20 @@ int amr_harvest(amr_ctx* c, long* n, double* samples, uint8_t* labels) {
     return AMR_OK;
 }
 
+int amr_autotune(amr_ctx* c) {
+    GUARD(c);
+    return c->precision == 64 ? autotune_impl<double>(c) : autotune_impl<float>(c);
+}
+
+int amr_get_tuning(amr_ctx* c, int params[AMR_TUNE_N], float ms[AMR_TUNE_N]) {
+    if (!c || !params) return AMR_ERR_ARG;
+    for (int i = 0; i < AMR_TUNE_N; ++i) {
+        params[i] = c->tune[i];
+        if (ms) ms[i] = c->tune_ms[i];
+    }
+    return AMR_OK;
+}
+
 int amr_set_timing(amr_ctx* c, int enable) {
     GUARD(c);
     const bool en = enable != 0;
@@ -1043,9 +1215,7 @@ int amr_set_timing(amr_ctx* c, int enable) {
         c->regrid_timed = false;
     }
     // the captured step graphs carry the event-record nodes or not: capture again
-    if (c->graph_cfl) cudaGraphExecDestroy(c->graph_cfl);
-    if (c->graph_fixed) cudaGraphExecDestroy(c->graph_fixed);
-    c->graph_cfl = c->graph_fixed = nullptr;
+    drop_graphs(c);
     c->timing = en;
     return AMR_OK;
 }
@@ -1098,8 +1268,7 @@ int amr_get_counters(amr_ctx* c, long long* h2d, long long* d2h, long long* kern
 void amr_destroy(amr_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->graph_cfl) cudaGraphExecDestroy(c->graph_cfl);
-    if (c->graph_fixed) cudaGraphExecDestroy(c->graph_fixed);
+    drop_graphs(c);
     if (c->ev[0][0]) {
         for (int s = 0; s < 3; ++s)
             for (int i = 0; i < 5; ++i) cudaEventDestroy(c->ev[s][i]);

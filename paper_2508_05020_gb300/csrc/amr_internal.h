@@ -82,7 +82,7 @@ struct Kernels {
     // ghost cells of every patch of `level` (same-level copy, prolongation,
     // physical boundaries) at time t + tfrac * dt
     static cudaError_t ghost_fill(const Grid& g, T* U, int level, double tfrac, int grid,
-                                  cudaStream_t s, int one_slot);
+                                  cudaStream_t s, int one_slot, int chunk = 512);
     // RHS + SSP-RK3 stage of every patch (or one patch if one_slot >= 0)
     static cudaError_t rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces,
                                  int stage, int grid, cudaStream_t s, int one_slot);

@@ -97,6 +97,16 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     const T e0 = T(1.0e-6) + b0;
     const T e1 = T(1.0e-6) + b1;
     const T e2 = T(1.0e-6) + b2;
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the normalised weights are unchanged when every alpha_k is
+        // multiplied by e0^2 e1^2 e2^2, which leaves a single division; used
+        // while the products stay far inside the FP32 range
+        const T s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
+        if (fmaxf(s0, fmaxf(s1, s2)) < T(1.0e12)) {
+            const T m0 = T(0.0625) * (s1 * s2), m1 = T(0.625) * (s0 * s2), m2 = T(0.3125) * (s0 * s1);
+            return Num<T>::div(m0 * q0 + m1 * q1 + m2 * q2, m0 + m1 + m2);
+        }
+    }
     const T a0 = Num<T>::div(T(0.0625), e0 * e0);
     const T a1 = Num<T>::div(T(0.625), e1 * e1);
     const T a2 = Num<T>::div(T(0.3125), e2 * e2);
@@ -408,12 +418,13 @@ __device__ void ghost_value(const Grid& g, const T* U, const PatchMeta& m, int* 
 
 // ---------------------------------------------------------------------------
 // K1-K3: ghost fill of every patch of one level. A work item is a patch and a
-// run of 512 of its ghost cells (slot order); the CTA stages the patch's
-// metadata in shared memory once per item.
+// run of `chunk` of its ghost cells (slot order; the size is a launch
+// parameter chosen by the autotuner); the CTA stages the patch's metadata in
+// shared memory once per item.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
-                                               double4 pre, double4 post) {
+                                               double4 pre, double4 post, int chunk) {
     constexpr int NV = D + 2;
     __shared__ PatchMeta m;
     const int lo = g.level_off[level], hi = g.level_off[level + 1];
@@ -421,12 +432,11 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
     const double t = g.time->t + tfrac * g.time->dt;
     const double pr[4] = {pre.x, pre.y, pre.z, pre.w};
     const double po[4] = {post.x, post.y, post.z, post.w};
-    constexpr int CHUNK = 512;                           // ghost cells per work item
-    const int nchunk = (g.n_ghost + CHUNK - 1) / CHUNK;
+    const int nchunk = (g.n_ghost + chunk - 1) / chunk;   // chunk: ghost cells per work item
     for (int item = blockIdx.x; item < npatch * nchunk; item += gridDim.x) {
         const int pi = item / nchunk;
-        const int g0 = (item - pi * nchunk) * CHUNK;
-        const int g1 = min(g0 + CHUNK, g.n_ghost);
+        const int g0 = (item - pi * nchunk) * chunk;
+        const int g1 = min(g0 + chunk, g.n_ghost);
         const int slot = one_slot >= 0 ? one_slot : g.all_list[lo + pi];
         load_meta(g, slot, m);
         for (int gi = g0 + threadIdx.x; gi < g1; gi += blockDim.x) {
@@ -565,14 +575,18 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
             const int ex = d == 0, ey = d == 1, ez = d == 2;
             const int FX = C::CX + ex, FY = C::CY + ey, FZ = C::CZ + ez;
             const int nf = FX * FY * FZ;
+            // f -> (fi, fj, fk) by multiply-high division, exact for f * FX < 2^32
+            const unsigned mFX = 0xFFFFFFFFu / (unsigned)FX + 1u;
+            const unsigned mFY = D == 1 ? 0u : 0xFFFFFFFFu / (unsigned)FY + 1u;   // 1D: FY = FZ = 1
             const int step = d == 0 ? 1 : C::QX;          // x and y pencils stay in one centre plane
             // tangential velocity components in increasing dimension order
             const int t1 = d == 0 ? 1 : 0;
             const int t2 = d == 2 ? 1 : 2;
             for (int f = threadIdx.x; f < nf; f += NTH) {
-                const int fi = f % FX;
-                const int fj = (f / FX) % FY;
-                const int fk = f / (FX * FY);
+                const int q1 = (int)__umulhi((unsigned)f, mFX);
+                const int fk = D == 1 ? 0 : (int)__umulhi((unsigned)q1, mFY);
+                const int fi = f - q1 * FX;
+                const int fj = q1 - fk * FY;
                 // smem index of pencil node 0 (cell index - 3 along d; G = 3)
                 int base = 0;
                 if (d < 2) {
@@ -624,6 +638,7 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
             }
             __syncthreads();
             const T dxd = T(g.dx[lev][d]);
+            const T idx = T(1) / dxd;                        // FP32: multiply by the reciprocal
             const int fstep = d == 0 ? 1 : (d == 1 ? FX : FX * FY);
 #pragma unroll
             for (int n = 0; n < CPT; ++n) {
@@ -636,7 +651,8 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
                     const int fhi = flo + fstep;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        const T dv = Num<T>::div(Fs[v * C::FMAX + fhi] - Fs[v * C::FMAX + flo], dxd);
+                        const T df = Fs[v * C::FMAX + fhi] - Fs[v * C::FMAX + flo];
+                        const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
                         R[n][v] = d == 0 ? -dv : R[n][v] - dv;
                     }
                 }
@@ -745,9 +761,12 @@ __global__ void __launch_bounds__(256) k_reflux(Grid g, T* Uout, const T* __rest
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int one_slot) {
+    // thread <-> coarse cell; the 2^d children of every variable are read
+    // before anything is written (the sums are FP64 and bound by the FP64 pipe)
     constexpr int NV = D + 2;
     constexpr int H = N / 2;
     constexpr int HC = D == 1 ? H : (D == 2 ? H * H : H * H * H);
+    constexpr int NCH = 1 << D;
     const int lo = g.level_off[level], hi = g.level_off[level + 1];
     const int npatch = one_slot >= 0 ? 1 : hi - lo;
     const long long total = (long long)npatch * HC;
@@ -763,20 +782,22 @@ __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int o
             continue;
         }
         const int cx = ci % H, cy = D >= 2 ? (ci / H) % H : 0, cz = D == 3 ? ci / (H * H) : 0;
+        T f[NV][NCH];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {                // child order: z, then y, then x
+                const int ax = k & 1, ay = D >= 2 ? (k >> 1) & 1 : 0, az = D == 3 ? k >> 2 : 0;
+                f[v][k] = U[slot_index(g, slot, v, D == 3 ? 2 * cz + az + G : 0, D >= 2 ? 2 * cy + ay + G : 0,
+                                       2 * cx + ax + G)];
+            }
         const int ox = (g.coord[slot * 3 + 0] & 1) * H, oy = D >= 2 ? (g.coord[slot * 3 + 1] & 1) * H : 0,
                   oz = D == 3 ? (g.coord[slot * 3 + 2] & 1) * H : 0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            double acc = 0.0;
-            bool first = true;
-            for (int az = 0; az < (D == 3 ? 2 : 1); ++az)
-                for (int ay = 0; ay < (D >= 2 ? 2 : 1); ++ay)
-                    for (int ax = 0; ax < 2; ++ax) {
-                        const double val = (double)U[slot_index(g, slot, v, D == 3 ? 2 * cz + az + G : 0,
-                                                                D >= 2 ? 2 * cy + ay + G : 0, 2 * cx + ax + G)];
-                        acc = first ? val : acc + val;
-                        first = false;
-                    }
+            double acc = (double)f[v][0];
+#pragma unroll
+            for (int k = 1; k < NCH; ++k) acc = acc + (double)f[v][k];
             U[slot_index(g, par, v, D == 3 ? oz + cz + G : 0, D >= 2 ? oy + cy + G : 0, ox + cx + G)] =
                 T(acc * scale);
         }

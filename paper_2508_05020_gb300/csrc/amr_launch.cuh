@@ -56,9 +56,10 @@ cudaError_t Kernels<T>::prepare(const Grid& g) {
 
 template <typename T>
 cudaError_t Kernels<T>::ghost_fill(const Grid& g, T* U, int level, double tfrac, int grid, cudaStream_t s,
-                                   int one_slot) {
+                                   int one_slot, int chunk) {
+    if (chunk < 32) return cudaErrorInvalidValue;
     AMR_DISPATCH(g, (k_ghost<T, D, N><<<grid, 256, 0, s>>>(g, U, level, tfrac, one_slot, d4(g.dmr_pre),
-                                                            d4(g.dmr_post))));
+                                                            d4(g.dmr_post), chunk)));
     return cudaGetLastError();
 }
 
