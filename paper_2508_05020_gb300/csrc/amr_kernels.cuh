@@ -811,14 +811,18 @@ __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int o
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
+    // the running maximum is kept in the storage precision (exact: the
+    // maximum of FP32 values converts to the maximum of their FP64 images)
+    // and turned into FP64 once per CTA
     constexpr int NV = D + 2;
     constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
     const int npatch = one_slot >= 0 ? 1 : g.counts[1];
     const long long total = (long long)npatch * NC;
     const T gamma = T(g.gamma);
     const T gm1 = T(g.gamma) - T(1);
-    double lmax = 0.0;
+    T lmax = T(0);
     bool bad = false;
+#pragma unroll 4
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
          it += (long long)gridDim.x * blockDim.x) {
         const int pi = (int)(it / NC);
@@ -837,15 +841,17 @@ __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
         T lam = Num<T>::div(fabs(u[0]) + c, T(g.dx[lev][0]));
 #pragma unroll
         for (int d = 1; d < D; ++d) lam = lam + Num<T>::div(fabs(u[d]) + c, T(g.dx[lev][d]));
-        const double ld = (double)lam;
-        if (!(ld <= 1.0e300)) bad = true;
-        else lmax = fmax(lmax, ld);
+        if (!((double)lam <= 1.0e300)) bad = true;       // FP32: not finite; FP64: out of range
+        else lmax = lmax > lam ? lmax : lam;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const T other = __shfl_xor_sync(0xffffffffu, lmax, o);
+        lmax = lmax > other ? lmax : other;
+    }
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = lmax;
+    if (lane == 0) red[wid] = (double)lmax;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&g.time->err, ERR_NONFINITE);
     if (wid == 0) {
         double m = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
@@ -859,14 +865,22 @@ __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
 // K9 (plain): relative-jump sensor on rho and p over the band [-2, N+1]^d of
 // each leaf patch (in-domain cells): a cell is flagged if for some dimension
 // |phi+ - phi-| > theta (phi+ + 2 phi0 + phi-) for phi in (rho, p) (the
-// relative jump above theta, without the division). rho and p of the whole
-// slot are staged in shared memory once per patch, in the storage precision;
-// per-patch OR by __syncthreads_or.
+// relative jump above theta, without the division). A work item is a patch
+// (1D/2D) or a slab of DZB band planes of it (3D, four slabs); rho and p of
+// the slab and its +-1 planes are staged in shared memory in the storage
+// precision from 16-byte vector loads of the slot rows, and a patch's flag is
+// the OR over its items.
 // ---------------------------------------------------------------------------
 template <int D, int N> struct FlagStage {
     static constexpr int S = N + 2 * G;
-    static constexpr int SX = S, SY = D >= 2 ? S : 1, SZ = D == 3 ? S : 1;
-    static constexpr int NS = SX * SY * SZ;
+    static constexpr int SXP = PatchShape<N>::SX;            // padded x pitch of the slot
+    static constexpr int B = N + 4;                         // band cells per dimension
+    static constexpr int NSLAB = D == 3 ? 4 : 1;
+    static constexpr int DZB = D == 3 ? B / 4 : 1;           // band planes per slab
+    static_assert(D != 3 || B % 4 == 0, "four slabs tile the band");
+    static constexpr int PZ = D == 3 ? DZB + 2 : 1;          // staged planes
+    static constexpr int SY = D >= 2 ? S : 1;
+    static constexpr int NS = PZ * SY * SXP;                 // staged cells per field
 };
 
 template <typename T, int D, int N>
@@ -876,32 +890,52 @@ template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* anyflag) {
     using F = FlagStage<D, N>;
     constexpr int NV = D + 2;
-    constexpr int B = N + 4;
-    constexpr int NB = D == 1 ? B : (D == 2 ? B * B : B * B * B);
+    constexpr int B = F::B;
+    constexpr int NB = D == 1 ? B : (D == 2 ? B * B : B * B * F::DZB);     // band cells per item
+    constexpr int VE = 16 / sizeof(T), NXV = F::SXP / VE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* srho = reinterpret_cast<T*>(smem_raw);
     T* sp = srho + F::NS;
     const int npatch = g.counts[1];
     const T gm1 = T(g.gamma) - T(1);
     const T thr = T(g.theta_rho), thp = T(g.theta_p);
-    for (int pi = blockIdx.x; pi < npatch; pi += gridDim.x) {
+    for (int item = blockIdx.x; item < npatch * F::NSLAB; item += gridDim.x) {
+        const int pi = item / F::NSLAB, slab = item - pi * F::NSLAB;
         const int slot = g.leaf_list[pi];
         const int lev = g.level[slot];
         const int c[3] = {g.coord[slot * 3], g.coord[slot * 3 + 1], g.coord[slot * 3 + 2]};
-        for (int idx = threadIdx.x; idx < F::NS; idx += blockDim.x) {
-            const int x = idx % F::SX, y = (idx / F::SX) % F::SY, z = idx / (F::SX * F::SY);
-            T Uc[NV];
+        const int sz0 = D == 3 ? slab * F::DZB : 0;             // first staged slot plane
+        for (int iv = threadIdx.x; iv < F::PZ * F::SY * NXV; iv += blockDim.x) {
+            const int xv = iv % NXV, y = (iv / NXV) % F::SY, z = iv / (NXV * F::SY);
+            T Uv[NV][VE];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Uc[v] = U[slot_index(g, slot, v, z, y, x)];
-            T rho, u[D], p, Tt;
-            primitives<T, D>(Uc, gm1, rho, u, p, Tt);
-            srho[idx] = rho;
-            sp[idx] = p;
+            for (int v = 0; v < NV; ++v) {
+                const T* src = U + slot_index(g, slot, v, sz0 + z, y, xv * VE);
+                if constexpr (sizeof(T) == 4) {
+                    const float4 q = *reinterpret_cast<const float4*>(src);
+                    Uv[v][0] = q.x; Uv[v][1] = q.y; Uv[v][2] = q.z; Uv[v][3] = q.w;
+                } else {
+                    const double2 q = *reinterpret_cast<const double2*>(src);
+                    Uv[v][0] = q.x; Uv[v][1] = q.y;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < VE; ++e) {
+                T Uc[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Uc[v] = Uv[v][e];
+                T rho, u[D], p, Tt;
+                primitives<T, D>(Uc, gm1, rho, u, p, Tt);
+                const int idx = (z * F::SY + y) * F::SXP + xv * VE + e;
+                srho[idx] = rho;
+                sp[idx] = p;
+            }
         }
         __syncthreads();
         bool any = false;
         for (int bi = threadIdx.x; bi < NB; bi += blockDim.x) {
-            const int l[3] = {bi % B - 2, D >= 2 ? (bi / B) % B - 2 : 0, D == 3 ? bi / (B * B) - 2 : 0};
+            const int l[3] = {bi % B - 2, D >= 2 ? (bi / B) % B - 2 : 0,
+                              D == 3 ? bi / (B * B) - 2 + slab * F::DZB : 0};
             bool indom = true;
 #pragma unroll
             for (int d = 0; d < D; ++d) {
@@ -910,12 +944,12 @@ __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* any
                 indom = indom && Gd >= 0 && Gd < g.ext[lev][d] * N;
             }
             if (!indom) continue;
-            const int i0 = (sc<D>(2, l[2]) * F::SY + sc<D>(1, l[1])) * F::SX + sc<D>(0, l[0]);
+            const int i0 = ((D == 3 ? l[2] + G - sz0 : 0) * F::SY + sc<D>(1, l[1])) * F::SXP + sc<D>(0, l[0]);
             const T r0 = srho[i0], p0 = sp[i0];
             bool f = false;
 #pragma unroll
             for (int d = 0; d < D; ++d) {
-                const int st = d == 0 ? 1 : (d == 1 ? F::SX : F::SX * F::SY);
+                const int st = d == 0 ? 1 : (d == 1 ? F::SXP : F::SXP * F::SY);
                 const T rm = srho[i0 - st], rp = srho[i0 + st];
                 const T pm = sp[i0 - st], pp = sp[i0 + st];
                 f = f || (fabs(rp - rm) > thr * (rp + T(2) * r0 + rm)) || (fabs(pp - pm) > thp * (pp + T(2) * p0 + pm));
@@ -923,7 +957,7 @@ __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* any
             any = any || f;
         }
         const int res = __syncthreads_or(any);
-        if (threadIdx.x == 0) anyflag[slot] = res ? 1 : 0;
+        if (threadIdx.x == 0 && res) atomicOr(&anyflag[slot], 1);
     }
 }
 

@@ -107,6 +107,8 @@ cudaError_t Kernels<T>::prolong_new(const Grid& g, T* U, const int* list, int n,
 
 template <typename T>
 cudaError_t Kernels<T>::flag_plain(const Grid& g, const T* U, int* anyflag, int grid, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(anyflag, 0, sizeof(int) * (size_t)g.cap, s);   // OR over the items
+    if (e != cudaSuccess) return e;
     AMR_DISPATCH(g, (k_flag_plain<T, D, N><<<grid, 256, flag_smem_bytes<T, D, N>(), s>>>(g, U, anyflag)));
     return cudaGetLastError();
 }
