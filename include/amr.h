@@ -138,6 +138,13 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
  * passing NULL avoids a device-to-host synchronisation. */
 int amr_step(amr_ctx* ctx, double dt, double* dt_used);
 
+/* n_steps CFL steps (amr_step with dt <= 0), each followed by amr_regrid when
+ * regrid != 0: the production loop, with no return to the caller between
+ * steps. Stops at the first error and returns it (the steps before it stand);
+ * n_steps < 0 is AMR_ERR_ARG. The only host synchronisation is the regrid's
+ * read-back of the refinement requests. */
+int amr_advance(amr_ctx* ctx, int n_steps, int regrid);
+
 /* Flag (plain sensor or learned indicator), close the requests under R2
  * (Algorithm 1), coarsen by the Sec. 4.3 rule, and fill new patches by
  * limited-linear prolongation from their parents. */

@@ -60,6 +60,7 @@ SIGNATURES = [
                            C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(Options)]),
     ('amr_step', C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     ('amr_regrid', C.c_int, [C.c_void_p]),
+    ('amr_advance', C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     ('amr_get_level', C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p]),
     ('amr_get_diag', C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
     ('amr_set_state', C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
@@ -221,6 +222,10 @@ class AMR:
 
     def regrid(self):
         self._check(self.lib.amr_regrid(self.ctx))
+
+    def advance(self, n_steps, regrid=True):
+        """n_steps CFL steps, each followed by a regrid (amr_advance)."""
+        self._check(self.lib.amr_advance(self.ctx, int(n_steps), 1 if regrid else 0))
 
     def get_level(self, level, data=True):
         n = C.c_int()

@@ -54,7 +54,8 @@ struct amr_ctx {
     int* meta_h = nullptr;                     // pinned mirror
     size_t meta_ints = 0;
     int* anyflag = nullptr;
-    int* req_d = nullptr;                      // [2 + 2 cap]: counts, refine, coarsen
+    int* req_d = nullptr;                      // [3 + 3 cap]: counts, refine, coarsen, rejected candidates
+    int* rej_d = nullptr;                      // req_d + 2 + 2 cap: [count or -1, slots] the host could not coarsen
     int* req_h = nullptr;
     double* cons_partial = nullptr;
     double* cons_d = nullptr;
@@ -75,6 +76,8 @@ struct amr_ctx {
     // the ghosts of U0 hold the values the first stage's ghost fill would
     // write (a regrid filled them at the current time and left the mesh as it was)
     bool ghosts_valid = false;
+    cudaEvent_t ev_req = nullptr;         // end of a regrid's request read-back
+    std::chrono::steady_clock::time_point rg_t0{};
     // per-class CUDA-event timing of the last step (ghost, rhs, reflux, restrict, cfl);
     // inside a graph capture the events become external event-record nodes
     bool timing = false;
@@ -303,6 +306,9 @@ void assign_slots(amr_ctx* c, const std::vector<Key>& created, const std::vector
 
 int grid_size(const amr_ctx* c, int per_sm) { return c->nsm * per_sm; }
 
+// request-list entries read back with the counts (longer lists take a second read-back)
+constexpr int REQ_READ = 2048;
+
 void drop_graphs(amr_ctx* c) {
     for (auto& row : c->graph)
         for (auto& ex : row) {
@@ -419,10 +425,8 @@ int per_patch_step(amr_ctx* c, bool with_cfl) {
     return AMR_OK;
 }
 
-int read_time(amr_ctx* c) {
-    CK(cudaMemcpyAsync(c->time_h, c->time_d, sizeof(DevTime), cudaMemcpyDeviceToHost, c->stream), "read time");
-    CK(cudaStreamSynchronize(c->stream), "read time");
-    c->d2h += sizeof(DevTime);
+// error bits of the time record already copied to time_h
+int check_time(amr_ctx* c) {
     if (c->time_h->err & ERR_NONFINITE) {
         c->broken = true;
         return fail(c, AMR_ERR_NONFINITE, "non-positive density or pressure, or non-finite wave speed");
@@ -436,6 +440,13 @@ int read_time(amr_ctx* c) {
         return fail(c, AMR_ERR_TIMEOUT, "a bounded wait on the tensor cores gave up");
     }
     return AMR_OK;
+}
+
+int read_time(amr_ctx* c) {
+    CK(cudaMemcpyAsync(c->time_h, c->time_d, sizeof(DevTime), cudaMemcpyDeviceToHost, c->stream), "read time");
+    CK(cudaStreamSynchronize(c->stream), "read time");
+    c->d2h += sizeof(DevTime);
+    return check_time(c);
 }
 
 template <typename T>
@@ -484,9 +495,12 @@ int step_impl(amr_ctx* c, double dt, double* dt_used) {
     return AMR_OK;
 }
 
-// flags of the current state (ghosts filled first) -> compacted request lists on the host
+// The flagging half of a regrid, enqueued: ghost fill, flags, request
+// compaction (which sets DevTime::cancel when there are requests), and the
+// read-back of the request lists and of the time record; ev_req marks its end.
 template <typename T>
-int compute_requests(amr_ctx* c, std::vector<Key>& refine, std::vector<Key>& coarsen) {
+int regrid_enqueue(amr_ctx* c) {
+    c->rg_t0 = std::chrono::steady_clock::now();
     auto mark = [&](cudaEvent_t e) { return c->timing ? cudaEventRecord(e, c->stream) : cudaSuccess; };
     CK(mark(c->ev_rg[0]), "event");
     const long long k0 = c->kernels;
@@ -504,48 +518,104 @@ int compute_requests(amr_ctx* c, std::vector<Key>& refine, std::vector<Key>& coa
            "flag");
     }
     CK(mark(c->ev_rg[2]), "event");
-    CK(launch_requests(c->grid, c->anyflag, c->req_d + 2, c->req_d + 2 + c->cap, c->req_d, c->stream), "requests");
+    CK(launch_requests(c->grid, c->anyflag, c->rej_d, c->req_d + 2, c->req_d + 2 + c->cap, c->req_d, c->stream),
+       "requests");
     c->kernels += 2;
-    CK(cudaMemcpyAsync(c->req_h, c->req_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read requests");
-    CK(cudaStreamSynchronize(c->stream), "read requests");
-    const int nr = c->req_h[0], nc = c->req_h[1];
-    if (nr > 0)
-        CK(cudaMemcpyAsync(c->req_h + 2, c->req_d + 2, nr * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
-           "read requests");
-    if (nc > 0)
-        CK(cudaMemcpyAsync(c->req_h + 2 + c->cap, c->req_d + 2 + c->cap, nc * sizeof(int), cudaMemcpyDeviceToHost,
-                           c->stream),
-           "read requests");
-    c->d2h += (long long)(2 + nr + nc) * sizeof(int);
-    r = read_time(c);
-    if (r) return r;
-    refine.clear();
-    coarsen.clear();
-    for (int i = 0; i < nr; ++i) refine.push_back(unpack(c->key_of[c->req_h[2 + i]]));
-    for (int i = 0; i < nc; ++i) coarsen.push_back(unpack(c->key_of[c->req_h[2 + c->cap + i]]));
+    // counts and the first REQ_READ entries of both lists, and the time record, in one read-back
+    const int head = std::min(c->cap, REQ_READ);
+    CK(cudaMemcpyAsync(c->req_h, c->req_d, (2 + (size_t)head) * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "read requests");
+    CK(cudaMemcpyAsync(c->req_h + 2 + c->cap, c->req_d + 2 + c->cap, (size_t)head * sizeof(int),
+                       cudaMemcpyDeviceToHost, c->stream),
+       "read requests");
+    CK(cudaMemcpyAsync(c->time_h, c->time_d, sizeof(DevTime), cudaMemcpyDeviceToHost, c->stream), "read time");
+    CK(cudaEventRecord(c->ev_req, c->stream), "read requests");
+    c->ghosts_valid = true;                                // filled at the current time for the flags
     return AMR_OK;
 }
 
-template <typename T>
-int regrid_impl(amr_ctx* c, bool resample_ic) {
-    std::vector<Key> req, cand;
-    const auto t0 = std::chrono::steady_clock::now();
-    int r = compute_requests<T>(c, req, cand);
+// Wait for the requests of regrid_enqueue and turn them into keys; clears
+// DevTime::cancel when there were any. void_step (may be NULL): the
+// compaction set DevTime::cancel, so a step issued after regrid_enqueue is void.
+int read_requests(amr_ctx* c, std::vector<Key>& req, std::vector<Key>& cand, bool* void_step = nullptr) {
+    CK(cudaEventSynchronize(c->ev_req), "read requests");
+    if (void_step) *void_step = c->time_h->cancel != 0;
+    const int nr = c->req_h[0], nc = c->req_h[1];
+    const int head = std::min(c->cap, REQ_READ);
+    c->d2h += (long long)(2 + 2 * head) * sizeof(int) + sizeof(DevTime);
+    if (nr | nc) {
+        CK(cudaMemsetAsync(&c->time_d->cancel, 0, sizeof(int), c->stream), "clear cancel");
+        if (nr > head || nc > head) {                      // long lists: the rest in a second read-back
+            if (nr > head)
+                CK(cudaMemcpyAsync(c->req_h + 2 + head, c->req_d + 2 + head, (size_t)(nr - head) * sizeof(int),
+                                   cudaMemcpyDeviceToHost, c->stream),
+                   "read requests");
+            if (nc > head)
+                CK(cudaMemcpyAsync(c->req_h + 2 + c->cap + head, c->req_d + 2 + c->cap + head,
+                                   (size_t)(nc - head) * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                   "read requests");
+            CK(cudaStreamSynchronize(c->stream), "read requests");
+            c->d2h += (long long)(std::max(nr - head, 0) + std::max(nc - head, 0)) * sizeof(int);
+        }
+    }
+    int r = check_time(c);
     if (r) return r;
-    c->ghosts_valid = true;                                // filled at the current time for the flags
-    const auto t1 = std::chrono::steady_clock::now();
-    c->regrid_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    req.clear();
+    cand.clear();
+    for (int i = 0; i < nr; ++i) req.push_back(unpack(c->key_of[c->req_h[2 + i]]));
+    for (int i = 0; i < nc; ++i) cand.push_back(unpack(c->key_of[c->req_h[2 + c->cap + i]]));
+    c->regrid_ms[0] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c->rg_t0).count();
     c->regrid_timed = c->timing;
+    return AMR_OK;
+}
+
+// flags of the current state (ghosts filled first) -> request keys on the host
+template <typename T>
+int compute_requests(amr_ctx* c, std::vector<Key>& req, std::vector<Key>& cand) {
+    int r = regrid_enqueue<T>(c);
+    if (r) return r;
+    return read_requests(c, req, cand);
+}
+
+// The device copy of the coarsening candidates the host found it could not
+// coarsen (n >= 0), or none (n = -1), for the request compaction's test.
+int set_rejected(amr_ctx* c, int n) {
+    int* stage = c->req_h + 2 + 2 * (size_t)c->cap;      // pinned staging word
+    *stage = n;
+    if (n > 0)
+        CK(cudaMemcpyAsync(c->rej_d + 1, c->req_d + 2 + c->cap, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice,
+                           c->stream),
+           "rejected");
+    CK(cudaMemcpyAsync(c->rej_d, stage, sizeof(int), cudaMemcpyHostToDevice, c->stream), "rejected");
+    return AMR_OK;
+}
+
+// The host half of a regrid: the requests, closed under R2 (Algorithm 1),
+// coarsening, and the new hierarchy applied. void_step (may be NULL): a step
+// issued after regrid_enqueue is void; changed (may be NULL): the hierarchy
+// changed.
+template <typename T>
+int regrid_finish(amr_ctx* c, bool resample_ic, bool* void_step, bool* changed) {
+    if (changed) *changed = false;
+    std::vector<Key> req, cand;
+    int r = read_requests(c, req, cand, void_step);
+    if (r) return r;
+    const auto t1 = std::chrono::steady_clock::now();
     c->regrid_ms[1] = c->regrid_ms[2] = 0.0;
+    if (req.empty() && cand.empty()) return AMR_OK;
     Mesh m2 = c->mesh;
     std::vector<Key> created = m2.refine(req);
     std::unordered_set<uint64_t> just;
     for (const auto& k : created) just.insert(pack(k));
     std::vector<Key> deleted = m2.coarsen(cand, just);
-    if (created.empty() && deleted.empty()) return AMR_OK;
+    if (created.empty() && deleted.empty())                // the same candidates give the same answer
+        return set_rejected(c, req.empty() ? (int)cand.size() : -1);
     if ((long long)m2.patches.size() > c->cap)
         return fail(c, AMR_ERR_POOL, "patch pool capacity exceeded; hierarchy left unchanged");
     c->ghosts_valid = false;                               // new and removed patches: neighbours' ghosts stale
+    if (changed) *changed = true;
+    r = set_rejected(c, -1);
+    if (r) return r;
     c->mesh.patches.swap(m2.patches);
     assign_slots(c, created, deleted);
     const auto t2 = std::chrono::steady_clock::now();
@@ -560,6 +630,36 @@ int regrid_impl(amr_ctx* c, bool resample_ic) {
     const auto t3 = std::chrono::steady_clock::now();
     c->regrid_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
     c->regrid_ms[2] = std::chrono::duration<double, std::milli>(t3 - t2).count();
+    return AMR_OK;
+}
+
+template <typename T>
+int regrid_impl(amr_ctx* c, bool resample_ic) {
+    int r = regrid_enqueue<T>(c);
+    if (r) return r;
+    return regrid_finish<T>(c, resample_ic, nullptr, nullptr);
+}
+
+// n steps, each followed by a regrid. The next step is issued before the
+// host has read the regrid's requests; if there were any, that step's kernels
+// found DevTime::cancel set and did nothing, and it is issued again once the
+// hierarchy has been updated.
+template <typename T>
+int advance_impl(amr_ctx* c, int n) {
+    if (n == 0) return AMR_OK;
+    int r = step_impl<T>(c, 0.0, nullptr);
+    if (r) return r;
+    for (int i = 0; i < n; ++i) {
+        if ((r = regrid_enqueue<T>(c))) return r;
+        const bool more = i + 1 < n;
+        if (more && (r = step_impl<T>(c, 0.0, nullptr))) return r;
+        bool had = false, changed = false;                 // had: the step issued ahead is void
+        if ((r = regrid_finish<T>(c, false, &had, &changed))) return r;
+        if (more && had) {
+            if (!changed) c->ghosts_valid = true;          // the void step left the filled ghosts as they were
+            if ((r = step_impl<T>(c, 0.0, nullptr))) return r;
+        }
+    }
     return AMR_OK;
 }
 
@@ -625,6 +725,7 @@ int set_state_impl(amr_ctx* c, int n, const int* levels, const int* coords, cons
     std::vector<Key> all = c->mesh.canonical();
     assign_slots(c, all, {});
     c->ghosts_valid = false;
+    if (int r0 = set_rejected(c, -1)) return r0;                 // a new hierarchy
     int r = rebuild_tables(c, {});
     if (r) return r;
     long long ncell = 1;
@@ -648,6 +749,7 @@ int set_state_impl(amr_ctx* c, int n, const int* levels, const int* coords, cons
     c->time_h->dt = 0.0;
     c->time_h->lam = 0ull;
     c->time_h->err = 0;
+    c->time_h->cancel = 0;
     CK(cudaMemcpyAsync(c->time_d, c->time_h, sizeof(DevTime), cudaMemcpyHostToDevice, c->stream), "set time");
     CK(cudaStreamSynchronize(c->stream), "set time");
     return AMR_OK;
@@ -932,7 +1034,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     c->meta_ints = ml.total;
     c->meta_d = (int*)dalloc(c, ml.total * sizeof(int));
     c->anyflag = (int*)dalloc(c, (c->cap + 32) * sizeof(int));     // flags + the learned flagger's work counter
-    c->req_d = (int*)dalloc(c, (2 + 2 * (size_t)c->cap) * sizeof(int));
+    c->req_d = (int*)dalloc(c, (3 + 3 * (size_t)c->cap) * sizeof(int));
     c->cons_partial = (double*)dalloc(c, (size_t)c->cap * c->nv * sizeof(double));
     c->cons_d = (double*)dalloc(c, 8 * sizeof(double));
     c->dense_cap = std::max<size_t>((size_t)g.patch_elems * 64, (size_t)1 << 22);
@@ -945,9 +1047,12 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
         !c->slots_d || !c->time_d)
         return fail(c, AMR_ERR_CUDA, "device allocation failed");
     if (cudaMallocHost((void**)&c->meta_h, ml.total * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&c->req_h, (2 + 2 * (size_t)c->cap) * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->req_h, (3 + 2 * (size_t)c->cap) * sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&c->time_h, sizeof(DevTime)) != cudaSuccess)
         return fail(c, AMR_ERR_CUDA, "pinned host allocation failed");
+    CK(cudaEventCreateWithFlags(&c->ev_req, cudaEventDisableTiming), "event");
+    c->rej_d = c->req_d + 2 + 2 * (size_t)c->cap;
+    CK(cudaMemsetAsync(c->rej_d, 0xFF, sizeof(int), c->stream), "clear rejected");   // -1: none
     for (int i = 0; i < 3; ++i) CK(cudaMemsetAsync(c->U[i], 0, state_bytes, c->stream), "clear pool");
     CK(cudaMemsetAsync(c->faces, 0, face_bytes, c->stream), "clear faces");
     CK(cudaMemsetAsync(c->anyflag, 0, c->cap * sizeof(int), c->stream), "clear flags");
@@ -1049,6 +1154,22 @@ int amr_regrid(amr_ctx* c) {
     GUARD(c);
     if (c->L == 1) return AMR_OK;
     return c->precision == 64 ? regrid_impl<double>(c, false) : regrid_impl<float>(c, false);
+}
+
+int amr_advance(amr_ctx* c, int n_steps, int regrid) {
+    GUARD(c);
+    if (n_steps < 0) return fail(c, AMR_ERR_ARG, "negative step count");
+    if (regrid && c->L > 1 && c->mode == AMR_MODE_BATCHED)
+        return c->precision == 64 ? advance_impl<double>(c, n_steps) : advance_impl<float>(c, n_steps);
+    for (int i = 0; i < n_steps; ++i) {
+        int r = c->precision == 64 ? step_impl<double>(c, 0.0, nullptr) : step_impl<float>(c, 0.0, nullptr);
+        if (r) return r;
+        if (regrid && c->L > 1) {
+            r = c->precision == 64 ? regrid_impl<double>(c, false) : regrid_impl<float>(c, false);
+            if (r) return r;
+        }
+    }
+    return AMR_OK;
 }
 
 int amr_get_level(amr_ctx* c, int level, int* n_patches, int* coords, double* data) {
@@ -1276,6 +1397,7 @@ void amr_destroy(amr_ctx* c) {
         cudaEventDestroy(c->ev_cfl[1]);
         for (int i = 0; i < 3; ++i) cudaEventDestroy(c->ev_rg[i]);
     }
+    if (c->ev_req) cudaEventDestroy(c->ev_req);
     dfree_all(c);
     if (c->meta_h) cudaFreeHost(c->meta_h);
     if (c->req_h) cudaFreeHost(c->req_h);

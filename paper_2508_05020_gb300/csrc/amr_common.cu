@@ -8,6 +8,7 @@ namespace amr {
 // dt = CFL / lambda_max (Sec. 3.1: the sound speed sets the step), clipped to
 // t_end; the maximum is reset for the next step.
 __global__ void k_finalize_dt(DevTime* tm, double cfl, double t_end) {
+    if (tm->cancel) return;
     const double lam = __longlong_as_double((long long)tm->lam);
     if (!(lam > 0.0) || !(lam <= 1.0e300)) {
         tm->err |= ERR_NONFINITE;
@@ -20,9 +21,13 @@ __global__ void k_finalize_dt(DevTime* tm, double cfl, double t_end) {
     tm->lam = 0ull;
 }
 
-__global__ void k_set_dt(DevTime* tm, double dt) { tm->dt = dt; }
+__global__ void k_set_dt(DevTime* tm, double dt) {
+    if (!tm->cancel) tm->dt = dt;
+}
 
-__global__ void k_advance_time(DevTime* tm) { tm->t = tm->t + tm->dt; }
+__global__ void k_advance_time(DevTime* tm) {
+    if (!tm->cancel) tm->t = tm->t + tm->dt;
+}
 
 cudaError_t launch_finalize_dt(const Grid& g, cudaStream_t s) {
     k_finalize_dt<<<1, 1, 0, s>>>(g.time, g.cfl, g.t_end);
@@ -43,8 +48,8 @@ cudaError_t launch_advance_time(DevTime* t, cudaStream_t s) {
 // coarsen = has children, all children leaves, none flagged. One block; an
 // exclusive scan per 1024-patch chunk (warp shuffles + shared totals) keeps
 // the canonical order of the compacted lists.
-__global__ void __launch_bounds__(1024) k_requests(Grid g, const int* anyflag, int* out_refine, int* out_coarsen,
-                                                   int* out_counts) {
+__global__ void __launch_bounds__(1024) k_requests(Grid g, const int* anyflag, const int* rejected,
+                                                   int* out_refine, int* out_coarsen, int* out_counts) {
     __shared__ int wsum[2][32];
     __shared__ int base[2];
     const int n = g.counts[0];
@@ -104,12 +109,30 @@ __global__ void __launch_bounds__(1024) k_requests(Grid g, const int* anyflag, i
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) { out_counts[0] = base[0]; out_counts[1] = base[1]; }
+    // a step issued next is void if the mesh may change: on refinement requests, or
+    // coarsening candidates other than the list the host last found it could not
+    // coarsen on this same hierarchy (rejected[0] = its length, -1: none)
+    const int nr = base[0], nc = base[1];
+    int cancel = nr > 0 ? 1 : 0;
+    if (!cancel && nc > 0) {
+        if (!rejected || rejected[0] != nc) {
+            cancel = 1;
+        } else {
+            bool differ = false;
+            for (int i = threadIdx.x; i < nc; i += blockDim.x) differ = differ || out_coarsen[i] != rejected[1 + i];
+            cancel = __syncthreads_or(differ) ? 1 : 0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        out_counts[0] = nr;
+        out_counts[1] = nc;
+        g.time->cancel = cancel;
+    }
 }
 
-cudaError_t launch_requests(const Grid& g, const int* anyflag, int* out_refine, int* out_coarsen, int* out_counts,
-                            cudaStream_t s) {
-    k_requests<<<1, 1024, 0, s>>>(g, anyflag, out_refine, out_coarsen, out_counts);
+cudaError_t launch_requests(const Grid& g, const int* anyflag, const int* rejected, int* out_refine,
+                            int* out_coarsen, int* out_counts, cudaStream_t s) {
+    k_requests<<<1, 1024, 0, s>>>(g, anyflag, rejected, out_refine, out_coarsen, out_counts);
     return cudaGetLastError();
 }
 

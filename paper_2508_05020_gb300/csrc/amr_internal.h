@@ -28,7 +28,9 @@ struct DevTime {
     double dt;                  // step in use
     unsigned long long lam;     // bit pattern of the max wave-speed sum (non-negative double)
     int err;                    // ERR_* bits
-    int pad;
+    int cancel;                 // nonzero: the kernels of a step return at once (set by the request
+                                // compaction when the mesh may change; a step issued ahead of that
+                                // decision is then void and issued again)
 };
 
 // Read-only description of the grid and the metadata tables, passed by value.
@@ -116,7 +118,7 @@ struct Kernels {
 cudaError_t launch_finalize_dt(const Grid& g, cudaStream_t s);
 cudaError_t launch_set_dt(DevTime* t, double dt, cudaStream_t s);
 cudaError_t launch_advance_time(DevTime* t, cudaStream_t s);
-cudaError_t launch_requests(const Grid& g, const int* anyflag, int* out_refine, int* out_coarsen,
+cudaError_t launch_requests(const Grid& g, const int* anyflag, const int* rejected, int* out_refine, int* out_coarsen,
                             int* out_counts, cudaStream_t s);
 
 // MLP pieces (amr_mlp.cu)

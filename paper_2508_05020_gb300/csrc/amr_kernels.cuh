@@ -427,6 +427,7 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
                                                double4 pre, double4 post, int chunk) {
     constexpr int NV = D + 2;
     __shared__ PatchMeta m;
+    if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
     const int lo = g.level_off[level], hi = g.level_off[level + 1];
     const int npatch = one_slot >= 0 ? 1 : hi - lo;
     const double t = g.time->t + tfrac * g.time->dt;
@@ -494,6 +495,7 @@ __global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, c
     constexpr int NT = D - 1;
     constexpr int CPT = (C::CELLS + NTH - 1) / NTH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
     T* q = reinterpret_cast<T*>(smem_raw);                 // [NV][QZ][QY][QX]
     T* Fs = q + NV * C::QN;                               // [NV][FMAX]
     const T gamma = T(g.gamma);
@@ -694,6 +696,7 @@ __global__ void __launch_bounds__(256) k_reflux(Grid g, T* Uout, const T* __rest
                                                 int one_item) {
     constexpr int NV = D + 2;
     constexpr int TRANS = Chunk<D, N, 1>::TRANS;
+    if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
     const T rb = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2.0 / 3.0));
     const T dt = T(g.time->dt);
     const int n = one_item >= 0 ? one_item + 1 : g.counts[2];
@@ -767,6 +770,7 @@ __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int o
     constexpr int H = N / 2;
     constexpr int HC = D == 1 ? H : (D == 2 ? H * H : H * H * H);
     constexpr int NCH = 1 << D;
+    if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
     const int lo = g.level_off[level], hi = g.level_off[level + 1];
     const int npatch = one_slot >= 0 ? 1 : hi - lo;
     const long long total = (long long)npatch * HC;
@@ -816,6 +820,7 @@ __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
     // and turned into FP64 once per CTA
     constexpr int NV = D + 2;
     constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
+    if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
     const int npatch = one_slot >= 0 ? 1 : g.counts[1];
     const long long total = (long long)npatch * NC;
     const T gamma = T(g.gamma);
