@@ -113,6 +113,53 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     return Num<T>::div(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
 }
 
+// FP32: left- (nodes 0..4) and right-biased (nodes 5..1) WENO5-JS values of one
+// face together; the right stencil is the left one mirrored, so two candidate
+// values and two smoothness terms are shared between them. Same formulas as
+// weno5, evaluated with the single-division weights.
+__device__ __forceinline__ void weno5_pair(float v0, float v1, float v2, float v3, float v4, float v5, float& left,
+                                           float& right) {
+    const float c1312 = 13.0f / 12.0f;
+    const float qA = (-v1 + 6.0f * v2 + 3.0f * v3) * 0.125f;   // left q1 = right q2
+    const float qB = (3.0f * v2 + 6.0f * v3 - v4) * 0.125f;    // left q2 = right q1
+    const float tA = v1 - 2.0f * v2 + v3, tB = v2 - 2.0f * v3 + v4;
+    const float cA = c1312 * (tA * tA), cB = c1312 * (tB * tB);
+    auto combine = [](float q0, float q1, float q2, float b0, float b1, float b2) {
+        const float e0 = 1.0e-6f + b0, e1 = 1.0e-6f + b1, e2 = 1.0e-6f + b2;
+        const float s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
+        if (fmaxf(s0, fmaxf(s1, s2)) < 1.0e12f) {
+            const float m0 = 0.0625f * (s1 * s2), m1 = 0.625f * (s0 * s2), m2 = 0.3125f * (s0 * s1);
+            return __fdividef(m0 * q0 + m1 * q1 + m2 * q2, m0 + m1 + m2);
+        }
+        const float a0 = __fdividef(0.0625f, s0), a1 = __fdividef(0.625f, s1), a2 = __fdividef(0.3125f, s2);
+        return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+    };
+    {   // left: a = v0, b = v1, c = v2, d = v3, e = v4
+        const float q0 = (3.0f * v0 - 10.0f * v1 + 15.0f * v2) * 0.125f;
+        const float t0 = v0 - 2.0f * v1 + v2, s0 = v0 - 4.0f * v1 + 3.0f * v2;
+        const float s1 = v1 - v3, s2 = 3.0f * v2 - 4.0f * v3 + v4;
+        left = combine(q0, qA, qB, c1312 * (t0 * t0) + 0.25f * (s0 * s0), cA + 0.25f * (s1 * s1),
+                       cB + 0.25f * (s2 * s2));
+    }
+    {   // right: a = v5, b = v4, c = v3, d = v2, e = v1
+        const float q0 = (3.0f * v5 - 10.0f * v4 + 15.0f * v3) * 0.125f;
+        const float t0 = v5 - 2.0f * v4 + v3, s0 = v5 - 4.0f * v4 + 3.0f * v3;
+        const float s1 = v4 - v2, s2 = 3.0f * v3 - 4.0f * v2 + v1;
+        right = combine(q0, qB, qA, c1312 * (t0 * t0) + 0.25f * (s0 * s0), cB + 0.25f * (s1 * s1),
+                        cA + 0.25f * (s2 * s2));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void weno5_lr(const T (&w)[6], T& left, T& right) {
+    if constexpr (sizeof(T) == 4) {
+        weno5_pair(w[0], w[1], w[2], w[3], w[4], w[5], left, right);
+    } else {
+        left = weno5(w[0], w[1], w[2], w[3], w[4]);
+        right = weno5(w[5], w[4], w[3], w[2], w[1]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Face flux between pencil nodes 2 and 3 (Sec. 3.2, Eqs. 10-12).
 // Pencil node k holds (p, un, ut[NT], T). Frozen state: pbar, Tbar means of
@@ -138,21 +185,15 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
         T w[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) w[k] = p[k] - z * un[k];
-        wl[0] = weno5(w[0], w[1], w[2], w[3], w[4]);
-        wr[0] = weno5(w[5], w[4], w[3], w[2], w[1]);
+        weno5_lr(w, wl[0], wr[0]);
 #pragma unroll
         for (int k = 0; k < 6; ++k) w[k] = Tt[k] - kap * p[k];
-        wl[1] = weno5(w[0], w[1], w[2], w[3], w[4]);
-        wr[1] = weno5(w[5], w[4], w[3], w[2], w[1]);
+        weno5_lr(w, wl[1], wr[1]);
 #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-            wl[2 + j] = weno5(ut[j][0], ut[j][1], ut[j][2], ut[j][3], ut[j][4]);
-            wr[2 + j] = weno5(ut[j][5], ut[j][4], ut[j][3], ut[j][2], ut[j][1]);
-        }
+        for (int j = 0; j < NT; ++j) weno5_lr(ut[j], wl[2 + j], wr[2 + j]);
 #pragma unroll
         for (int k = 0; k < 6; ++k) w[k] = p[k] + z * un[k];
-        wl[NF - 1] = weno5(w[0], w[1], w[2], w[3], w[4]);
-        wr[NF - 1] = weno5(w[5], w[4], w[3], w[2], w[1]);
+        weno5_lr(w, wl[NF - 1], wr[NF - 1]);
     }
     const T z2 = T(2) * z;
     T pL = T(0.5) * (wl[0] + wl[NF - 1]);
@@ -486,8 +527,8 @@ constexpr size_t rhs_smem_bytes() {
     return sizeof(T) * ((size_t)(D + 2) * C::QN + (size_t)(D + 2) * C::FMAX);
 }
 
-template <typename T, int D, int N, int DZ, int NTH>
-__global__ void __launch_bounds__(NTH) k_rhs(Grid g, const T* __restrict__ Us, const T* U0,
+template <typename T, int D, int N, int DZ, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__ Us, const T* U0,
                                              T* Uout, T* __restrict__ faces,
                                              int stage, int one_slot) {
     using C = Chunk<D, N, DZ>;

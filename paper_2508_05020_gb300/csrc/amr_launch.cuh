@@ -8,8 +8,11 @@ namespace amr {
 
 // chunk depth (3D) and block size of the fused RHS kernel per precision
 template <typename T, int D, int N> struct RhsCfg {
-    static constexpr int DZ = D == 3 ? (sizeof(T) == 8 ? 2 : 4) : 1;
+    // 3D: two-plane chunks (61 KB of staging in FP32) so that three CTAs of
+    // at most 85 registers share an SM
+    static constexpr int DZ = D == 3 ? 2 : 1;
     static constexpr int NTH = D == 1 ? 64 : 256;
+    static constexpr int MINB = (D == 3 && sizeof(T) == 4) ? 3 : 1;
 };
 
 #define AMR_DISPATCH(g, CALL)                                   \
@@ -32,7 +35,7 @@ static cudaError_t rhs_launch(const Grid& g, const T* Us, const T* U0, T* Uout, 
                               cudaStream_t s, int one_slot) {
     using C = RhsCfg<T, D, N>;
     constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
-    auto kern = k_rhs<T, D, N, C::DZ, C::NTH>;
+    auto kern = k_rhs<T, D, N, C::DZ, C::NTH, C::MINB>;
     kern<<<grid, C::NTH, smem, s>>>(g, Us, U0, Uout, faces, stage, one_slot);
     return cudaGetLastError();
 }
@@ -41,7 +44,7 @@ template <typename T, int D, int N>
 static cudaError_t rhs_prepare() {
     using C = RhsCfg<T, D, N>;
     constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
-    cudaError_t e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_flag_plain<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
