@@ -34,9 +34,9 @@ FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 
 # DRAM bytes (read + write) of one k_rhs launch (SSP-RK3 stage 1, 1536 patches) from the ncu capture
 # summarised in profiles/k_rhs_blast3d_128_fp32.md, valid while the kernel sources hash as they did then
-RHS_TRAFFIC = {'bytes': 452502272 + 170149120, 'workload': 'blast3d', 'base': 128,
-               'sources': {'paper_2508_05020_gb300/csrc/amr_kernels.cuh': 'f6596d8592ca8f4f',
-                           'paper_2508_05020_gb300/csrc/amr_launch.cuh': '187a014027af0415'}}
+RHS_TRAFFIC = {'bytes': 452855296 + 171131136, 'workload': 'blast3d', 'base': 128,
+               'sources': {'paper_2508_05020_gb300/csrc/amr_kernels.cuh': '9b81136c640f4e31',
+                           'paper_2508_05020_gb300/csrc/amr_launch.cuh': '9556f0d287340bd7'}}
 
 
 def rhs_traffic(workload_name, base):
