@@ -233,6 +233,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     _, _, k0 = amr.counters()
+    _, cons0, _ = amr.diag()                   # conserved sums before the timed steps
     clocks = ClockSampler(local)
     clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -259,6 +260,7 @@ def main():
         dist.barrier()
     value = units / elapsed
     t_now, cons, ppl = amr.diag()
+    drift = [float(abs(c1 - c0) / max(abs(c0), 1e-300)) for c0, c1 in zip(cons0, cons)]
 
     peaks = load_json(PEAKS_FILE, {})
     sm_max = float(peaks.get('sm_max_mhz', 2070.0))
@@ -286,6 +288,10 @@ def main():
                 'launch_parameters': tuned, 'autotuned': not args.no_autotune,
                 'cells_per_step': cell_counts(w, ppl)},
             'clocks': clk, 'gpu_launches': int(k1 - k0), 'roofline': roof,
+            'conservation': {'relative_drift_over_timed_steps': drift,
+                             'variables': ['rho'] + ['rho u%d' % d for d in range(w['dim'])] + ['rho E'],
+                             'note': 'sums over leaf cells times cell volume (FP64); exact conservation on '
+                                     'periodic or closed domains up to round-off'},
             'phase_ms_last_step': dict(zip(AMR.TIMING_SLOTS, [float(x) for x in kinds])),
             'wall_s': wall}
 

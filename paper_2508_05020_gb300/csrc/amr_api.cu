@@ -31,7 +31,7 @@ struct amr_ctx {
     int nsm = 1;
     // launch parameters of the batched step (CTAs per SM; ghost cells per work
     // item), the defaults or the autotuner's choice (AMR_TUNE_* order)
-    int tune[AMR_TUNE_N] = {16, 512, 2, 4, 8, 8, 4};
+    int tune[AMR_TUNE_N] = {16, 128, 2, 4, 8, 8, 4};
     float tune_ms[AMR_TUNE_N] = {0, 0, 0, 0, 0, 0, 0};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -822,7 +822,7 @@ int autotune_impl(amr_ctx* c) {
         return cudaSuccess;
     };
     if (err == cudaSuccess) {                            // ghost fill of every level: grid x work-item size
-        const int grids[] = {4, 8, 16, 32}, chunks[] = {256, 512, 1024, 2048, 4096};
+        const int grids[] = {4, 8, 16, 32}, chunks[] = {64, 128, 256, 512, 1024};
         float bestv = 1e30f;
         for (int gr : grids)
             for (int ch : chunks) {

@@ -279,6 +279,25 @@ __device__ __forceinline__ void load_meta(const Grid& g, int slot, PatchMeta& m)
     __syncthreads();
 }
 
+// the same, by one warp into its own copy (no CTA barrier)
+__device__ __forceinline__ void load_meta_warp(const Grid& g, int slot, PatchMeta& m) {
+    const int lane = threadIdx.x & 31;
+    const int par = g.parent[slot];
+    if (lane == 0) {
+        m.slot = slot;
+        m.lev = g.level[slot];
+        m.par = par;
+        m.c[0] = g.coord[slot * 3];
+        m.c[1] = g.coord[slot * 3 + 1];
+        m.c[2] = g.coord[slot * 3 + 2];
+    }
+    if (lane < NBR) {
+        m.nbr[lane] = g.nbr[slot * NBR + lane];
+        m.pnbr[lane] = par >= 0 ? g.nbr[par * NBR + lane] : -1;
+    }
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // Limited-linear prolongation of the conserved variables at fine local cell l
 // of a patch (slot, level lev, coords c): coarse cell C = G // 2 in the
@@ -460,28 +479,32 @@ __device__ void ghost_value(const Grid& g, const T* U, const PatchMeta& m, int* 
 // ---------------------------------------------------------------------------
 // K1-K3: ghost fill of every patch of one level. A work item is a patch and a
 // run of `chunk` of its ghost cells (slot order; the size is a launch
-// parameter chosen by the autotuner); the CTA stages the patch's metadata in
-// shared memory once per item.
+// parameter chosen by the autotuner), taken by one warp, which stages the
+// patch's metadata in its own shared-memory copy; warps never wait for one
+// another.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
                                                double4 pre, double4 post, int chunk) {
     constexpr int NV = D + 2;
-    __shared__ PatchMeta m;
+    __shared__ PatchMeta metas[256 / 32];
     if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    PatchMeta& m = metas[warp];
     const int lo = g.level_off[level], hi = g.level_off[level + 1];
     const int npatch = one_slot >= 0 ? 1 : hi - lo;
     const double t = g.time->t + tfrac * g.time->dt;
     const double pr[4] = {pre.x, pre.y, pre.z, pre.w};
     const double po[4] = {post.x, post.y, post.z, post.w};
     const int nchunk = (g.n_ghost + chunk - 1) / chunk;   // chunk: ghost cells per work item
-    for (int item = blockIdx.x; item < npatch * nchunk; item += gridDim.x) {
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int item = blockIdx.x * (blockDim.x >> 5) + warp; item < npatch * nchunk; item += nw) {
         const int pi = item / nchunk;
         const int g0 = (item - pi * nchunk) * chunk;
         const int g1 = min(g0 + chunk, g.n_ghost);
         const int slot = one_slot >= 0 ? one_slot : g.all_list[lo + pi];
-        load_meta(g, slot, m);
-        for (int gi = g0 + threadIdx.x; gi < g1; gi += blockDim.x) {
+        load_meta_warp(g, slot, m);
+        for (int gi = g0 + lane; gi < g1; gi += 32) {
             const int pk = g.ghost_tab[gi];
             int l[3] = {(pk & 1023) - G, ((pk >> 10) & 1023) - G, ((pk >> 20) & 1023) - G};
             const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
@@ -490,7 +513,7 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
 #pragma unroll
             for (int v = 0; v < NV; ++v) U[slot_index(g, slot, v, sz, sy, sx)] = val[v];
         }
-        __syncthreads();
+        __syncwarp();                                    // the copy is read until here
     }
 }
 

@@ -37,9 +37,9 @@ def test_autotune_leaves_results_unchanged(name, base, precision):
     pa, ta = a.tuning()
     pb, tb = b.tuning()
     # defaults before tuning; candidates of the tuner after it, each with a measured time
-    assert pa == {'ghost_ctas_per_sm': 16, 'ghost_cells_per_item': 512, 'rhs_ctas_per_sm': 2,
+    assert pa == {'ghost_ctas_per_sm': 16, 'ghost_cells_per_item': 128, 'rhs_ctas_per_sm': 2,
                   'reflux_ctas_per_sm': 4, 'restrict_ctas_per_sm': 8, 'cfl_ctas_per_sm': 8, 'flag_ctas_per_sm': 4}
-    assert pb['ghost_ctas_per_sm'] in (4, 8, 16, 32) and pb['ghost_cells_per_item'] in (256, 512, 1024, 2048, 4096)
+    assert pb['ghost_ctas_per_sm'] in (4, 8, 16, 32) and pb['ghost_cells_per_item'] in (64, 128, 256, 512, 1024)
     assert pb['rhs_ctas_per_sm'] in (1, 2, 3, 4)
     assert all(tb[k] > 0 for k in TUNE_NAMES)
     # tuning again leaves the state, time and dt untouched
