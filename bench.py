@@ -260,7 +260,10 @@ def main():
         dist.barrier()
     value = units / elapsed
     t_now, cons, ppl = amr.diag()
-    drift = [float(abs(c1 - c0) / max(abs(c0), 1e-300)) for c0, c1 in zip(cons0, cons)]
+    # mass and energy: relative change; momenta (whose totals can vanish by symmetry): change per unit mass
+    nv = w['dim'] + 2
+    drift = [float(abs(cons[v] - cons0[v]) / max(abs(cons0[v] if v in (0, nv - 1) else cons0[0]), 1e-300))
+             for v in range(nv)]
 
     peaks = load_json(PEAKS_FILE, {})
     sm_max = float(peaks.get('sm_max_mhz', 2070.0))
@@ -290,8 +293,9 @@ def main():
             'clocks': clk, 'gpu_launches': int(k1 - k0), 'roofline': roof,
             'conservation': {'relative_drift_over_timed_steps': drift,
                              'variables': ['rho'] + ['rho u%d' % d for d in range(w['dim'])] + ['rho E'],
-                             'note': 'sums over leaf cells times cell volume (FP64); exact conservation on '
-                                     'periodic or closed domains up to round-off'},
+                             'note': 'sums over leaf cells times cell volume (FP64); mass and energy relative to their '
+                                     'totals, momenta relative to the total mass; exact conservation on periodic or '
+                                     'closed domains up to round-off'},
             'phase_ms_last_step': dict(zip(AMR.TIMING_SLOTS, [float(x) for x in kinds])),
             'wall_s': wall}
 
