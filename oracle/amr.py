@@ -434,7 +434,8 @@ class Oracle:
         inner = self.inner()
         faces = {}
         for k in keys:
-            R, faces[k] = euler.patch_rhs(src[k], self.dim, self.N, G, self.dx[k[0]], self.gamma)
+            R, faces[k] = euler.patch_rhs(src[k], self.dim, self.N, G, self.dx[k[0]], self.gamma,
+                                          self.w.get('flux', 'rusanov'))
             Us = src[k][inner]
             if s == 0:
                 new = Us + dt * R

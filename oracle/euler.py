@@ -111,7 +111,37 @@ def char_inverse(w, z, kap):
     return p, un, list(w[2:nf - 1]), T
 
 
-def face_flux(P, dim, gamma):
+def hllc(left, right, nt):
+    """HLLC flux (Toro's three-wave approximate Riemann solver: the HLL
+    fan split at the contact) from the two face states. Each side is a dict
+    with rho, un, ut (list), p, E, c and U, F in pencil order. Wave-speed
+    bounds S_L = min(un_L - c_L, un_R - c_R), S_R = max(un_L + c_L, un_R + c_R);
+    contact speed S* = (p_R - p_L + a_L un_L - a_R un_R) / (a_L - a_R) with
+    a_K = rho_K (S_K - un_K); star state U*_K = f_K (1, S*, ut_K, E_K / rho_K +
+    (S* - un_K)(S* + p_K / a_K)), f_K = a_K / (S_K - S*); flux F_L if S_L >= 0,
+    else F_L + S_L (U*_L - U_L) if S* >= 0, else F_R + S_R (U*_R - U_R) if
+    S_R > 0, else F_R."""
+    L, R = left, right
+    sL = np.minimum(L['un'] - L['c'], R['un'] - R['c'])
+    sR = np.maximum(L['un'] + L['c'], R['un'] + R['c'])
+    aL = L['rho'] * (sL - L['un'])
+    aR = R['rho'] * (sR - R['un'])
+    sM = (R['p'] - L['p'] + aL * L['un'] - aR * R['un']) / (aL - aR)
+
+    def star_flux(K, a, s):
+        f = a / (s - sM)
+        Us = [f, f * sM] + [f * K['ut'][j] for j in range(nt)] + \
+             [f * (K['E'] / K['rho'] + (sM - K['un']) * (sM + K['p'] / a))]
+        return [K['F'][v] + s * (Us[v] - K['U'][v]) for v in range(nt + 3)]
+
+    FsL = star_flux(L, aL, sL)
+    FsR = star_flux(R, aR, sR)
+    return [np.where(sL >= 0.0, L['F'][v],
+                     np.where(sM >= 0.0, FsL[v], np.where(sR > 0.0, FsR[v], R['F'][v])))
+            for v in range(nt + 3)]
+
+
+def face_flux(P, dim, gamma, flux='rusanov'):
     """Rusanov flux at the face between pencil nodes 2 and 3 (Sec. 3.2, Eqs. 11-12).
 
     P is a list of 6 pencil nodes (i-2 .. i+3), each a tuple (p, un, ut, T) where
@@ -130,6 +160,8 @@ def face_flux(P, dim, gamma):
          with a first-order fallback (nodes i, i+1) if p or T is not positive;
       5. conserved states and Euler fluxes at both sides, S = max(c + |un|) and
          F = (F^R + F^L)/2 - S (U^R - U^L)/2.
+    With flux='hllc', step 5 uses the HLLC flux of `hllc` from the same states
+    instead (an option the method leaves open; not in the paper).
     Returns the flux in pencil order (mass, normal momentum, tangential momenta,
     energy).
     """
@@ -166,10 +198,12 @@ def face_flux(P, dim, gamma):
         U = [rho, mn] + [rho * ut[j] for j in range(nt)] + [E]
         F = [mn, mn * un + p] + [mn * ut[j] for j in range(nt)] + [(E + p) * un]
         s = c + np.abs(un)
-        return U, F, s
+        return U, F, s, dict(rho=rho, un=un, ut=ut, p=p, E=E, c=c, U=U, F=F)
 
-    UL, FL, sL = side(pL, unL, utL, TL)
-    UR, FR, sR = side(pR, unR, utR, TR)
+    UL, FL, sL, left = side(pL, unL, utL, TL)
+    UR, FR, sR, right = side(pR, unR, utR, TR)
+    if flux == 'hllc':
+        return hllc(left, right, nt)
     hS = 0.5 * np.maximum(sR, sL)
     return [0.5 * (FR[v] + FL[v]) - hS * (UR[v] - UL[v]) for v in range(dim + 2)]
 
@@ -187,7 +221,7 @@ def pencil_to_global(F, dim, d):
     return out
 
 
-def patch_rhs(A, dim, N, g, dx, gamma):
+def patch_rhs(A, dim, N, g, dx, gamma, flux='rusanov'):
     """Right-hand side R = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d on a patch interior
     (Sec. 3.2, Eq. 10: divergence of the Riemann fluxes; dims in order x, y, z).
 
@@ -213,7 +247,7 @@ def patch_rhs(A, dim, N, g, dx, gamma):
             sl[ax] = slice(k, k + N + 1)   # faces i+1/2, i = -1..N-1
             sl = tuple(sl[1:])
             P.append((p[sl], u[d][sl], [u[e][sl] for e in tdims], T[sl]))
-        Fp = face_flux(P, dim, gamma)
+        Fp = face_flux(P, dim, gamma, flux)
         F = pencil_to_global(Fp, dim, d)
         F = np.stack(F)                      # (nv, ..., N+1 along ax)
         hi = [slice(None)] * 4

@@ -18,6 +18,7 @@ ic             initial-condition name
 cfl            CFL number
 t_end          final time (the time step is clipped to it)
 theta_rho/p    thresholds of the relative-jump refinement sensor
+flux           numerical flux at faces: 'rusanov' (Sec. 3.2) or 'hllc' (an option)
 seed           seed of the +-1 % density perturbation (blast only)
 amp            amplitude of that perturbation (blast only; 0.01)
 
@@ -85,6 +86,7 @@ def workload(name, **overrides):
     """Return a deep copy of a named workload with fields overridden."""
     w = copy.deepcopy(WORKLOADS[name])
     w['name'] = name
+    w.setdefault('flux', 'rusanov')
     for k, v in overrides.items():
         if k not in w:
             raise KeyError(k)

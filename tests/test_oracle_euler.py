@@ -156,6 +156,64 @@ def test_rusanov_step_data_gives_eq11(nt):
     assert np.allclose(F, ref, rtol=1e-9, atol=1e-9)
 
 
+# ------------------------------------------------------------ HLLC flux
+@pytest.mark.parametrize('nt', [0, 1, 2])
+def test_hllc_uniform_state_is_physical_flux(nt):
+    gamma = 1.4
+    for un in (0.4, -0.3, 2.5, -2.5):                    # subsonic both ways and supersonic both ways
+        st = (1.3, un, [0.2, -0.1][:nt], 0.9)
+        F = euler.face_flux([node(*st) for _ in range(6)], nt + 1, gamma, flux='hllc')
+        Fref, _ = euler_flux(*st, gamma)
+        assert np.allclose(F, Fref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize('nt', [0, 1, 2])
+def test_hllc_resolves_a_stationary_contact(nt):
+    # density jump at rest in uniform pressure (tangential velocity jumps too):
+    # the contact is a steady solution, HLLC carries no mass or energy through
+    # it and the momentum flux is the pressure; Rusanov diffuses the jump
+    gamma = 1.4
+    Lst = (1.0, 0.0, [0.3, -0.2][:nt], 1.0)
+    Rst = (0.125, 0.0, [-0.1, 0.4][:nt], 1.0)
+    P = [node(*Lst)] * 3 + [node(*Rst)] * 3
+    F = euler.face_flux(P, nt + 1, gamma, flux='hllc')
+    assert abs(F[0]) < 1e-13 and abs(F[nt + 2]) < 1e-13
+    assert F[1] == pytest.approx(1.0, abs=1e-13)
+    for j in range(nt):
+        assert abs(F[2 + j]) < 1e-13
+    Fr = euler.face_flux(P, nt + 1, gamma)
+    assert abs(Fr[0]) > 0.3
+
+
+@pytest.mark.parametrize('nt', [0, 2])
+def test_hllc_supersonic_upwinding_and_mirror_symmetry(nt):
+    gamma = 1.4
+    Lst = (1.0, 3.0, [0.1, 0.2][:nt], 1.0)               # u - c > 0 on both sides
+    Rst = (0.8, 3.4, [0.3, -0.4][:nt], 0.7)
+    P = [node(*Lst)] * 3 + [node(*Rst)] * 3
+    F = euler.face_flux(P, nt + 1, gamma, flux='hllc')
+    FL, _ = euler_flux(*Lst, gamma)
+    # the flux of the left face state (WENO leaves ~1e-7 of the mild jump in
+    # it); the Rusanov flux of the same states differs by its dissipation
+    assert np.allclose(F, FL, rtol=1e-6, atol=1e-6)
+    Fr = euler.face_flux(P, nt + 1, gamma)
+    assert max(abs(a - b) for a, b in zip(Fr, FL)) > 1e-2
+    # a subsonic two-state problem and its mirror image (sides swapped, normal
+    # velocity negated): mass and energy fluxes change sign, the normal
+    # momentum flux and the tangential momentum fluxes keep / flip with them
+    Lst = (1.0, 0.75, [0.1, 0.2][:nt], 1.0)
+    Rst = (0.125, -0.2, [0.3, -0.4][:nt], 0.1)
+    P = [node(*Lst)] * 3 + [node(*Rst)] * 3
+    Pm = [node(Rst[0], -Rst[1], Rst[2], Rst[3])] * 3 + [node(Lst[0], -Lst[1], Lst[2], Lst[3])] * 3
+    F = euler.face_flux(P, nt + 1, gamma, flux='hllc')
+    Fm = euler.face_flux(Pm, nt + 1, gamma, flux='hllc')
+    assert Fm[0] == pytest.approx(-F[0], rel=1e-12, abs=1e-12)
+    assert Fm[1] == pytest.approx(F[1], rel=1e-12, abs=1e-12)
+    assert Fm[nt + 2] == pytest.approx(-F[nt + 2], rel=1e-12, abs=1e-12)
+    for j in range(nt):
+        assert Fm[2 + j] == pytest.approx(-F[2 + j], rel=1e-12, abs=1e-12)
+
+
 # --------------------------------------------------------- exact Riemann solver
 def test_exact_riemann_sod_digits():
     g = json.load(open(os.path.join(GOLD, 'sod_exact.json')))
@@ -235,6 +293,23 @@ def test_sod_converges_to_exact_solution():
     assert s[0] == pytest.approx(0.5625, rel=1e-10)
     assert s[2] == pytest.approx(1.375, rel=1e-10)
     assert s[1] == pytest.approx(0.9 * 0.2, rel=1e-9)
+
+
+def test_sod_with_hllc_converges_and_sharpens_the_contact():
+    # the same run with the HLLC flux: converges to the exact solution, with a
+    # smaller error than the Rusanov flux (the contact is not smeared by the
+    # maximum wave speed)
+    w = workload('sod', levels=2, flux='hllc')
+    o = run_to(Oracle(w), w['t_end'])
+    rho = o.leaf_field(0)[0, 0]
+    x = (np.arange(rho.size) + 0.5) / rho.size
+    ex, _, _ = riemann.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, x, 0.5, o.t)
+    e_hllc = float(np.mean(np.abs(rho - ex)))
+    e_rus, _ = sod_l1(2)
+    assert e_hllc < 0.9 * e_rus
+    s = o.cons_sums()
+    assert s[0] == pytest.approx(0.5625, rel=1e-10)
+    assert s[2] == pytest.approx(1.375, rel=1e-10)
 
 
 def test_density_wave_second_order():
