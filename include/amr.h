@@ -106,7 +106,12 @@ typedef struct {
                                   amr_set_mlp must precede the first amr_regrid */
     long mlp_n_weights;
     int autotune;         /* 1: amr_init ends with amr_autotune on the initial hierarchy */
+    int flux;             /* AMR_FLUX_RUSANOV (Sec. 3.2, Eqs. 11-12; default) or AMR_FLUX_HLLC (an
+                             option the method leaves open: Toro's HLLC from the same face states) */
 } amr_options_t;
+
+#define AMR_FLUX_RUSANOV 0
+#define AMR_FLUX_HLLC 1
 
 /* Launch parameters of the batched step (amr_get_tuning), in this order:
  * CTAs per SM of the ghost fill, ghost cells per ghost-fill work item, CTAs per

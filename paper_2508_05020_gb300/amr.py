@@ -39,7 +39,9 @@ class Options(C.Structure):
                 ('mode', C.c_int), ('use_graph', C.c_int),
                 ('dev_alloc', ALLOC_FN), ('dev_free', FREE_FN), ('user', C.c_void_p),
                 ('stream', C.c_void_p), ('mlp_weights', C.c_void_p), ('mlp_n_weights', C.c_long),
-                ('autotune', C.c_int)]
+                ('autotune', C.c_int), ('flux', C.c_int)]
+
+FLUX = {'rusanov': 0, 'hllc': 1}
 
 TUNE_NAMES = ('ghost_ctas_per_sm', 'ghost_cells_per_item', 'rhs_ctas_per_sm', 'reflux_ctas_per_sm',
               'restrict_ctas_per_sm', 'cfl_ctas_per_sm', 'flag_ctas_per_sm')
@@ -133,7 +135,7 @@ class _TorchMemory:
 
 def make_options(precision=64, cfl=0.5, t_end=0.0, flagger='plain', theta_rho=0.05, theta_p=0.05,
                  max_patches=0, seed=0, amp=0.01, mode='batched', use_graph=True, torch_memory=True,
-                 autotune=False):
+                 autotune=False, flux='rusanov'):
     """Options struct plus the objects that must outlive it."""
     lib = load()
     o = Options()
@@ -150,6 +152,7 @@ def make_options(precision=64, cfl=0.5, t_end=0.0, flagger='plain', theta_rho=0.
     o.mode = MODE[mode]
     o.use_graph = 1 if use_graph else 0
     o.autotune = 1 if autotune else 0
+    o.flux = FLUX[flux]
     keep = []
     if torch_memory:
         import torch
@@ -182,7 +185,7 @@ class AMR:
             dom.bc_hi[d] = BC[w['bc'][d][1]]
         self.opt, self._keep = make_options(precision, w['cfl'], w['t_end'], flagger, w['theta_rho'],
                                             w['theta_p'], max_patches, w.get('seed', 0), w.get('amp', 0.01),
-                                            mode, use_graph, torch_memory, autotune)
+                                            mode, use_graph, torch_memory, autotune, w.get('flux', 'rusanov'))
         if mlp_weights is not None:
             self._w_host = np.ascontiguousarray(mlp_weights, dtype=np.float32)
             self.opt.mlp_weights = _ptr(self._w_host)

@@ -1019,6 +1019,8 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.theta_rho = c->opt.theta_rho;
     g.theta_p = c->opt.theta_p;
     g.ic = ic_id;
+    if (c->opt.flux != AMR_FLUX_RUSANOV && c->opt.flux != AMR_FLUX_HLLC) return bad("unknown flux");
+    g.flux = c->opt.flux;
     g.seed = c->opt.seed;
     g.amp = c->opt.amp;
     dmr_states(gamma, g.dmr_pre, g.dmr_post);

@@ -49,6 +49,7 @@ struct Grid {
     double cfl, t_end;
     double theta_rho, theta_p;
     int ic;
+    int flux;                   // AMR_FLUX_RUSANOV or AMR_FLUX_HLLC
     unsigned long long seed;
     double amp;
     int base_cells[3];

@@ -167,10 +167,13 @@ __device__ __forceinline__ void weno5_lr(const T (&w)[6], T& left, T& right) {
 // kappa = (gamma-1) / (gamma rhobar). Characteristic fields of the primitive
 // system in (p, u, T): w1 = p - z un, w2 = T - kappa p, w_t = ut, w5 = p + z un.
 // Left/right WENO5, inverse transform, first-order fallback if p or T is not
-// positive, Rusanov flux with S = max(c + |un|). Output in pencil order
-// (mass, normal momentum, tangential momenta, energy).
+// positive, Rusanov flux with S = max(c + |un|), or (flux = AMR_FLUX_HLLC)
+// the HLLC flux of the same states: wave-speed bounds S_L = min(un - c),
+// S_R = max(un + c) over the sides, contact speed S*, star states and the
+// four-way choice by the signs of S_L, S*, S_R. Output in pencil order (mass,
+// normal momentum, tangential momenta, energy).
 // ---------------------------------------------------------------------------
-template <typename T, int NT>
+template <typename T, int NT, int FLUX>
 __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], const T (&ut)[NT > 0 ? NT : 1][6],
                                           const T (&Tt)[6], T gamma, T gm1, T (&F)[NT + 3]) {
     constexpr int NF = NT + 3;
@@ -215,6 +218,7 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
     // conserved states and Euler fluxes at both sides
     T UL[NF], FL[NF], UR[NF], FR[NF];
     T sL, sR;
+    T rhoS[2], ES[2], cS[2];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         const T ps = side ? pR : pL;
@@ -246,6 +250,38 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
         Fo[NF - 1] = (E + ps) * uns;
         const T s = c + fabs(uns);
         if (side) sR = s; else sL = s;
+        rhoS[side] = rho;
+        ES[side] = E;
+        cS[side] = c;
+    }
+    if constexpr (FLUX == AMR_FLUX_HLLC) {
+        const T wL = fmin(unL - cS[0], unR - cS[1]);
+        const T wR = fmax(unL + cS[0], unR + cS[1]);
+        const T aL = rhoS[0] * (wL - unL);
+        const T aR = rhoS[1] * (wR - unR);
+        const T sM = Num<T>::div(pR - pL + aL * unL - aR * unR, aL - aR);
+        if (wL >= T(0)) {                                  // F_L, F*_L (S* >= 0), F*_R (S_R > 0), F_R
+#pragma unroll
+            for (int v = 0; v < NF; ++v) F[v] = FL[v];
+        } else if (!(sM >= T(0)) && !(wR > T(0))) {
+#pragma unroll
+            for (int v = 0; v < NF; ++v) F[v] = FR[v];
+        } else {
+            const bool left = sM >= T(0);               // the star state on the contact's upwind side
+            const T a = left ? aL : aR, w = left ? wL : wR, un_s = left ? unL : unR, p_s = left ? pL : pR;
+            const T* Uo = left ? UL : UR;
+            const T* Fo = left ? FL : FR;
+            const T f = Num<T>::div(a, w - sM);
+            T Us[NF];
+            Us[0] = f;
+            Us[1] = f * sM;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) Us[2 + j] = f * (left ? utL[j] : utR[j]);
+            Us[NF - 1] = f * (Num<T>::div(ES[left ? 0 : 1], rhoS[left ? 0 : 1]) + (sM - un_s) * (sM + Num<T>::div(p_s, a)));
+#pragma unroll
+            for (int v = 0; v < NF; ++v) F[v] = Fo[v] + w * (Us[v] - Uo[v]);
+        }
+        return;
     }
     const T hS = T(0.5) * fmax(sR, sL);
 #pragma unroll
@@ -550,7 +586,7 @@ constexpr size_t rhs_smem_bytes() {
     return sizeof(T) * ((size_t)(D + 2) * C::QN + (size_t)(D + 2) * C::FMAX);
 }
 
-template <typename T, int D, int N, int DZ, int NTH, int MINB>
+template <typename T, int D, int N, int DZ, int NTH, int MINB, int FLUX>
 __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__ Us, const T* U0,
                                              T* Uout, T* __restrict__ faces,
                                              int stage, int one_slot) {
@@ -679,7 +715,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                     if (NT >= 2) ut[NT > 1 ? 1 : 0][k] = q[(1 + t2) * C::QN + id];
                 }
                 T Fp[NT + 3];
-                face_flux<T, NT>(pp, un, ut, Tt, gamma, gm1, Fp);
+                face_flux<T, NT, FLUX>(pp, un, ut, Tt, gamma, gm1, Fp);
                 // pencil order -> global variable order
                 T Fg[NV];
                 Fg[0] = Fp[0];

@@ -35,7 +35,9 @@ static cudaError_t rhs_launch(const Grid& g, const T* Us, const T* U0, T* Uout, 
                               cudaStream_t s, int one_slot) {
     using C = RhsCfg<T, D, N>;
     constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
-    auto kern = k_rhs<T, D, N, C::DZ, C::NTH, C::MINB>;
+    // one instantiation per flux: the Rusanov kernel carries no HLLC code
+    auto kern = g.flux == AMR_FLUX_HLLC ? k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>
+                                        : k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_RUSANOV>;
     kern<<<grid, C::NTH, smem, s>>>(g, Us, U0, Uout, faces, stage, one_slot);
     return cudaGetLastError();
 }
@@ -44,8 +46,11 @@ template <typename T, int D, int N>
 static cudaError_t rhs_prepare() {
     using C = RhsCfg<T, D, N>;
     constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
-    cudaError_t e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_RUSANOV>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_flag_plain<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)flag_smem_bytes<T, D, N>());

@@ -83,6 +83,11 @@ def run_both(w, steps, regrid=True, **kw):
     ('constant', {}, 3, 0.0),
     ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2), 2, 0.0),
     ('blast3d', dict(base_cells=(32, 32, 32), patch=16, levels=2), 1, 0.0),
+    # the HLLC flux option
+    ('sod', dict(flux='hllc'), 25, 0.0),
+    ('riemann2d', dict(base_cells=(32, 32, 1), patch=8, flux='hllc'), 4, 0.0),
+    ('dmr', dict(base_cells=(64, 16, 1), patch=8, levels=3, flux='hllc'), 3, 0.0),
+    ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2, flux='hllc'), 2, 0.0),
 ])
 def test_fp64_matches_oracle(name, kw, steps, tol):
     w = workload(name, **kw)
@@ -133,6 +138,7 @@ def l1_rho_rel(gpu, ref):
     ('sod', {}, 60),
     ('riemann2d', dict(base_cells=(32, 32, 1), patch=8), 6),
     ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2), 2),
+    ('riemann2d', dict(base_cells=(32, 32, 1), patch=8, flux='hllc'), 6),
 ])
 def test_fp32_l1_against_oracle(name, kw, steps):
     # same mesh sequence: both sides regrid from their own flags; a flag near
