@@ -186,6 +186,9 @@ def main():
     ap.add_argument('--precision', type=int, default=32)
     ap.add_argument('--flagger', default='mlp', choices=['plain', 'mlp'])
     ap.add_argument('--weights', default=None, help='float32 .npy weights of the learned indicator')
+    ap.add_argument('--keep-margin', type=float, default=12.0,
+                    help='learned flags: a leaf blocks the coarsening of its parent while a band logit is above '
+                         'minus this margin (refinement still needs a logit above 0)')
     ap.add_argument('--max-patches', type=int, default=0, help='pool capacity (0: every level fully refined)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
@@ -219,7 +222,7 @@ def main():
         path = args.weights or os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights', 'indicator_d%d.npy' % w['dim'])
         weights = np.load(path).astype(np.float32)
     amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights, max_patches=args.max_patches,
-              autotune=not args.no_autotune)
+              autotune=not args.no_autotune, mlp_keep_margin=args.keep_margin)
     tuned, tuned_ms = amr.tuning()
     stream = amr._keep[1]
     amr.set_timing(True)
@@ -291,6 +294,7 @@ def main():
                 'l2': 'inputs larger than L2 (state arrays of several GB)',
                 'parallelism': 'replicas (dp%d, no data-path collective)' % world,
                 'launch_parameters': tuned, 'autotuned': not args.no_autotune,
+                'mlp_keep_margin': args.keep_margin if args.flagger == 'mlp' else None,
                 'cells_per_step': cell_counts(w, ppl)},
             'clocks': clk, 'gpu_launches': int(k1 - k0), 'roofline': roof,
             'conservation': {'relative_drift_over_timed_steps': drift,
@@ -379,7 +383,8 @@ def compare_fp64_plain(AMR, w, args, fe, weights, value):
                                  'steps': steps, 'timing': 'host wall clock around steps + regrids'}
     l1 = {}
     for name, prec, flagger in (('fp32_learned', 32, 'mlp'), ('fp32_plain', 32, 'plain'), ('fp64_batched_plain', 64, 'plain')):
-        a = AMR(w, precision=prec, flagger=flagger, mlp_weights=weights if flagger == 'mlp' else None)
+        a = AMR(w, precision=prec, flagger=flagger, mlp_weights=weights if flagger == 'mlp' else None,
+                mlp_keep_margin=args.keep_margin)
         for dt in dts:
             a.step(dt=dt)
             a.regrid()
@@ -398,7 +403,7 @@ def e2e_measure(AMR, w, args, fe, weights=None):
     amr_step + amr_regrid + amr_get_diag (time and conservation sums read
     back), and the final state is read back to host memory (amr_get_level)."""
     import numpy as np
-    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights)
+    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights, mlp_keep_margin=args.keep_margin)
     lv, co, da = [], [], []
     for l in range(w['levels']):
         c, x = amr.get_level(l)

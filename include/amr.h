@@ -108,6 +108,9 @@ typedef struct {
     int autotune;         /* 1: amr_init ends with amr_autotune on the initial hierarchy */
     int flux;             /* AMR_FLUX_RUSANOV (Sec. 3.2, Eqs. 11-12; default) or AMR_FLUX_HLLC (an
                              option the method leaves open: Toro's HLLC from the same face states) */
+    double mlp_keep_margin;  /* H >= 0, learned flagger only: a patch requests refinement if a band
+                                cell's logit is > 0 and blocks the coarsening of its parent if one
+                                is > -H (hysteresis between the two decisions; 0: the same test) */
 } amr_options_t;
 
 #define AMR_FLUX_RUSANOV 0

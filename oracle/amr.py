@@ -596,9 +596,14 @@ class Oracle:
         return flag & mask
 
     def anyflag(self, key):
+        """(refine, keep) flags of a leaf: refine requests refinement; keep
+        blocks the coarsening of its parent. The plain sensor gives one flag
+        for both; a learned flagger may return a pair (a hysteresis margin)."""
         if self.flag_override is not None:
-            return bool(self.flag_override(self, key))
-        return bool(np.any(self.patch_flags(key)))
+            f = self.flag_override(self, key)
+            return (bool(f[0]), bool(f[1])) if isinstance(f, tuple) else (bool(f), bool(f))
+        f = bool(np.any(self.patch_flags(key)))
+        return f, f
 
     def requests(self):
         """Refinement requests (leaves below the finest level with a flag) and
@@ -607,15 +612,15 @@ class Oracle:
         self.fill_ghosts(self.U, self.t)
         leaves = [k for k in self.mesh.canonical() if self.mesh.is_leaf(k)]
         af = {k: self.anyflag(k) for k in leaves}
-        req = [k for k in leaves if k[0] < self.L - 1 and af[k]]
+        req = [k for k in leaves if k[0] < self.L - 1 and af[k][0]]
         cand = []
         for k in self.mesh.canonical():
             if self.mesh.is_leaf(k):
                 continue
             ch = self.mesh.children(k)
-            if all(self.mesh.is_leaf(x) for x in ch) and not any(af[x] for x in ch):
+            if all(self.mesh.is_leaf(x) for x in ch) and not any(af[x][1] for x in ch):
                 cand.append(k)
-        return req, cand, af
+        return req, cand, {k: v[0] for k, v in af.items()}
 
     def regrid(self, resample_ic=False):
         """Flag, close under R2 (Algorithm 1), coarsen (Sec. 4.3 rule), then fill

@@ -1021,6 +1021,8 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.ic = ic_id;
     if (c->opt.flux != AMR_FLUX_RUSANOV && c->opt.flux != AMR_FLUX_HLLC) return bad("unknown flux");
     g.flux = c->opt.flux;
+    if (!(c->opt.mlp_keep_margin >= 0.0) || !(c->opt.mlp_keep_margin < 1.0e30)) return bad("mlp_keep_margin");
+    g.mlp_keep = (float)c->opt.mlp_keep_margin;
     g.seed = c->opt.seed;
     g.amp = c->opt.amp;
     dmr_states(gamma, g.dmr_pre, g.dmr_post);

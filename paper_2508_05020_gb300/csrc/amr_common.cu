@@ -44,8 +44,9 @@ cudaError_t launch_advance_time(DevTime* t, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Requests in canonical order: refine = leaf, below the finest level, flagged;
-// coarsen = has children, all children leaves, none flagged. One block; an
+// Requests in canonical order: refine = leaf, below the finest level, refine
+// bit (1) set; coarsen = has children, all children leaves, none with the keep
+// bit (2) set (the plain sensor sets both bits together). One block; an
 // exclusive scan per 1024-patch chunk (warp shuffles + shared totals) keeps
 // the canonical order of the compacted lists.
 __global__ void __launch_bounds__(1024) k_requests(Grid g, const int* anyflag, const int* rejected,
@@ -64,13 +65,13 @@ __global__ void __launch_bounds__(1024) k_requests(Grid g, const int* anyflag, c
             const int pf = g.pflag[slot];
             const int lev = g.level[slot];
             if (!(pf & 1)) {
-                r = (lev < g.L - 1 && anyflag[slot]) ? 1 : 0;
+                r = (lev < g.L - 1 && (anyflag[slot] & 1)) ? 1 : 0;
             } else {
                 const int nch = 1 << g.dim;
                 bool ok = true;
                 for (int k = 0; k < nch; ++k) {
                     const int ch = g.child[slot * 8 + k];
-                    if (ch < 0 || (g.pflag[ch] & 1) || anyflag[ch]) { ok = false; break; }
+                    if (ch < 0 || (g.pflag[ch] & 1) || (anyflag[ch] & 2)) { ok = false; break; }
                 }
                 c = ok ? 1 : 0;
             }

@@ -50,6 +50,7 @@ struct Grid {
     double theta_rho, theta_p;
     int ic;
     int flux;                   // AMR_FLUX_RUSANOV or AMR_FLUX_HLLC
+    float mlp_keep;             // learned flagger: a logit above -mlp_keep sets the keep bit
     unsigned long long seed;
     double amp;
     int base_cells[3];

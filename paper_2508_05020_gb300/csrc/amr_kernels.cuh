@@ -1062,7 +1062,7 @@ __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* any
             any = any || f;
         }
         const int res = __syncthreads_or(any);
-        if (threadIdx.x == 0 && res) atomicOr(&anyflag[slot], 1);
+        if (threadIdx.x == 0 && res) atomicOr(&anyflag[slot], 3);   // refine and keep
     }
 }
 

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
                 const int it = atomicAdd(counter, 1);
                 if (it >= total || *abort_f) return -1;
                 if constexpr (STATS) return it;
-                if (!*((volatile int*)&anyflag[g.leaf_list[it % npatch]])) return it;
+                if (!(*((volatile int*)&anyflag[g.leaf_list[it % npatch]]) & 1)) return it;
             }
         };
         int s = 0, nxt = -2;                               // nxt: the item prefetched (-2: none taken yet)
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
             if (ptid == 0) {
                 int it = nxt == -2 ? grab() : nxt;
                 if constexpr (!STATS) {                    // flagged since it was taken: skip it
-                    if (it >= 0 && *((volatile int*)&anyflag[g.leaf_list[it % npatch]])) it = grab();
+                    if (it >= 0 && (*((volatile int*)&anyflag[g.leaf_list[it % npatch]]) & 1)) it = grab();
                 }
                 s_item[0] = it;
                 s_item[1] = it >= 0 ? grab() : -1;
@@ -546,8 +546,11 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
                 const int Gd = g.coord[slot * 3 + dd] * N + lc[dd];
                 indom = indom && Gd >= 0 && Gd < g.ext[lev][dd] * N;
             }
+            // bit 0: refine (logit > 0); bit 1: keep, blocks coarsening (logit > -H)
             const bool m = indom && z > 0.f;
-            if (__any_sync(0xffffffffu, m) && lane == 0) atomicOr(&anyflag[slot], 1);
+            const bool k = indom && z > -g.mlp_keep;
+            const int bits = (__any_sync(0xffffffffu, m) ? 1 : 0) | (__any_sync(0xffffffffu, k) ? 2 : 0);
+            if (bits && lane == 0) atomicOr(&anyflag[slot], bits);
             if constexpr (STATS) {
                 unsigned long long cnt[4] = {0, 0, 0, 0};
                 if (indom) {

@@ -117,9 +117,11 @@ def test_training_learns_the_plain_flag():
     assert recall > 0.9 and precision > 0.8, (recall, precision)
 
 
-def test_fused_flags_agree_with_oracle_flagger():
+@pytest.mark.parametrize('keep,b3', [(0.0, -0.5), (1.5, -2.5)])
+def test_fused_flags_agree_with_oracle_flagger(keep, b3):
     # identical state on both sides; per-patch decisions may differ only where
-    # the oracle's largest band logit is within the BF16 margin of zero
+    # the oracle's largest band logit is within the BF16 margin of zero (the
+    # refine bit) or of -keep (the keep bit, which blocks coarsening)
     from oracle import mlp
     from oracle.amr import Oracle
     from paper_2508_05020_gb300.amr import AMR
@@ -129,11 +131,11 @@ def test_fused_flags_agree_with_oracle_flagger():
         r.step()
         r.regrid()
     p = mlp_init(5, mlp.k_in(2))
-    p['b3'][:] = -0.5
+    p['b3'][:] = b3
     wf = flat(p)
     q = mlp.unflatten(wf.astype(np.float64), mlp.k_in(2))
-    r.flag_override = mlp.make_flagger(q, 1.4)
-    g = AMR(w, flagger='mlp')
+    r.flag_override = mlp.make_flagger(q, 1.4, keep_margin=keep)
+    g = AMR(w, flagger='mlp', mlp_keep_margin=keep)
     g.set_mlp(wf)
     keys = r.mesh.canonical()
     g.set_state(np.array([k[0] for k in keys]), np.array([[k[1][0], k[1][1]] for k in keys]),
@@ -155,6 +157,12 @@ def test_fused_flags_agree_with_oracle_flagger():
     for k in sg ^ sr:
         assert abs(margin[k]) < 0.05, (k, margin[k])
     assert len(sg ^ sr) <= max(1, len(sr) // 20)
+    cgs = {(int(x[0]), (int(x[1]), int(x[2]), int(x[3]))) for x in cg}
+    crs = set(cr)
+    assert crs, 'no coarsening candidates: the case does not test the keep bit'
+    for k in cgs ^ crs:
+        assert min(abs(margin[c] + keep) for c in r.mesh.children(k)) < 0.05, k
+    assert len(cgs ^ crs) <= max(1, len(crs) // 20)
     counts = g.flag_stats()
     assert counts.sum() > 0
     g.close()

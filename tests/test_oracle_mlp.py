@@ -87,3 +87,31 @@ def test_adam_training_reduces_loss():
         mlp.adam(params, g, st, 3e-3)
     l1, _ = mlp.loss_and_grad(params, X, y, pw)
     assert l1 < 0.5 * l0
+
+
+def test_keep_margin_hysteresis():
+    # refinement requests do not depend on the keep margin; coarsening
+    # candidates shrink as it grows (a child keeps its parent refined while
+    # any band logit is above -H), margin 0 is the single-threshold flagger,
+    # and a margin above every logit leaves no candidate at all
+    from oracle.amr import Oracle
+    from synth import workload
+    w = workload('riemann2d', base_cells=(16, 16, 1), patch=8, levels=2)
+    r = Oracle(w)
+    r.step()
+    r.regrid()
+    p = mlp_init(5, mlp.k_in(2))
+    p['b3'][:] = -3.0
+    q = mlp.unflatten(mlp.flatten(p), mlp.k_in(2))
+    out = {}
+    for H in (None, 0.0, 0.5, 2.0, 1e9):
+        r.flag_override = mlp.make_flagger(q, 1.4) if H is None else mlp.make_flagger(q, 1.4, keep_margin=H)
+        rr, cr, _ = r.requests()
+        out[H] = (rr, set(cr))
+    assert out[None][1], 'no coarsening candidates: the case does not test the keep bit'
+    for H in (0.0, 0.5, 2.0, 1e9):
+        assert out[H][0] == out[None][0]
+    assert out[0.0][1] == out[None][1]
+    assert out[2.0][1] <= out[0.5][1] <= out[0.0][1]
+    assert out[2.0][1] < out[None][1]
+    assert not out[1e9][1]
