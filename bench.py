@@ -34,9 +34,9 @@ FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 
 # DRAM bytes (read + write) of one k_rhs launch (SSP-RK3 stage 1, 1536 patches) from the ncu capture
 # summarised in profiles/k_rhs_blast3d_128_fp32.md, valid while the kernel sources hash as they did then
-RHS_TRAFFIC = {'bytes': 452855296 + 171131136, 'workload': 'blast3d', 'base': 128,
-               'sources': {'paper_2508_05020_gb300/csrc/amr_kernels.cuh': '9b81136c640f4e31',
-                           'paper_2508_05020_gb300/csrc/amr_launch.cuh': '9556f0d287340bd7'}}
+RHS_TRAFFIC = {'bytes': 452924416 + 171362816, 'workload': 'blast3d', 'base': 128,
+               'sources': {'paper_2508_05020_gb300/csrc/amr_kernels.cuh': '8ab8fa153f452c5e',
+                           'paper_2508_05020_gb300/csrc/amr_launch.cuh': '632a0c161e212f9e'}}
 
 
 def rhs_traffic(workload_name, base):
