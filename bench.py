@@ -164,15 +164,22 @@ def combine_ranks(elapsed, units, dist=None, device='cpu'):
 
 # ----------------------------------------------------------------------------- GPU
 def rhs_flops_per_launch(amr, w, flops):
-    """Algorithmic FLOPs of one fused RHS launch: faces x FLOP/face + cells x FLOP/cell."""
+    """Algorithmic FLOPs of one fused RHS launch: faces x FLOP/face + cells x
+    FLOP/cell (central: N + 3 face fluxes and N + 1 conservative face values
+    per row); None for a flux without a count (HLLC)."""
     d = w['dim']
     N = w['patch']
     _, _, ppl = amr.diag()
     n_patch = int(sum(ppl))
-    faces = n_patch * d * (N + 1) * N ** (d - 1)
+    rows = n_patch * d * N ** (d - 1)
     cells = n_patch * N ** d
     f = flops[str(d)]
-    return faces * f['face'] + cells * f['cell']
+    flux = w.get('flux', 'rusanov')
+    if flux == 'central':
+        return rows * ((N + 3) * f['face_central'] + (N + 1) * f['face_combine_central']) + cells * f['cell']
+    if flux != 'rusanov':
+        return None
+    return rows * (N + 1) * f['face'] + cells * f['cell']
 
 
 def main():
@@ -255,6 +262,8 @@ def main():
     kinds, nlaunch = amr.timing()           # last timed step and its regrid
     rhs_ms = [kinds[1] / max(nlaunch[1], 1)]
     flops_rhs = [rhs_flops_per_launch(amr, w, flops)] if flops else []
+    if flops_rhs and flops_rhs[0] is None:
+        flops_rhs = []
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1000.0
@@ -274,10 +283,12 @@ def main():
     sm_max = float(peaks.get('sm_max_mhz', 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 FLOP
     roof = None
-    if flops:
+    if flops_rhs:
         avg_ms = float(np.mean(rhs_ms))
         achieved = float(np.mean(flops_rhs)) / (avg_ms / 1000.0) / 1e12
-        roof = {'bound': 'alu', 'kernel': 'k_rhs (fused WENO5 + Rusanov + SSP-RK3 stage)',
+        scheme = ('central interpolation + 4th-order staggered divergence' if w.get('flux') == 'central'
+                  else 'WENO5 + Rusanov')
+        roof = {'bound': 'alu', 'kernel': 'k_rhs (fused %s + SSP-RK3 stage)' % scheme,
                 'achieved': achieved, 'peak': fp32_peak, 'unit': 'TFLOP/s', 'frac': achieved / fp32_peak,
                 'traffic': rhs_traffic(args.workload, args.base), 'traffic_unit': 'bytes per launch (stage 1)',
                 'avg_launch_ms': avg_ms,
@@ -287,9 +298,9 @@ def main():
             'warmup': args.warmup, 'ms_per_step': 1000.0 * elapsed / args.steps, 'higher_is_better': True,
             'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32' if args.precision == 32 else 'f64',
             'data': 'synthetic',
-            'config': {'workload': '%s base %s, %d levels, %d^%d patches, FP%d, %s flags' % (
+            'config': {'workload': '%s base %s, %d levels, %d^%d patches, FP%d, %s flags, %s flux' % (
                 args.workload, 'x'.join(str(b) for b in w['base_cells'][:w['dim']]), w['levels'], w['patch'],
-                w['dim'], args.precision, args.flagger),
+                w['dim'], args.precision, args.flagger, w.get('flux', 'rusanov')),
                 'fine_equivalent_cells': fe, 'patches_per_level': [int(x) for x in ppl],
                 'l2': 'inputs larger than L2 (state arrays of several GB)',
                 'parallelism': 'replicas (dp%d, no data-path collective)' % world,

@@ -62,6 +62,9 @@ extern "C" {
 #define AMR_IC_IMPLOSION    5  /* Sec. 6, Eq. 13: |x| + |y| < 0.15: (0.125, 0.140), else (1, 1) */
 #define AMR_IC_DENSITY_WAVE 6  /* rho = 1 + 0.2 sin(2 pi x), u_x = 1, p = 1 */
 #define AMR_IC_CONSTANT     7  /* rho = 1, u = (0.3, -0.2, 0.1), p = 1 */
+#define AMR_IC_SHEAR_LAYER  8  /* Sec. 6: periodic shear layers at y = -+0.15 in (-0.3, 0.3)^2: band rho 1, outer
+                                  rho 2, p 1, u = -+dU/2 with dU = 0.7 (c1 + c2), tanh profiles of width 0.01;
+                                  v = 0.05 sin(2 pi 5 (x + 0.3) / 0.6) times Gaussians of width 0.02 at the layers */
 
 /* refinement indicators */
 #define AMR_FLAG_PLAIN 0       /* relative-jump sensor on rho and p over the patch band [-2, N+1]^d */
@@ -106,8 +109,11 @@ typedef struct {
                                   amr_set_mlp must precede the first amr_regrid */
     long mlp_n_weights;
     int autotune;         /* 1: amr_init ends with amr_autotune on the initial hierarchy */
-    int flux;             /* AMR_FLUX_RUSANOV (Sec. 3.2, Eqs. 11-12; default) or AMR_FLUX_HLLC (an
-                             option the method leaves open: Toro's HLLC from the same face states) */
+    int flux;             /* AMR_FLUX_RUSANOV (Sec. 3.2, Eqs. 11-12; default), AMR_FLUX_HLLC (an
+                             option the method leaves open: Toro's HLLC from the same face states) or
+                             AMR_FLUX_CENTRAL (Sec. 3.2's shock-free schemes: 4th-order central mid-point
+                             interpolation of p, u, T (Eq. 8), the Euler flux of that edge state, and the
+                             4th-order staggered divergence (Eq. 9) in conservative form) */
     double mlp_keep_margin;  /* H >= 0, learned flagger only: a patch requests refinement if a band
                                 cell's logit is > 0 and blocks the coarsening of its parent if one
                                 is > -H (hysteresis between the two decisions; 0: the same test) */
@@ -115,6 +121,7 @@ typedef struct {
 
 #define AMR_FLUX_RUSANOV 0
 #define AMR_FLUX_HLLC 1
+#define AMR_FLUX_CENTRAL 2
 
 /* Launch parameters of the batched step (amr_get_tuning), in this order:
  * CTAs per SM of the ghost fill, ghost cells per ghost-fill work item, CTAs per

@@ -126,6 +126,25 @@ def initial_primitive(w, X, Gidx, level):
         rho = 1.0 + 0.2 * np.sin(2.0 * math.pi * x)
         u = [one.copy()] + [zero.copy() for _ in range(dim - 1)]
         p = one.copy()
+    elif ic == 'shear_layer':
+        # two periodic shear layers at y = -0.15, 0.15 (Sec. 6): band |y| < 0.15
+        # moves with +dU/2 at rho 1, the rest with -dU/2 at rho 2 (density ratio
+        # 2), p = 1; dU = Mc (c1 + c2) for convective Mach number Mc = 0.7;
+        # tanh profiles of thickness 0.01; the transverse velocity is perturbed
+        # with 5 periods across the domain, Gaussian (width 0.02) about each layer
+        y = X[1]
+        g = w['gamma']
+        c1 = math.sqrt(g * 1.0 / 1.0)
+        c2 = math.sqrt(g * 1.0 / 2.0)
+        du = 0.7 * (c1 + c2)
+        f = 0.5 * (np.tanh((y + 0.15) / 0.01) - np.tanh((y - 0.15) / 0.01))
+        rho = 2.0 + (1.0 - 2.0) * f
+        ux = -0.5 * du + du * f
+        a = (y - 0.15) / 0.02
+        b = (y + 0.15) / 0.02
+        uy = 0.05 * np.sin(2.0 * math.pi * 5.0 * (x + 0.3) / 0.6) * (np.exp(-(a * a)) + np.exp(-(b * b)))
+        u = [ux, uy] + [zero.copy() for _ in range(dim - 2)]
+        p = one.copy()
     elif ic == 'constant':
         vel = (0.3, -0.2, 0.1)
         rho = one.copy()

@@ -208,6 +208,45 @@ def face_flux(P, dim, gamma, flux='rusanov'):
     return [0.5 * (FR[v] + FL[v]) - hS * (UR[v] - UL[v]) for v in range(dim + 2)]
 
 
+def central_mid(a, b, c, d):
+    """4th-order central mid-point value at x_{i+1/2} from nodes i-1 .. i+2
+    (Sec. 3.2, Eq. 8, read with the node and edge roles the other way round:
+    the printed form gives a node value from edge values):
+    (9 (phi_i + phi_{i+1}) - (phi_{i-1} + phi_{i+2})) / 16, exact for cubics."""
+    return (9.0 * (b + c) - (a + d)) * 0.0625
+
+
+def central_face_flux(P, dim, gamma):
+    """Shock-free face flux (Sec. 3.2: central mid-point interpolation of the
+    primitive set p, T, u_j, then the flux assembled at the edge point).
+
+    P is a list of 4 pencil nodes (i-1 .. i+2), each a tuple (p, un, ut, T) as
+    in `face_flux`. Each of p, un, ut, T is interpolated with `central_mid`; if
+    p or T is not positive there, the face takes the mean of nodes i and i+1
+    (a guard the paper leaves open). The flux is the Euler flux of that single
+    edge state: no upwinding and no dissipation. Returns it in pencil order.
+    """
+    gm1 = gamma - 1.0
+    nt = dim - 1
+    p = central_mid(P[0][0], P[1][0], P[2][0], P[3][0])
+    un = central_mid(P[0][1], P[1][1], P[2][1], P[3][1])
+    ut = [central_mid(P[0][2][j], P[1][2][j], P[2][2][j], P[3][2][j]) for j in range(nt)]
+    T = central_mid(P[0][3], P[1][3], P[2][3], P[3][3])
+    bad = ~((p > 0.0) & (T > 0.0))
+    if np.any(bad):
+        p = np.where(bad, 0.5 * (P[1][0] + P[2][0]), p)
+        un = np.where(bad, 0.5 * (P[1][1] + P[2][1]), un)
+        ut = [np.where(bad, 0.5 * (P[1][2][j] + P[2][2][j]), ut[j]) for j in range(nt)]
+        T = np.where(bad, 0.5 * (P[1][3] + P[2][3]), T)
+    rho = p / T
+    usq = un * un
+    for j in range(nt):
+        usq = usq + ut[j] * ut[j]
+    E = p / gm1 + 0.5 * rho * usq
+    mn = rho * un
+    return [mn, mn * un + p] + [mn * ut[j] for j in range(nt)] + [(E + p) * un]
+
+
 def pencil_to_global(F, dim, d):
     """Map a flux in pencil order (mass, normal, tangentials, energy) back to
     the global order (mass, m_0 .. m_{d-1}, energy) for a face normal to d."""
@@ -224,6 +263,14 @@ def pencil_to_global(F, dim, d):
 def patch_rhs(A, dim, N, g, dx, gamma, flux='rusanov'):
     """Right-hand side R = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d on a patch interior
     (Sec. 3.2, Eq. 10: divergence of the Riemann fluxes; dims in order x, y, z).
+
+    With flux='central' (the shock-free schemes of Sec. 3.2) the face fluxes
+    come from `central_face_flux` at faces i-3/2 .. N+1/2 and the divergence is
+    the 4th-order staggered difference of Eq. 9,
+    (27 (F_{i+1/2} - F_{i-1/2}) - (F_{i+3/2} - F_{i-3/2})) / (24 dx), evaluated
+    in its conservative form: the difference of the face values
+    G_{i+1/2} = (26 F_{i+1/2} - F_{i-1/2} - F_{i+3/2}) / 24, so that sums over
+    patches telescope and the coarse-fine correction acts on G.
 
     A: slot array (nv, Z, Y, X) with g ghost layers in every active dimension
     (array axis 3 - d holds dimension d). Returns (R, faces) where R has the
@@ -242,14 +289,29 @@ def patch_rhs(A, dim, N, g, dx, gamma, flux='rusanov'):
         ax = 3 - d
         tdims = [e for e in range(dim) if e != d]
         P = []
-        for k in range(6):
-            sl = list(inner)
-            sl[ax] = slice(k, k + N + 1)   # faces i+1/2, i = -1..N-1
-            sl = tuple(sl[1:])
-            P.append((p[sl], u[d][sl], [u[e][sl] for e in tdims], T[sl]))
-        Fp = face_flux(P, dim, gamma, flux)
-        F = pencil_to_global(Fp, dim, d)
-        F = np.stack(F)                      # (nv, ..., N+1 along ax)
+        if flux == 'central':
+            for k in range(4):
+                sl = list(inner)
+                sl[ax] = slice(k, k + N + 3)   # faces i+1/2, i = -2..N (nodes i-1..i+2)
+                sl = tuple(sl[1:])
+                P.append((p[sl], u[d][sl], [u[e][sl] for e in tdims], T[sl]))
+            Fc = np.stack(pencil_to_global(central_face_flux(P, dim, gamma), dim, d))
+            mid = [slice(None)] * 4
+            below = [slice(None)] * 4
+            above = [slice(None)] * 4
+            mid[ax] = slice(1, N + 2)
+            below[ax] = slice(0, N + 1)
+            above[ax] = slice(2, N + 3)
+            F = (26.0 * Fc[tuple(mid)] - Fc[tuple(below)] - Fc[tuple(above)]) / 24.0
+        else:
+            for k in range(6):
+                sl = list(inner)
+                sl[ax] = slice(k, k + N + 1)   # faces i+1/2, i = -1..N-1
+                sl = tuple(sl[1:])
+                P.append((p[sl], u[d][sl], [u[e][sl] for e in tdims], T[sl]))
+            Fp = face_flux(P, dim, gamma, flux)
+            F = pencil_to_global(Fp, dim, d)
+            F = np.stack(F)                      # (nv, ..., N+1 along ax)
         hi = [slice(None)] * 4
         lo = [slice(None)] * 4
         hi[ax] = slice(1, N + 1)

@@ -1,9 +1,10 @@
 """Instrumented FLOP count of the oracle's face flux and cell update.
 
 Test infrastructure (see ``oracle/__init__``). Runs ``euler.face_flux`` (Sec. 3.2,
-Eqs. 10-12), the primitive-variable conversion and the SSP-RK3 stage update
-on a scalar type that counts every floating-point operation, and writes
-``flop_counts.json`` beside this file. Each +, -, *, /, sqrt, |.| and max counts
+Eqs. 10-12), ``euler.central_face_flux`` (Sec. 3.2, Eq. 8), the
+primitive-variable conversion and the SSP-RK3 stage update on a scalar type
+that counts every floating-point operation, and writes ``flop_counts.json``
+beside this file. Each +, -, *, /, sqrt, |.| and max counts
 as one FLOP (a fused multiply-add on the GPU performs two of them).
 
     python -m oracle.flopcount
@@ -72,6 +73,9 @@ def count(dim, gamma=1.4):
         _Count.n = 0
         euler.face_flux(P, dim, F(gamma))
         face = _Count.n
+        _Count.n = 0
+        euler.central_face_flux(P[1:5], dim, F(gamma))
+        face_central = _Count.n
         # one conversion to primitives per cell
         U = [F(1.1)] + [F(0.1)] * dim + [F(2.6)]
         _Count.n = 0
@@ -84,14 +88,19 @@ def count(dim, gamma=1.4):
     div = dim * nv * 3
     # stage update a U0 + b (Us + dt R): 5 operations per variable
     upd = nv * 5
-    return {'face': face, 'cell': prim + div + upd, 'primitives': prim, 'divergence': div, 'update': upd}
+    # central: the conservative face value G = (26 F_f - F_{f-1} - F_{f+1}) / 24
+    # of Eq. 9, 4 operations per variable on each of the N + 1 faces of a row
+    return {'face': face, 'cell': prim + div + upd, 'primitives': prim, 'divergence': div, 'update': upd,
+            'face_central': face_central, 'face_combine_central': nv * 4}
 
 
 def main():
     out = {str(d): count(d) for d in (1, 2, 3)}
     out['note'] = ('FLOPs counted by running the oracle on a counting scalar: face = one Rusanov '
                    'face flux (characteristic WENO5-JS, Eqs. 10-12); cell = primitives + divergence + '
-                   'SSP-RK3 stage update of one cell')
+                   'SSP-RK3 stage update of one cell; face_central = one central face flux (Eq. 8), '
+                   'N + 3 of them per row; face_combine_central = the conservative face value of '
+                   'Eq. 9, N + 1 per row')
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'flop_counts.json')
     with open(path, 'w') as f:
         json.dump(out, f, indent=1)

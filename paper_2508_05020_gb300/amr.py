@@ -19,7 +19,7 @@ ERRORS = {-1: 'AMR_ERR_ARG', -2: 'AMR_ERR_POOL', -3: 'AMR_ERR_CUDA', -4: 'AMR_ER
           -5: 'AMR_ERR_TIMEOUT', -6: 'AMR_ERR_STATE', -7: 'AMR_ERR_MESH'}
 BC = {'outflow': 0, 'reflect': 1, 'periodic': 2, 'dmr_inflow': 3, 'dmr_bottom': 4, 'dmr_top': 5}
 IC = {'sod': 0, 'shu_osher': 1, 'riemann2d': 2, 'dmr': 3, 'blast3d': 4, 'implosion': 5,
-      'density_wave': 6, 'constant': 7}
+      'density_wave': 6, 'constant': 7, 'shear_layer': 8}
 FLAGGER = {'plain': 0, 'mlp': 1}
 MODE = {'batched': 0, 'per_patch': 1}
 
@@ -42,7 +42,7 @@ class Options(C.Structure):
                 ('autotune', C.c_int), ('flux', C.c_int),
                 ('mlp_keep_margin', C.c_double)]
 
-FLUX = {'rusanov': 0, 'hllc': 1}
+FLUX = {'rusanov': 0, 'hllc': 1, 'central': 2}
 
 TUNE_NAMES = ('ghost_ctas_per_sm', 'ghost_cells_per_item', 'rhs_ctas_per_sm', 'reflux_ctas_per_sm',
               'restrict_ctas_per_sm', 'cfl_ctas_per_sm', 'flag_ctas_per_sm')

@@ -932,7 +932,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     if (levels < 1 || levels > MAXL) return bad("levels must be in [1, 8]");
     if (!(gamma > 1.0)) return bad("gamma must exceed 1");
     if (c->opt.precision != 32 && c->opt.precision != 64) return bad("precision must be 32 or 64");
-    if (ic_id < AMR_IC_SOD || ic_id > AMR_IC_CONSTANT) return bad("unknown initial condition");
+    if (ic_id < AMR_IC_SOD || ic_id > AMR_IC_SHEAR_LAYER) return bad("unknown initial condition");
     if (!(c->opt.cfl > 0.0)) return bad("cfl must be positive");
     if (c->opt.flagger != AMR_FLAG_PLAIN && c->opt.flagger != AMR_FLAG_MLP) return bad("unknown flagger");
     if (c->opt.mode != AMR_MODE_BATCHED && c->opt.mode != AMR_MODE_PER_PATCH) return bad("unknown mode");
@@ -1019,7 +1019,8 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.theta_rho = c->opt.theta_rho;
     g.theta_p = c->opt.theta_p;
     g.ic = ic_id;
-    if (c->opt.flux != AMR_FLUX_RUSANOV && c->opt.flux != AMR_FLUX_HLLC) return bad("unknown flux");
+    if (c->opt.flux != AMR_FLUX_RUSANOV && c->opt.flux != AMR_FLUX_HLLC && c->opt.flux != AMR_FLUX_CENTRAL)
+        return bad("unknown flux");
     g.flux = c->opt.flux;
     if (!(c->opt.mlp_keep_margin >= 0.0) || !(c->opt.mlp_keep_margin < 1.0e30)) return bad("mlp_keep_margin");
     g.mlp_keep = (float)c->opt.mlp_keep_margin;

@@ -288,6 +288,42 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
     for (int v = 0; v < NF; ++v) F[v] = T(0.5) * (FR[v] + FL[v]) - hS * (UR[v] - UL[v]);
 }
 
+// ---------------------------------------------------------------------------
+// Shock-free face flux (Sec. 3.2, Eq. 8 read as the edge value from node
+// values): p, u_n, u_t, T at the face from pencil nodes 1..4 (cells i-1 ..
+// i+2) by (9 (phi_i + phi_{i+1}) - (phi_{i-1} + phi_{i+2})) / 16; if p or T is
+// not positive there, the mean of nodes 2 and 3. The flux is the Euler flux of
+// that one edge state (no dissipation). Output in pencil order.
+// ---------------------------------------------------------------------------
+template <typename T, int NT>
+__device__ __forceinline__ void central_flux(const T (&p)[6], const T (&un)[6], const T (&ut)[NT > 0 ? NT : 1][6],
+                                             const T (&Tt)[6], T gm1, T (&F)[NT + 3]) {
+    constexpr int NF = NT + 3;
+    auto mid = [](const T (&v)[6]) { return (T(9) * (v[2] + v[3]) - (v[1] + v[4])) * T(0.0625); };
+    T pf = mid(p), unf = mid(un), Tf = mid(Tt);
+    T utf[NT > 0 ? NT : 1];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) utf[j] = mid(ut[j]);
+    if (!(pf > T(0)) || !(Tf > T(0))) {
+        pf = T(0.5) * (p[2] + p[3]);
+        unf = T(0.5) * (un[2] + un[3]);
+        Tf = T(0.5) * (Tt[2] + Tt[3]);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) utf[j] = T(0.5) * (ut[j][2] + ut[j][3]);
+    }
+    const T rho = Num<T>::div(pf, Tf);
+    T usq = unf * unf;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) usq = usq + utf[j] * utf[j];
+    const T E = Num<T>::div(pf, gm1) + T(0.5) * rho * usq;
+    const T mn = rho * unf;
+    F[0] = mn;
+    F[1] = mn * unf + pf;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) F[2 + j] = mn * utf[j];
+    F[NF - 1] = (E + pf) * unf;
+}
+
 // Metadata of one patch staged in shared memory by the CTA that serves it:
 // level, coordinates, its 27-entry neighbour table and its parent's.
 struct PatchMeta {
@@ -561,7 +597,9 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
 // divergence of its own cells in registers, then writes
 // U_out = a U0 + b (U_s + dt R)  (a = 0, b = 1 in stage 1).
 // ---------------------------------------------------------------------------
-template <int D, int N, int DZ> struct Chunk {
+// EXT: extra faces per dimension beyond the N + 1 of a patch row (2 for the
+// central scheme, whose divergence reads the faces at i -+ 3/2)
+template <int D, int N, int DZ, int EXT = 0> struct Chunk {
     static constexpr int S = N + 2 * G;
     static constexpr int CX = N, CY = D >= 2 ? N : 1, CZ = D == 3 ? DZ : 1;
     // staged cells per variable: 1D/2D the whole slot; 3D the DZ centre planes
@@ -573,16 +611,16 @@ template <int D, int N, int DZ> struct Chunk {
     static constexpr int QN = QC + QH;
     static constexpr int CELLS = CX * CY * CZ;
     static constexpr int NCH = D == 3 ? N / DZ : 1;
-    static constexpr int F0 = (CX + 1) * CY * CZ;
-    static constexpr int F1 = D >= 2 ? CX * (CY + 1) * CZ : 0;
-    static constexpr int F2 = D == 3 ? CX * CY * (CZ + 1) : 0;
+    static constexpr int F0 = (CX + 1 + EXT) * CY * CZ;
+    static constexpr int F1 = D >= 2 ? CX * (CY + 1 + EXT) * CZ : 0;
+    static constexpr int F2 = D == 3 ? CX * CY * (CZ + 1 + EXT) : 0;
     static constexpr int FMAX = F0 > F1 ? (F0 > F2 ? F0 : F2) : (F1 > F2 ? F1 : F2);
     static constexpr int TRANS = D == 1 ? 1 : (D == 2 ? N : N * N);   // cells on a patch face
 };
 
-template <typename T, int D, int N, int DZ>
+template <typename T, int D, int N, int DZ, int FLUX>
 constexpr size_t rhs_smem_bytes() {
-    using C = Chunk<D, N, DZ>;
+    using C = Chunk<D, N, DZ, FLUX == AMR_FLUX_CENTRAL ? 2 : 0>;
     return sizeof(T) * ((size_t)(D + 2) * C::QN + (size_t)(D + 2) * C::FMAX);
 }
 
@@ -590,7 +628,9 @@ template <typename T, int D, int N, int DZ, int NTH, int MINB, int FLUX>
 __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__ Us, const T* U0,
                                              T* Uout, T* __restrict__ faces,
                                              int stage, int one_slot) {
-    using C = Chunk<D, N, DZ>;
+    constexpr bool CEN = FLUX == AMR_FLUX_CENTRAL;
+    constexpr int EXT = CEN ? 2 : 0;                   // central: faces i - 3/2 .. N + 1/2 along d
+    using C = Chunk<D, N, DZ, EXT>;
     constexpr int NV = D + 2;
     constexpr int NT = D - 1;
     constexpr int CPT = (C::CELLS + NTH - 1) / NTH;
@@ -675,7 +715,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
 #pragma unroll 1
         for (int d = 0; d < D; ++d) {
             const int ex = d == 0, ey = d == 1, ez = d == 2;
-            const int FX = C::CX + ex, FY = C::CY + ey, FZ = C::CZ + ez;
+            const int FX = C::CX + ex * (1 + EXT), FY = C::CY + ey * (1 + EXT), FZ = C::CZ + ez * (1 + EXT);
             const int nf = FX * FY * FZ;
             // f -> (fi, fj, fk) by multiply-high division, exact for f * FX < 2^32
             const unsigned mFX = 0xFFFFFFFFu / (unsigned)FX + 1u;
@@ -689,21 +729,23 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 const int fk = D == 1 ? 0 : (int)__umulhi((unsigned)q1, mFY);
                 const int fi = f - q1 * FX;
                 const int fj = q1 - fk * FY;
-                // smem index of pencil node 0 (cell index - 3 along d; G = 3)
+                // smem index of pencil node 0 (cell index - 3 along d; G = 3).
+                // Central: face index a along d is the face i - 1/2 of cell
+                // i = a - 1, and only nodes 1..4 (cells i - 2 .. i + 1) are read
                 int base = 0;
                 if (d < 2) {
-                    const int bx = fi + G - (ex ? G : 0);
-                    const int by = (D >= 2 ? fj + G : 0) - (ey ? G : 0);
+                    const int bx = fi + G - (ex ? G + EXT / 2 : 0);
+                    const int by = (D >= 2 ? fj + G : 0) - (ey ? G + EXT / 2 : 0);
                     base = ((D == 3 ? fk : 0) * C::QY + by) * C::QX + bx;
                 }
                 T pp[6], un[6], ut[NT > 0 ? NT : 1][6], Tt[6];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
+                for (int k = CEN ? 1 : 0; k < (CEN ? 5 : 6); ++k) {
                     int id;
                     if (D < 3 || d < 2) {
                         id = base + k * step;
                     } else {                                 // z pencil: halo plane or centre plane
-                        const int zz = fk + k;               // staged z index 0 .. DZ + 5
+                        const int zz = fk + k - EXT / 2;     // staged z index 0 .. DZ + 5
                         id = (zz >= G && zz < G + DZ)
                                  ? ((zz - G) * C::QY + fj + G) * C::QX + fi + G
                                  : C::QC + ((zz < G ? zz : zz - DZ) * N + fj) * N + fi;
@@ -715,7 +757,8 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                     if (NT >= 2) ut[NT > 1 ? 1 : 0][k] = q[(1 + t2) * C::QN + id];
                 }
                 T Fp[NT + 3];
-                face_flux<T, NT, FLUX>(pp, un, ut, Tt, gamma, gm1, Fp);
+                if constexpr (CEN) central_flux<T, NT>(pp, un, ut, Tt, gm1, Fp);
+                else face_flux<T, NT, FLUX>(pp, un, ut, Tt, gamma, gm1, Fp);
                 // pencil order -> global variable order
                 T Fg[NV];
                 Fg[0] = Fp[0];
@@ -726,9 +769,10 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Fs[v * C::FMAX + f] = Fg[v];
                 // patch-boundary faces needed by the coarse-fine flux correction
+                // (central: the conservative face values, saved by the divergence)
                 const int fd = d == 0 ? fi : (d == 1 ? fj : fk + z0);
                 const int side = fd == 0 ? 0 : (fd == N ? 1 : -1);
-                if (side >= 0 && ((pf >> (8 + 2 * d + side)) & 1)) {
+                if (!CEN && side >= 0 && ((pf >> (8 + 2 * d + side)) & 1)) {
                     int tidx;
                     if (D == 1) tidx = 0;
                     else if (D == 2) tidx = d == 0 ? fj : fi;
@@ -749,13 +793,41 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                     const int ci = cidx % C::CX;
                     const int cj = (cidx / C::CX) % C::CY;
                     const int ck = cidx / (C::CX * C::CY);
-                    const int flo = (ck * FY + cj) * FX + ci;
+                    const int flo = (ck * FY + cj) * FX + ci + (CEN ? fstep : 0);
                     const int fhi = flo + fstep;
+                    if constexpr (CEN) {
+                        // Eq. 9 as the difference of G = (26 F_f - F_{f-1} - F_{f+1}) / 24
+                        const int cd = d == 0 ? ci : (d == 1 ? cj : ck + z0);
+                        const int side = cd == 0 ? 0 : (cd == N - 1 ? 1 : -1);
+                        const bool save = side >= 0 && ((pf >> (8 + 2 * d + side)) & 1);
+                        T* dst = nullptr;
+                        if (save) {
+                            int tidx;
+                            if (D == 1) tidx = 0;
+                            else if (D == 2) tidx = d == 0 ? cj : ci;
+                            else tidx = d == 0 ? (ck + z0) * N + cj : (d == 1 ? (ck + z0) * N + ci : cj * N + ci);
+                            dst = faces + ((long long)slot * 2 * D + 2 * d + side) * NV * C::TRANS + tidx;
+                        }
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        const T df = Fs[v * C::FMAX + fhi] - Fs[v * C::FMAX + flo];
-                        const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
-                        R[n][v] = d == 0 ? -dv : R[n][v] - dv;
+                        for (int v = 0; v < NV; ++v) {
+                            const T* Fv = Fs + v * C::FMAX;
+                            const T flo_m = Fv[flo - fstep], flo_c = Fv[flo], fhi_c = Fv[fhi], fhi_p = Fv[fhi + fstep];
+                            T glo = T(26) * flo_c - flo_m - fhi_c;
+                            T ghi = T(26) * fhi_c - flo_c - fhi_p;
+                            if constexpr (sizeof(T) == 4) { glo = glo * T(1.0 / 24.0); ghi = ghi * T(1.0 / 24.0); }
+                            else { glo = glo / T(24); ghi = ghi / T(24); }
+                            if (save) dst[v * C::TRANS] = side ? ghi : glo;
+                            const T df = ghi - glo;
+                            const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
+                            R[n][v] = d == 0 ? -dv : R[n][v] - dv;
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) {
+                            const T df = Fs[v * C::FMAX + fhi] - Fs[v * C::FMAX + flo];
+                            const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
+                            R[n][v] = d == 0 ? -dv : R[n][v] - dv;
+                        }
                     }
                 }
             }
@@ -1124,6 +1196,17 @@ __device__ void ic_primitive(const Grid& g, const double* X, const int* Gi, int 
     case AMR_IC_DENSITY_WAVE: {
         rho = 1.0 + 0.2 * sin(2.0 * 3.141592653589793 * x);
         u[0] = 1.0;
+        p = 1.0;
+    } break;
+    case AMR_IC_SHEAR_LAYER: {
+        const double y = X[1];
+        const double c1 = sqrt(g.gamma * 1.0 / 1.0), c2 = sqrt(g.gamma * 1.0 / 2.0);
+        const double du = 0.7 * (c1 + c2);
+        const double f = 0.5 * (tanh((y + 0.15) / 0.01) - tanh((y - 0.15) / 0.01));
+        rho = 2.0 + (1.0 - 2.0) * f;
+        u[0] = -0.5 * du + du * f;
+        const double a = (y - 0.15) / 0.02, b = (y + 0.15) / 0.02;
+        u[1] = 0.05 * sin(2.0 * 3.141592653589793 * 5.0 * (x + 0.3) / 0.6) * (exp(-(a * a)) + exp(-(b * b)));
         p = 1.0;
     } break;
     default: {   // AMR_IC_CONSTANT

@@ -34,23 +34,36 @@ template <typename T, int D, int N>
 static cudaError_t rhs_launch(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
                               cudaStream_t s, int one_slot) {
     using C = RhsCfg<T, D, N>;
-    constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
     // one instantiation per flux: the Rusanov kernel carries no HLLC code
-    auto kern = g.flux == AMR_FLUX_HLLC ? k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>
-                                        : k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_RUSANOV>;
-    kern<<<grid, C::NTH, smem, s>>>(g, Us, U0, Uout, faces, stage, one_slot);
+    if (g.flux == AMR_FLUX_CENTRAL)
+        k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_CENTRAL>
+            <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_CENTRAL>(), s>>>(g, Us, U0, Uout, faces, stage,
+                                                                                   one_slot);
+    else if (g.flux == AMR_FLUX_HLLC)
+        k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>
+            <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HLLC>(), s>>>(g, Us, U0, Uout, faces, stage,
+                                                                                one_slot);
+    else
+        k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_RUSANOV>
+            <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_RUSANOV>(), s>>>(g, Us, U0, Uout, faces, stage,
+                                                                                   one_slot);
     return cudaGetLastError();
 }
 
 template <typename T, int D, int N>
 static cudaError_t rhs_prepare() {
     using C = RhsCfg<T, D, N>;
-    constexpr size_t smem = rhs_smem_bytes<T, D, N, C::DZ>();
     cudaError_t e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_RUSANOV>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_RUSANOV>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HLLC>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_CENTRAL>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_CENTRAL>());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_flag_plain<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)flag_smem_bytes<T, D, N>());

@@ -18,13 +18,15 @@ ic             initial-condition name
 cfl            CFL number
 t_end          final time (the time step is clipped to it)
 theta_rho/p    thresholds of the relative-jump refinement sensor
-flux           numerical flux at faces: 'rusanov' (Sec. 3.2) or 'hllc' (an option)
+flux           numerical flux at faces: 'rusanov' (Sec. 3.2), 'hllc' (an option) or
+               'central' (the shock-free central interpolation and 4th-order
+               staggered divergence of Sec. 3.2, Eqs. 8-9)
 seed           seed of the +-1 % density perturbation (blast only)
 amp            amplitude of that perturbation (blast only; 0.01)
 
 The five named workloads are the shock-tube, shock-entropy, four-quadrant,
 double-Mach-reflection and 3D blast problems; ``implosion`` is the periodic
-demonstration problem of Sec. 6 (Eq. 13).
+demonstration problem of Sec. 6 (Eq. 13) and ``shear2d`` its second one.
 """
 import copy
 
@@ -74,6 +76,17 @@ WORKLOADS = {
                          bc=(_PER, _UNUSED, _UNUSED), gamma=1.4,
                          base_cells=(64, 1, 1), levels=1, patch=16, ic='density_wave',
                          cfl=0.5, t_end=0.0, theta_rho=0.05, theta_p=0.05, seed=0),
+    # Periodic shear layers (Sec. 6, second demonstration): (-0.3, 0.3)^2, density
+    # ratio 2, convective Mach number 0.7, perturbation with 5 periods across the
+    # domain; shock-free, so the central schemes of Sec. 3.2 (flux 'central').
+    # 1024^2 finest-equivalent cells = 256^2 base with 3 levels; CFL 0.45 as the
+    # implosion. Sensor thresholds 0.01: the tanh layers (width 0.01, about 4
+    # base cells) give relative jumps near 0.04 on level 0 and 0.02 on level 1,
+    # so both coarse levels refine about them.
+    'shear2d': dict(dim=2, lo=(-0.3, -0.3, 0.0), hi=(0.3, 0.3, 1.0),
+                    bc=(_PER, _PER, _UNUSED), gamma=1.4,
+                    base_cells=(256, 256, 1), levels=3, patch=16, ic='shear_layer',
+                    cfl=0.45, t_end=0.0, theta_rho=0.01, theta_p=0.01, seed=0, flux='central'),
     # Uniform state rho = 1, u = (0.3, -0.2, 0.1), p = 1 (for constant preservation).
     'constant': dict(dim=2, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
                      bc=(_PER, _OUT, _UNUSED), gamma=1.4,

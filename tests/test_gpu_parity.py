@@ -88,6 +88,11 @@ def run_both(w, steps, regrid=True, **kw):
     ('riemann2d', dict(base_cells=(32, 32, 1), patch=8, flux='hllc'), 4, 0.0),
     ('dmr', dict(base_cells=(64, 16, 1), patch=8, levels=3, flux='hllc'), 3, 0.0),
     ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2, flux='hllc'), 2, 0.0),
+    # the shock-free central schemes (Eqs. 8-9); Sod exercises their positivity guard
+    ('density_wave', dict(levels=2, patch=16, flux='central'), 5, TOL64),
+    ('sod', dict(flux='central'), 8, 0.0),
+    ('shear2d', dict(base_cells=(32, 32, 1), patch=8, levels=3), 4, TOL64),
+    ('shear2d', dict(base_cells=(64, 64, 1), patch=16, levels=3), 2, TOL64),
 ])
 def test_fp64_matches_oracle(name, kw, steps, tol):
     w = workload(name, **kw)
@@ -275,4 +280,61 @@ def test_invalid_arguments_rejected():
         g.set_state(np.array([0] * 16 + [1]), np.array([[i % 4, i // 4] for i in range(16)] + [[0, 0]]),
                     np.ones((17, 4, 8, 8)))
     assert 'MESH' in str(e.value)
+    g.close()
+
+
+def smooth3d_hierarchy(patch, levels, flux):
+    """A refined 3D hierarchy (the shear layers, refined about y = -+0.15,
+    which the domain places inside patches so that refinement is partial)
+    carrying a smooth periodic field that varies along x, y and z, on the
+    oracle."""
+    w = workload('shear2d', dim=3, base_cells=(16, 16, 16), patch=patch, levels=levels, flux=flux,
+                 lo=(-0.3, -0.35, -0.3), hi=(0.3, 0.25, 0.3), theta_rho=0.05, theta_p=0.05,
+                 bc=(('periodic', 'periodic'),) * 3)
+    r = oracle(w)
+    from oracle import euler
+    for k in r.mesh.canonical():
+        _, X = r.cells(k, [0, 0, 0], [r.N] * 3)
+        ph = 2.0 * np.pi * (X[0] + 2.0 * X[1] - X[2]) / 0.6
+        rho = 1.0 + 0.2 * np.sin(ph)
+        u = [0.3 + 0.1 * np.cos(ph), -0.2 + 0.05 * np.sin(2.0 * ph), 0.1 * np.cos(ph + 2.0 * np.pi * X[2] / 0.6)]
+        pr = 1.0 + 0.1 * np.cos(ph)
+        r.U[k][r.inner()] = np.stack(euler.conserved_from_primitive(rho, u, pr, 1.4))
+    return w, r
+
+
+@pytest.mark.parametrize('patch,levels', [(8, 3), (16, 2)])
+def test_fp64_central_3d_bitwise_given_identical_state(patch, levels):
+    # every dimension's pencils see variation (the z pencils included)
+    w, r = smooth3d_hierarchy(patch, levels, 'central')
+    n = [len(r.mesh.level_list(l)) for l in range(levels)]
+    assert n[-1] > 0 and (levels == 2 or n[-1] < 8 * n[-2]), n
+    g = amr(w)
+    keys = r.mesh.canonical()
+    g.set_state(np.array([k[0] for k in keys]), np.array([list(k[1]) for k in keys]),
+                np.stack([r.U[k][r.inner()] for k in keys]), t=0.0)
+    compare(g, r, tol=0.0)
+    for _ in range(2):
+        dr = r.step()
+        dg = g.step()
+        assert dg == dr
+    compare(g, r, tol=0.0)
+    g.close()
+
+
+@pytest.mark.parametrize('name,kw,steps', [
+    ('shear2d', dict(base_cells=(64, 64, 1), patch=16, levels=3), 4),
+    ('density_wave', dict(levels=2, patch=16, flux='central'), 20),
+])
+def test_fp32_central_l1_rho(name, kw, steps):
+    w = workload(name, **kw)
+    g = amr(w, precision=32)
+    r = oracle(w)
+    for _ in range(steps):
+        dt = r.step()
+        g.step(dt)
+        r.regrid()
+        g.regrid()
+    err = l1_rho_rel(g, r)
+    assert err <= 1e-5, err
     g.close()

@@ -335,3 +335,114 @@ def test_constant_state_preserved():
         assert np.allclose(A[0], 1.0, rtol=0, atol=1e-14)
         assert np.allclose(A[1], 0.3, rtol=0, atol=1e-14)
         assert np.allclose(A[2], -0.2, rtol=0, atol=1e-14)
+
+
+def test_central_mid_point_is_exact_for_cubics():
+    # Eq. 8 (read as the edge value from node values) is the cubic through
+    # nodes i-1 .. i+2 evaluated at the mid-point
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        c = rng.normal(size=4)
+        f = lambda x: ((c[3] * x + c[2]) * x + c[1]) * x + c[0]
+        v = euler.central_mid(f(-1.0), f(0.0), f(1.0), f(2.0))
+        assert abs(v - f(0.5)) <= 1e-13 * max(1.0, np.max(np.abs(c)))
+    # and not for a quartic: the stencil has exactly 4th-order accuracy
+    g = lambda x: x ** 4
+    assert abs(euler.central_mid(g(-1.0), g(0.0), g(1.0), g(2.0)) - g(0.5)) > 0.1
+
+
+def central_rhs_error(n):
+    """Max error of the central right-hand side of a smooth periodic wave
+    against its exact value: rho = 1 + 0.2 sin(2 pi x), u = 1, p = 1 gives
+    R = -(rho', rho', rho'/2) (mass, momentum, energy)."""
+    g = 3
+    dx = 1.0 / n
+    x = (np.arange(-g, n + g) + 0.5) * dx
+    rho = 1.0 + 0.2 * np.sin(2.0 * math.pi * x)
+    A = np.stack(euler.conserved_from_primitive(rho, [np.ones_like(x)], np.ones_like(x), 1.4))
+    R, _ = euler.patch_rhs(A.reshape(3, 1, 1, -1), 1, n, g, [dx], 1.4, flux='central')
+    xi = x[g:g + n]
+    drho = 0.2 * 2.0 * math.pi * np.cos(2.0 * math.pi * xi)
+    ex = np.stack([-drho, -drho, -0.5 * drho])
+    return np.max(np.abs(R.reshape(3, n) - ex))
+
+
+def test_central_divergence_is_fourth_order():
+    # Eqs. 8-9 together: halving dx divides the error of the right-hand side
+    # by 16 (2^4); a second-order slip (a wrong weight) would give 4
+    e = [central_rhs_error(n) for n in (16, 32, 64)]
+    assert e[0] / e[1] > 13.0 and e[1] / e[2] > 14.5, e
+    assert e[2] < 1e-4
+
+
+def test_central_rhs_conserves_and_keeps_constants():
+    # periodic random data: the face values telescope, so sum(R) dx = 0 to
+    # round-off; a uniform state gives R = 0 exactly
+    rng = np.random.default_rng(3)
+    n, g = 16, 3
+    core = np.stack([1.0 + 0.3 * rng.uniform(size=n), 0.2 * rng.normal(size=n), 2.5 + rng.uniform(size=n)])
+    A = np.concatenate([core[:, -g:], core, core[:, :g]], axis=1)
+    R, faces = euler.patch_rhs(A.reshape(3, 1, 1, -1), 1, n, g, [1.0 / n], 1.4, flux='central')
+    assert np.all(np.abs(R.reshape(3, n).sum(axis=1)) <= 1e-12 * np.max(np.abs(R)))
+    assert np.allclose(faces[0][0], faces[0][1], rtol=0, atol=0)
+    B = np.stack(euler.conserved_from_primitive(np.full(n + 2 * g, 0.7), [np.full(n + 2 * g, -0.4)],
+                                                np.full(n + 2 * g, 1.3), 1.4))
+    R0, _ = euler.patch_rhs(B.reshape(3, 1, 1, -1), 1, n, g, [1.0 / n], 1.4, flux='central')
+    assert np.all(R0 == 0.0)
+
+
+def test_central_density_wave_fourth_order_in_space():
+    # the whole solver (ghosts, RK3, two patches) on the advected wave: with
+    # dt tied to dx^(4/3) the RK3 error falls like the spatial one
+    errs = []
+    for n in (16, 32):
+        w = workload('density_wave', base_cells=(n, 1, 1), patch=8, flux='central')
+        o = Oracle(w)
+        t_end = 0.25
+        k = int(math.ceil(t_end / (0.5 * (1.0 / n) ** (4.0 / 3.0))))
+        for _ in range(k):
+            o.step(dt=t_end / k)
+        rho = o.leaf_field(0)[0, 0]
+        x = (np.arange(n) + 0.5) / n
+        errs.append(np.max(np.abs(rho - (1.0 + 0.2 * np.sin(2.0 * math.pi * (x - o.t))))))
+    assert errs[0] / errs[1] > 12.0, errs
+
+
+def test_central_shear_layer_conserves_with_refinement():
+    # periodic shear layers on a refined hierarchy: the coarse-fine correction
+    # acts on the conservative face values, so every total is kept to round-off
+    w = workload('shear2d', base_cells=(64, 64, 1), patch=8, levels=2)
+    o = Oracle(w)
+    assert 0 < len(o.mesh.level_list(1)) < 4 * len(o.mesh.level_list(0))   # coarse-fine faces exist
+    s0 = o.cons_sums()
+    for _ in range(3):
+        o.step()
+        o.regrid()
+    s1 = o.cons_sums()
+    scale = np.array([s0[0], s0[0], s0[0], s0[3]])
+    assert np.all(np.abs(s1 - s0) <= 1e-13 * scale), (s1 - s0) / scale
+
+
+def test_shear_layer_initial_state():
+    # density ratio 2, uniform pressure, convective Mach number
+    # (u1 - u2) / (c1 + c2) = 0.7 between the band and the outer flow
+    w = workload('shear2d', base_cells=(64, 64, 1), patch=16, levels=1)
+    o = Oracle(w)
+    rho = o.leaf_field(0)[0]
+    mx = o.leaf_field(1)[0]
+    E = o.leaf_field(3)[0]
+    n = rho.shape[0]
+    mid, edge = n // 2, 0                        # y = 0 (band) and y = -0.3 (outer flow)
+    r1, r2 = rho[mid, 0], rho[edge, 0]
+    u1, u2 = mx[mid, 0] / r1, mx[edge, 0] / r2
+    assert r1 == pytest.approx(1.0, abs=1e-12) and r2 == pytest.approx(2.0, abs=1e-12)
+    c1, c2 = math.sqrt(1.4 / r1), math.sqrt(1.4 / r2)
+    assert (u1 - u2) / (c1 + c2) == pytest.approx(0.7, rel=1e-9)
+    rho_all = o.leaf_field(0)[0]
+    u_all = o.leaf_field(1)[0] / rho_all
+    v_all = o.leaf_field(2)[0] / rho_all
+    p_all = 0.4 * (E - 0.5 * rho_all * (u_all ** 2 + v_all ** 2))
+    assert np.allclose(p_all, 1.0, rtol=0, atol=1e-12)
+    # 5 periods of the transverse perturbation across the domain
+    v_layer = v_all[int(round((0.15 + 0.3) / 0.6 * n - 0.5))]
+    assert np.sum(np.diff(np.sign(v_layer)) != 0) in (9, 10, 11)
