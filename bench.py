@@ -34,14 +34,15 @@ FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 
 # DRAM bytes (read + write) of one k_rhs launch (SSP-RK3 stage 1, 1536 patches) from the ncu capture
 # summarised in profiles/k_rhs_blast3d_128_fp32.md, valid while the kernel sources hash as they did then
-RHS_TRAFFIC = {'bytes': 452924416 + 171362816, 'workload': 'blast3d', 'base': 128,
-               'sources': {'paper_2508_05020_gb300/csrc/amr_kernels.cuh': '8ab8fa153f452c5e',
-                           'paper_2508_05020_gb300/csrc/amr_launch.cuh': '632a0c161e212f9e'}}
+RHS_TRAFFIC = {'bytes': 452874752 + 170668544, 'workload': 'blast3d', 'base': 128, 'levels': 3,
+               'sources': {'paper_2508_05020_gb300/csrc/amr_kernels.cuh': '2cb20037fe3c2fc4',
+                           'paper_2508_05020_gb300/csrc/amr_launch.cuh': 'd8f8413b68574d01'}}
 
 
-def rhs_traffic(workload_name, base):
+def rhs_traffic(workload_name, base, levels):
     import hashlib
-    if workload_name != RHS_TRAFFIC['workload'] or base not in (0, RHS_TRAFFIC['base']):
+    if workload_name != RHS_TRAFFIC['workload'] or base not in (0, RHS_TRAFFIC['base']) or \
+            levels not in (0, RHS_TRAFFIC['levels']):
         return None
     for f, h in RHS_TRAFFIC['sources'].items():
         with open(os.path.join(ROOT, f), 'rb') as fh:
@@ -190,6 +191,7 @@ def main():
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--workload', default='blast3d')
     ap.add_argument('--base', type=int, default=0, help='override base cells per dimension')
+    ap.add_argument('--levels', type=int, default=0, help='override the number of levels')
     ap.add_argument('--precision', type=int, default=32)
     ap.add_argument('--flagger', default='mlp', choices=['plain', 'mlp'])
     ap.add_argument('--weights', default=None, help='float32 .npy weights of the learned indicator')
@@ -224,6 +226,8 @@ def main():
     w = workload(args.workload)
     if args.base:
         w['base_cells'] = tuple(args.base if d < w['dim'] else 1 for d in range(3))
+    if args.levels:
+        w['levels'] = args.levels
     weights = None
     if args.flagger == 'mlp':
         path = args.weights or os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights', 'indicator_d%d.npy' % w['dim'])
@@ -290,7 +294,7 @@ def main():
                   else 'WENO5 + Rusanov')
         roof = {'bound': 'alu', 'kernel': 'k_rhs (fused %s + SSP-RK3 stage)' % scheme,
                 'achieved': achieved, 'peak': fp32_peak, 'unit': 'TFLOP/s', 'frac': achieved / fp32_peak,
-                'traffic': rhs_traffic(args.workload, args.base), 'traffic_unit': 'bytes per launch (stage 1)',
+                'traffic': rhs_traffic(args.workload, args.base, args.levels), 'traffic_unit': 'bytes per launch (stage 1)',
                 'avg_launch_ms': avg_ms,
                 'peak_basis': 'FP32 ALU: 152 SMs x 128 lanes x 2 FLOP x %.0f MHz' % sm_max}
 
