@@ -34,20 +34,40 @@ FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 
 # DRAM bytes (read + write) of one k_rhs launch (SSP-RK3 stage 1, 1536 patches) from the ncu capture
 # summarised in profiles/k_rhs_blast3d_128_fp32.md, valid while the kernel sources hash as they did then
+# DRAM bytes of one stage-1 k_rhs launch (ncu, dram__bytes_read.sum +
+# dram__bytes_write.sum) on the default workload, valid while the sources
+# of the kernel (the regions below: EOS, WENO5, face fluxes, the kernel and
+# its launch) hash as recorded
 RHS_TRAFFIC = {'bytes': 452874752 + 170668544, 'workload': 'blast3d', 'base': 128, 'levels': 3,
-               'sources': {'paper_2508_05020_gb300/csrc/amr_kernels.cuh': '2cb20037fe3c2fc4',
-                           'paper_2508_05020_gb300/csrc/amr_launch.cuh': 'd8f8413b68574d01'}}
+               'regions': [('paper_2508_05020_gb300/csrc/amr_kernels.cuh', 'template <typename T> struct Num;',
+                            '// Metadata of one patch staged'),
+                           ('paper_2508_05020_gb300/csrc/amr_kernels.cuh', '// K4: fused right-hand side',
+                            '// K5: coarse-fine flux correction'),
+                           ('paper_2508_05020_gb300/csrc/amr_launch.cuh', 'template <typename T, int D, int N> struct RhsCfg',
+                            'template <typename T>\ncudaError_t Kernels<T>::prepare')],
+               'hash': 'e93b1e975a9d4da9'}
+
+
+def rhs_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f, a, b in RHS_TRAFFIC['regions']:
+        with open(os.path.join(ROOT, f)) as fh:
+            text = fh.read()
+        i = text.index(a)
+        h.update(text[i:text.index(b, i)].encode())
+    return h.hexdigest()[:16]
 
 
 def rhs_traffic(workload_name, base, levels):
-    import hashlib
     if workload_name != RHS_TRAFFIC['workload'] or base not in (0, RHS_TRAFFIC['base']) or \
             levels not in (0, RHS_TRAFFIC['levels']):
         return None
-    for f, h in RHS_TRAFFIC['sources'].items():
-        with open(os.path.join(ROOT, f), 'rb') as fh:
-            if hashlib.sha256(fh.read()).hexdigest()[:16] != h:
-                return None
+    try:
+        if rhs_source_hash() != RHS_TRAFFIC['hash']:
+            return None
+    except ValueError:
+        return None
     return RHS_TRAFFIC['bytes']
 
 

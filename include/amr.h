@@ -88,8 +88,9 @@ typedef struct {
  * the defaults (FP64, CFL 0.5, plain flags, thresholds 0.05, batched). */
 typedef struct {
     int precision;        /* 64 (FP64 storage and arithmetic) or 32 (FP32 storage, stencil
-                             arithmetic, CFL and flag tests; FP64 restriction and conservation
-                             sums and the CFL maximum) */
+                             arithmetic, CFL and flag tests; restriction sums carried error-free
+                             as FP32 pairs and rounded once; FP64 conservation sums and CFL
+                             maximum) */
     double cfl;           /* CFL number of the step (Sec. 3.1: c sets the step size) */
     double t_end;         /* > 0: the step is clipped so t never exceeds t_end */
     int flagger;          /* AMR_FLAG_PLAIN or AMR_FLAG_MLP */

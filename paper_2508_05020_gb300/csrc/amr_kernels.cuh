@@ -932,12 +932,12 @@ __global__ void __launch_bounds__(256) k_reflux(Grid g, T* Uout, const T* __rest
 // ---------------------------------------------------------------------------
 // K6: restriction of level `level` into its parents: the covered coarse cell
 // takes (sum of its 2^d children in lexicographic z, y, x order) * 2^-d,
-// summed in FP64
+// summed in FP64 (FP32 fields: an error-free FP32 pair sum, rounded once)
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int one_slot) {
     // thread <-> coarse cell; the 2^d children of every variable are read
-    // before anything is written (the sums are FP64 and bound by the FP64 pipe)
+    // before anything is written
     constexpr int NV = D + 2;
     constexpr int H = N / 2;
     constexpr int HC = D == 1 ? H : (D == 2 ? H * H : H * H * H);
@@ -971,11 +971,30 @@ __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int o
                   oz = D == 3 ? (g.coord[slot * 3 + 2] & 1) * H : 0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            double acc = (double)f[v][0];
+            T mean;
+            if constexpr (sizeof(T) == 4) {
+                // FP32 fields: the sum carried as an unevaluated pair s + e
+                // (Knuth's TwoSum adds each child without error into s and
+                // collects the rounding errors in e), rounded once; equal to
+                // the FP64 sum rounded to FP32 up to near-ties, at FP32 cost
+                float sum = f[v][0], err = 0.0f;
 #pragma unroll
-            for (int k = 1; k < NCH; ++k) acc = acc + (double)f[v][k];
-            U[slot_index(g, par, v, D == 3 ? oz + cz + G : 0, D >= 2 ? oy + cy + G : 0, ox + cx + G)] =
-                T(acc * scale);
+                for (int k = 1; k < NCH; ++k) {
+                    const float a = f[v][k];
+                    const float t = __fadd_rn(sum, a);
+                    const float bv = __fsub_rn(t, sum);
+                    const float e = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bv)), __fsub_rn(a, bv));
+                    sum = t;
+                    err = __fadd_rn(err, e);
+                }
+                mean = __fmul_rn(__fadd_rn(sum, err), (float)scale);
+            } else {
+                double acc = (double)f[v][0];
+#pragma unroll
+                for (int k = 1; k < NCH; ++k) acc = acc + (double)f[v][k];
+                mean = T(acc * scale);
+            }
+            U[slot_index(g, par, v, D == 3 ? oz + cz + G : 0, D >= 2 ? oy + cy + G : 0, ox + cx + G)] = mean;
         }
     }
 }
