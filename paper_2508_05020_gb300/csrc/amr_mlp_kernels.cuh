@@ -310,14 +310,21 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
         const T gm1 = T(g.gamma) - T(1);
         const int npatch = g.counts[1];
         // items are slab-major (slab = item / npatch): the slabs of a patch are
-        // far apart in the order, so a patch flagged by an earlier slab is
-        // seen as flagged when its later slabs come up and they are skipped
+        // far apart in the order, so a patch decided by an earlier slab is
+        // seen as decided when its later slabs come up and they are skipped.
+        // Decided: the refine bit below the finest level (it implies the keep
+        // bit), the keep bit on the finest level (which cannot refine)
+        auto decided = [&](int it) -> bool {
+            const int slot = g.leaf_list[it % npatch];
+            const int need = g.level[slot] == g.L - 1 ? 2 : 1;
+            return (*((volatile int*)&anyflag[slot]) & need) != 0;
+        };
         auto grab = [&]() -> int {
             for (;;) {
                 const int it = atomicAdd(counter, 1);
                 if (it >= total || *abort_f) return -1;
                 if constexpr (STATS) return it;
-                if (!(*((volatile int*)&anyflag[g.leaf_list[it % npatch]]) & 1)) return it;
+                if (!decided(it)) return it;
             }
         };
         int s = 0, nxt = -2;                               // nxt: the item prefetched (-2: none taken yet)
@@ -327,7 +334,7 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
             if (ptid == 0) {
                 int it = nxt == -2 ? grab() : nxt;
                 if constexpr (!STATS) {                    // flagged since it was taken: skip it
-                    if (it >= 0 && (*((volatile int*)&anyflag[g.leaf_list[it % npatch]]) & 1)) it = grab();
+                    if (it >= 0 && decided(it)) it = grab();
                 }
                 s_item[0] = it;
                 s_item[1] = it >= 0 ? grab() : -1;
