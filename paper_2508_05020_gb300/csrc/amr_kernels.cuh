@@ -614,7 +614,14 @@ template <int D, int N, int DZ, int EXT = 0> struct Chunk {
     static constexpr int F0 = (CX + 1 + EXT) * CY * CZ;
     static constexpr int F1 = D >= 2 ? CX * (CY + 1 + EXT) * CZ : 0;
     static constexpr int F2 = D == 3 ? CX * CY * (CZ + 1 + EXT) : 0;
-    static constexpr int FMAX = F0 > F1 ? (F0 > F2 ? F0 : F2) : (F1 > F2 ? F1 : F2);
+    // face buffer: the x and y faces of a chunk together, then the z faces
+    static constexpr int FMAX = F0 + F1 > F2 ? F0 + F1 : F2;
+    // face rows per dimension d (x extent FX_d, y extent FY_d) and their
+    // multiply-high reciprocals
+    static constexpr int FX0 = CX + 1 + EXT, FX1 = CX, FX2 = CX;
+    static constexpr int FY0 = CY, FY1 = CY + 1 + EXT, FY2 = CY;
+    static constexpr unsigned MX0 = 0xFFFFFFFFu / FX0 + 1u, MX1 = 0xFFFFFFFFu / FX1 + 1u, MX2 = MX1;
+    static constexpr unsigned MY0 = 0xFFFFFFFFu / FY0 + 1u, MY1 = 0xFFFFFFFFu / FY1 + 1u, MY2 = MY0;
     static constexpr int TRANS = D == 1 ? 1 : (D == 2 ? N : N * N);   // cells on a patch face
 };
 
@@ -710,21 +717,30 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
         }
         __syncthreads();
         T R[CPT][NV];
-        // one rolled loop over the dimensions: a single copy of the face-flux
-        // code keeps the kernel inside the instruction cache
+        // two phases: the x and y faces of the chunk in one pass (an even
+        // share of faces per thread), then the z faces; each phase ends with
+        // the divergence of its dimensions, x before y before z. One rolled
+        // loop: a single copy of the face-flux code keeps the kernel inside
+        // the instruction cache
+        constexpr int NPH = D == 3 ? 2 : 1;
 #pragma unroll 1
-        for (int d = 0; d < D; ++d) {
-            const int ex = d == 0, ey = d == 1, ez = d == 2;
-            const int FX = C::CX + ex * (1 + EXT), FY = C::CY + ey * (1 + EXT), FZ = C::CZ + ez * (1 + EXT);
-            const int nf = FX * FY * FZ;
-            // f -> (fi, fj, fk) by multiply-high division, exact for f * FX < 2^32
-            const unsigned mFX = 0xFFFFFFFFu / (unsigned)FX + 1u;
-            const unsigned mFY = D == 1 ? 0u : 0xFFFFFFFFu / (unsigned)FY + 1u;   // 1D: FY = FZ = 1
-            const int step = d == 0 ? 1 : C::QX;          // x and y pencils stay in one centre plane
-            // tangential velocity components in increasing dimension order
-            const int t1 = d == 0 ? 1 : 0;
-            const int t2 = d == 2 ? 1 : 2;
-            for (int f = threadIdx.x; f < nf; f += NTH) {
+        for (int ph = 0; ph < NPH; ++ph) {
+            const int dlo = ph == 0 ? 0 : 2, dhi = ph == 0 ? (D < 2 ? D : 2) : 3;
+            const int nfp = ph == 0 ? (D >= 2 ? C::F0 + C::F1 : C::F0) : C::F2;
+            for (int fp = threadIdx.x; fp < nfp; fp += NTH) {
+                const int d = ph == 1 ? 2 : (D >= 2 && fp >= C::F0 ? 1 : 0);
+                const int fbase = d == 1 ? C::F0 : 0;     // the dimension's faces in the buffer
+                const int f = fp - fbase;
+                const int ex = d == 0, ey = d == 1;
+                const int FX = d == 0 ? C::FX0 : (d == 1 ? C::FX1 : C::FX2);
+                const int FY = d == 0 ? C::FY0 : (d == 1 ? C::FY1 : C::FY2);
+                // f -> (fi, fj, fk) by multiply-high division, exact for f * FX < 2^32
+                const unsigned mFX = d == 0 ? C::MX0 : (d == 1 ? C::MX1 : C::MX2);
+                const unsigned mFY = D == 1 ? 0u : (d == 0 ? C::MY0 : (d == 1 ? C::MY1 : C::MY2));   // 1D: FY = FZ = 1
+                const int step = d == 0 ? 1 : C::QX;      // x and y pencils stay in one centre plane
+                // tangential velocity components in increasing dimension order
+                const int t1 = d == 0 ? 1 : 0;
+                const int t2 = d == 2 ? 1 : 2;
                 const int q1 = (int)__umulhi((unsigned)f, mFX);
                 const int fk = D == 1 ? 0 : (int)__umulhi((unsigned)q1, mFY);
                 const int fi = f - q1 * FX;
@@ -767,7 +783,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                     Fg[1 + e] = e == d ? Fp[1] : (e == t1 ? Fp[NT >= 1 ? 2 : 1] : Fp[NT >= 2 ? 3 : 1]);
                 Fg[NV - 1] = Fp[NT + 2];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) Fs[v * C::FMAX + f] = Fg[v];
+                for (int v = 0; v < NV; ++v) Fs[v * C::FMAX + fp] = Fg[v];
                 // patch-boundary faces needed by the coarse-fine flux correction
                 // (central: the conservative face values, saved by the divergence)
                 const int fd = d == 0 ? fi : (d == 1 ? fj : fk + z0);
@@ -783,6 +799,11 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 }
             }
             __syncthreads();
+#pragma unroll 1
+            for (int d = dlo; d < dhi; ++d) {
+            const int FX = d == 0 ? C::FX0 : (d == 1 ? C::FX1 : C::FX2);
+            const int FY = d == 0 ? C::FY0 : (d == 1 ? C::FY1 : C::FY2);
+            const T* Fd = Fs + (d == 1 ? C::F0 : 0);
             const T dxd = T(g.dx[lev][d]);
             const T idx = T(1) / dxd;                        // FP32: multiply by the reciprocal
             const int fstep = d == 0 ? 1 : (d == 1 ? FX : FX * FY);
@@ -810,7 +831,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                         }
 #pragma unroll
                         for (int v = 0; v < NV; ++v) {
-                            const T* Fv = Fs + v * C::FMAX;
+                            const T* Fv = Fd + v * C::FMAX;
                             const T flo_m = Fv[flo - fstep], flo_c = Fv[flo], fhi_c = Fv[fhi], fhi_p = Fv[fhi + fstep];
                             T glo = T(26) * flo_c - flo_m - fhi_c;
                             T ghi = T(26) * fhi_c - flo_c - fhi_p;
@@ -824,12 +845,13 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                     } else {
 #pragma unroll
                         for (int v = 0; v < NV; ++v) {
-                            const T df = Fs[v * C::FMAX + fhi] - Fs[v * C::FMAX + flo];
+                            const T df = Fd[v * C::FMAX + fhi] - Fd[v * C::FMAX + flo];
                             const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
                             R[n][v] = d == 0 ? -dv : R[n][v] - dv;
                         }
                     }
                 }
+            }
             }
             __syncthreads();
         }
