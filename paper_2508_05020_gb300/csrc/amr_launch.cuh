@@ -8,11 +8,13 @@ namespace amr {
 
 // chunk depth (3D) and block size of the fused RHS kernel per precision
 template <typename T, int D, int N> struct RhsCfg {
-    // 3D: two-plane chunks (61 KB of staging in FP32) so that three CTAs of
-    // at most 85 registers share an SM
-    static constexpr int DZ = D == 3 ? 2 : 1;
+    // 3D FP32 with 16^3 patches: four-plane chunks (110 KB of staging and face
+    // buffer), two CTAs of at most 128 registers per SM (fewer face-pass
+    // iterations per plane than two-plane chunks at three CTAs per SM);
+    // otherwise two-plane chunks
+    static constexpr int DZ = D == 3 ? (sizeof(T) == 4 && N == 16 ? 4 : 2) : 1;
     static constexpr int NTH = D == 1 ? 64 : 256;
-    static constexpr int MINB = (D == 3 && sizeof(T) == 4) ? 3 : 1;
+    static constexpr int MINB = (D == 3 && sizeof(T) == 4) ? (N == 16 ? 2 : 3) : 1;
 };
 
 #define AMR_DISPATCH(g, CALL)                                   \
