@@ -435,10 +435,12 @@ def compare_fp64_plain(AMR, w, args, fe, weights, value):
 def e2e_measure(AMR, w, args, fe, weights=None):
     """The same metric through the public API with host buffers: the initial
     hierarchy is uploaded from host memory (amr_set_state), every step calls
-    amr_step + amr_regrid + amr_get_diag (time and conservation sums read
-    back), and the final state is read back to host memory (amr_get_level)."""
+    amr_advance(1) (step + regrid) + amr_get_diag (time and conservation sums
+    read back), and the final state is read back to host memory
+    (amr_get_level). Same options and launch parameters as the timed run."""
     import numpy as np
-    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights, mlp_keep_margin=args.keep_margin)
+    amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights, mlp_keep_margin=args.keep_margin,
+              max_patches=args.max_patches, autotune=not args.no_autotune)
     lv, co, da = [], [], []
     for l in range(w['levels']):
         c, x = amr.get_level(l)
@@ -449,15 +451,13 @@ def e2e_measure(AMR, w, args, fe, weights=None):
     co = np.concatenate(co)
     da = np.concatenate(da)
     for _ in range(args.warmup):
-        amr.step(sync=False)
-        amr.regrid()
+        amr.advance(1)
         amr.diag()
     h0, d0, _ = amr.counters()
     t0 = time.perf_counter()
     amr.set_state(lv, co, da, t=0.0)
     for _ in range(args.steps):
-        amr.step(sync=False)
-        amr.regrid()
+        amr.advance(1)
         amr.diag()
     for l in range(w['levels']):
         amr.get_level(l)
@@ -467,7 +467,7 @@ def e2e_measure(AMR, w, args, fe, weights=None):
     return {'value': fe * args.steps / el, 'unit': UNIT,
             'h2d_bytes_per_step': int((h1 - h0) / args.steps), 'd2h_bytes_per_step': int((d1 - d0) / args.steps),
             'note': 'initial state uploaded and final state read back inside the timed region (amortised over '
-                    'the steps); per step amr_step + amr_regrid + amr_get_diag'}
+                    'the steps); per step amr_advance(1) (step + regrid) + amr_get_diag'}
 
 
 if __name__ == '__main__':

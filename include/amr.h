@@ -44,6 +44,7 @@ extern "C" {
 #define AMR_ERR_TIMEOUT   -5   /* a bounded device wait gave up */
 #define AMR_ERR_STATE     -6   /* call not allowed in the current state */
 #define AMR_ERR_MESH      -7   /* a patch set that breaks R1/R2 or the tree structure */
+#define AMR_ERR_IO        -8   /* a checkpoint file could not be written or read, or does not match */
 
 /* boundary kinds, per dimension and side */
 #define AMR_BC_OUTFLOW     0   /* ghost = nearest interior layer */
@@ -183,6 +184,21 @@ int amr_get_diag(amr_ctx* ctx, double* t, double cons_sums[5], int patches_per_l
  * complete sibling groups, and satisfy R2; otherwise AMR_ERR_MESH. */
 int amr_set_state(amr_ctx* ctx, int n, const int* levels, const int* coords,
                   const double* data, double t);
+
+/* Checkpoint and restart. amr_checkpoint writes the hierarchy to a file: the
+ * 8-byte tag "AMRCKPT1", then int32 dim, N, levels, dim+2, n (patches), the
+ * double time t, int32 levels[n], int32 coords[n x dim] and double
+ * interiors[n x (dim+2) x N^d] in canonical order (layout of amr_get_level),
+ * host byte order. The values are exact images of the state (FP32 fields
+ * widen exactly). amr_restore reads such a file into a context created with
+ * the same dimension, patch size and number of levels (either precision; an
+ * FP64 file restored into an FP32 context is rounded) and replaces its
+ * hierarchy, state and time as amr_set_state does, so a run continued from
+ * it repeats the original run's results. A file that cannot be opened, is
+ * short, or has another tag or shape gives AMR_ERR_IO and leaves the context
+ * unchanged. */
+int amr_checkpoint(amr_ctx* ctx, const char* path);
+int amr_restore(amr_ctx* ctx, const char* path);
 
 /* Refinement requests and coarsening candidates of the current state without
  * changing it: keys are (level, cx, cy, cz) quadruples in canonical order.

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, '_lib', 'libamr.so')
 
 OK = 0
 ERRORS = {-1: 'AMR_ERR_ARG', -2: 'AMR_ERR_POOL', -3: 'AMR_ERR_CUDA', -4: 'AMR_ERR_NONFINITE',
-          -5: 'AMR_ERR_TIMEOUT', -6: 'AMR_ERR_STATE', -7: 'AMR_ERR_MESH'}
+          -5: 'AMR_ERR_TIMEOUT', -6: 'AMR_ERR_STATE', -7: 'AMR_ERR_MESH', -8: 'AMR_ERR_IO'}
 BC = {'outflow': 0, 'reflect': 1, 'periodic': 2, 'dmr_inflow': 3, 'dmr_bottom': 4, 'dmr_top': 5}
 IC = {'sod': 0, 'shu_osher': 1, 'riemann2d': 2, 'dmr': 3, 'blast3d': 4, 'implosion': 5,
       'density_wave': 6, 'constant': 7, 'shear_layer': 8}
@@ -69,6 +69,8 @@ SIGNATURES = [
     ('amr_set_state', C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
     ('amr_get_requests', C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.POINTER(C.c_int),
                                    C.c_void_p]),
+    ('amr_checkpoint', C.c_int, [C.c_void_p, C.c_char_p]),
+    ('amr_restore', C.c_int, [C.c_void_p, C.c_char_p]),
     ('amr_set_mlp', C.c_int, [C.c_void_p, C.c_void_p, C.c_long]),
     ('amr_flag_stats', C.c_int, [C.c_void_p, C.c_void_p]),
     ('amr_harvest', C.c_int, [C.c_void_p, C.POINTER(C.c_long), C.c_void_p, C.c_void_p]),
@@ -263,6 +265,14 @@ class AMR:
         c = np.zeros((nc.value, 4), dtype=np.int32)
         self._check(self.lib.amr_get_requests(self.ctx, C.byref(nr), _ptr(r), C.byref(nc), _ptr(c)))
         return r, c
+
+    def checkpoint(self, path):
+        """Write the hierarchy, state and time to a file (amr_checkpoint)."""
+        self._check(self.lib.amr_checkpoint(self.ctx, os.fsencode(path)))
+
+    def restore(self, path):
+        """Replace the hierarchy, state and time by a checkpoint's (amr_restore)."""
+        self._check(self.lib.amr_restore(self.ctx, os.fsencode(path)))
 
     def set_mlp(self, weights):
         wv = np.ascontiguousarray(weights, dtype=np.float32)

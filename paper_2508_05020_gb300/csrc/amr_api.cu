@@ -1212,6 +1212,69 @@ int amr_set_state(amr_ctx* c, int n, const int* levels, const int* coords, const
                               : set_state_impl<float>(c, n, levels, coords, data, t);
 }
 
+static const char CKPT_TAG[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '1'};
+
+int amr_checkpoint(amr_ctx* c, const char* path) {
+    GUARD(c);
+    if (!path) return fail(c, AMR_ERR_ARG, "no path");
+    const long long per = (long long)c->nv * (c->dim == 1 ? c->N : (c->dim == 2 ? c->N * c->N : c->N * c->N * c->N));
+    std::vector<int> lv, co;
+    std::vector<double> da;
+    for (int l = 0; l < c->L; ++l) {
+        int n = 0;
+        int r = amr_get_level(c, l, &n, nullptr, nullptr);
+        if (r) return r;
+        const size_t o = lv.size();
+        lv.resize(o + n, l);
+        co.resize((o + n) * c->dim);
+        da.resize((o + n) * per);
+        r = amr_get_level(c, l, &n, co.data() + o * c->dim, da.data() + o * per);
+        if (r) return r;
+    }
+    double t = 0.0;
+    int r = amr_get_diag(c, &t, nullptr, nullptr);
+    if (r) return r;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(c, AMR_ERR_IO, "cannot open the checkpoint file for writing");
+    const int hdr[5] = {c->dim, c->N, c->L, c->nv, (int)lv.size()};
+    bool ok = std::fwrite(CKPT_TAG, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 5, f) == 5 &&
+              std::fwrite(&t, sizeof(double), 1, f) == 1 &&
+              std::fwrite(lv.data(), sizeof(int), lv.size(), f) == lv.size() &&
+              std::fwrite(co.data(), sizeof(int), co.size(), f) == co.size() &&
+              std::fwrite(da.data(), sizeof(double), da.size(), f) == da.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(c, AMR_ERR_IO, "checkpoint write failed");
+    return AMR_OK;
+}
+
+int amr_restore(amr_ctx* c, const char* path) {
+    GUARD(c);
+    if (!path) return fail(c, AMR_ERR_ARG, "no path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(c, AMR_ERR_IO, "cannot open the checkpoint file");
+    char tag[8];
+    int hdr[5];
+    double t = 0.0;
+    bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, CKPT_TAG, 8) == 0 &&
+              std::fread(hdr, sizeof(int), 5, f) == 5 && std::fread(&t, sizeof(double), 1, f) == 1;
+    ok = ok && hdr[0] == c->dim && hdr[1] == c->N && hdr[2] == c->L && hdr[3] == c->nv && hdr[4] > 0 &&
+         hdr[4] <= c->cap;
+    const long long per = (long long)c->nv * (c->dim == 1 ? c->N : (c->dim == 2 ? c->N * c->N : c->N * c->N * c->N));
+    std::vector<int> lv, co;
+    std::vector<double> da;
+    if (ok) {
+        const size_t n = (size_t)hdr[4];
+        lv.resize(n);
+        co.resize(n * c->dim);
+        da.resize(n * per);
+        ok = std::fread(lv.data(), sizeof(int), n, f) == n && std::fread(co.data(), sizeof(int), co.size(), f) == co.size() &&
+             std::fread(da.data(), sizeof(double), da.size(), f) == da.size();
+    }
+    std::fclose(f);
+    if (!ok) return fail(c, AMR_ERR_IO, "checkpoint file is short or does not match this context");
+    return amr_set_state(c, (int)lv.size(), lv.data(), co.data(), da.data(), t);
+}
+
 int amr_get_requests(amr_ctx* c, int* n_refine, int* refine_keys, int* n_coarsen, int* coarsen_keys) {
     GUARD(c);
     if (!n_refine || !n_coarsen) return fail(c, AMR_ERR_ARG, "count pointers required");
