@@ -191,7 +191,7 @@ def rhs_flops_per_launch(amr, w, flops):
     d = w['dim']
     N = w['patch']
     _, _, ppl = amr.diag()
-    n_patch = int(sum(ppl))
+    n_patch = leaf_patches(w, ppl)                 # the kernel updates leaves only
     rows = n_patch * d * N ** (d - 1)
     cells = n_patch * N ** d
     f = flops[str(d)]
@@ -361,13 +361,21 @@ def main():
     return 0
 
 
+def leaf_patches(w, ppl):
+    """Leaves of a hierarchy with ppl patches per level: every patch above
+    the base level has 2^d - 1 siblings and one parent, which is not a leaf."""
+    ppl = [int(x) for x in ppl[:w['levels']]]
+    return sum(ppl) - sum(ppl[1:]) // (2 ** w['dim'])
+
+
 def cell_counts(w, ppl):
-    """Cells one step updates: every patch of every level (and, of those, the leaves
-    need the learned or plain flags), against the fine-equivalent count."""
+    """Cells one step updates: the leaf patches (a patch with children is
+    restricted from them, not updated), all patches (whose ghosts are
+    filled), and the fine-equivalent count."""
     n = w['patch'] ** w['dim']
-    total = int(sum(ppl)) * n
-    return {'all_patches': total, 'fine_equivalent': int(fine_equivalent_cells(w)),
-            'stage_updates_per_step': 3 * total}
+    leaves = leaf_patches(w, ppl) * n
+    return {'leaf_cells': leaves, 'all_patch_cells': int(sum(ppl)) * n,
+            'fine_equivalent': int(fine_equivalent_cells(w)), 'stage_updates_per_step': 3 * leaves}
 
 
 def level0_rho(amr):

@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
 }
 
 // ---------------------------------------------------------------------------
-// K4: fused right-hand side and SSP-RK3 stage of a chunk of one patch.
+// K4: fused right-hand side and SSP-RK3 stage of a chunk of one leaf patch.
 // The chunk (DZ planes in 3D, the whole patch in 1D/2D) plus its ghost halo
 // is staged in shared memory as primitives (p, u_0.., T); face fluxes of one
 // dimension at a time go to a shared buffer; each thread accumulates the
@@ -651,12 +651,14 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
     const T dt = T(dtd);
     const T ra = stage == 0 ? T(0) : (stage == 1 ? T(0.75) : T(1.0 / 3.0));
     const T rb = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2.0 / 3.0));
-    const int npatch = one_slot >= 0 ? 1 : g.counts[0];
+    // leaves only: a patch with children is covered by them, and the
+    // restriction after the stage overwrites its whole interior
+    const int npatch = one_slot >= 0 ? 1 : g.counts[1];
     const int n_items = npatch * C::NCH;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int pi = item / C::NCH;
         const int z0 = (item - pi * C::NCH) * DZ;        // first interior plane of the chunk (3D)
-        const int slot = one_slot >= 0 ? one_slot : g.all_list[pi];
+        const int slot = one_slot >= 0 ? one_slot : g.leaf_list[pi];
         const int lev = g.level[slot];
         const int pf = g.pflag[slot];
         // 1. stage the chunk and its halo as primitives, loading 16-byte vectors
