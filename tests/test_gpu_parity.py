@@ -93,6 +93,9 @@ def run_both(w, steps, regrid=True, **kw):
     ('sod', dict(flux='central'), 8, 0.0),
     ('shear2d', dict(base_cells=(32, 32, 1), patch=8, levels=3), 4, TOL64),
     ('shear2d', dict(base_cells=(64, 64, 1), patch=16, levels=3), 2, TOL64),
+    # 32-cell patches in 2D, a single level in 3D
+    ('riemann2d', dict(base_cells=(128, 128, 1), patch=32, levels=2), 3, 0.0),
+    ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=1), 2, 0.0),
 ])
 def test_fp64_matches_oracle(name, kw, steps, tol):
     w = workload(name, **kw)
@@ -144,6 +147,8 @@ def l1_rho_rel(gpu, ref):
     ('riemann2d', dict(base_cells=(32, 32, 1), patch=8), 6),
     ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2), 2),
     ('riemann2d', dict(base_cells=(32, 32, 1), patch=8, flux='hllc'), 6),
+    ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2, flux='hllc'), 2),
+    ('blast3d', dict(base_cells=(32, 32, 32), patch=16, levels=2), 1),
 ])
 def test_fp32_l1_against_oracle(name, kw, steps):
     # same mesh sequence: both sides regrid from their own flags; a flag near
@@ -335,6 +340,22 @@ def test_fp32_central_l1_rho(name, kw, steps):
         g.step(dt)
         r.regrid()
         g.regrid()
+    err = l1_rho_rel(g, r)
+    assert err <= 1e-5, err
+    g.close()
+
+
+def test_fp32_central_3d_given_identical_state():
+    # the FP32 central instantiation in 3D (four-plane chunks at N = 16) on
+    # the smooth field of the refined 3D hierarchy
+    w, r = smooth3d_hierarchy(16, 2, 'central')
+    g = amr(w, precision=32)
+    keys = r.mesh.canonical()
+    g.set_state(np.array([k[0] for k in keys]), np.array([list(k[1]) for k in keys]),
+                np.stack([r.U[k][r.inner()] for k in keys]), t=0.0)
+    for _ in range(2):
+        dt = r.step()
+        g.step(dt)
     err = l1_rho_rel(g, r)
     assert err <= 1e-5, err
     g.close()
