@@ -238,3 +238,33 @@ def test_fused_cell_counts_match_oracle(name, base, patch):
     assert got[0] + got[2] == ref[0] + ref[2] and got[1] + got[3] == ref[1] + ref[3], (got, ref)
     # learned decisions may differ only where the logit is within the rounding margin
     assert np.all(np.abs(got - ref) <= near), (got, ref, near)
+
+
+def test_adam_steps_match_oracle():
+    # full-batch training for two epochs = two Adam steps; against the
+    # oracle's Adam on the oracle's FP64 gradients from the same start
+    from oracle import mlp
+    from paper_2508_05020_gb300 import amr
+    s = samples(6, 128)
+    dim = 1
+    X = amr.mlp_features(dim, 1.4, s)
+    y = np.repeat(mlp.plain_flag_1d(s, 0.05, 0.05), 2 * dim).astype(np.float32)
+    pw = mlp.bce_pos_weight(y)
+    w0 = flat(mlp_init(0, mlp.k_in(dim)))
+    n, lr = X.shape[0], 1e-3
+    p = mlp.unflatten(w0.astype(np.float64), mlp.k_in(dim))
+    st = {}
+    ref = []
+    for _ in range(2):
+        _, g = mlp.loss_and_grad(p, X.astype(np.float64), y.astype(np.float64), pw)
+        if not ref:
+            g1 = mlp.flatten(g)
+        mlp.adam(p, g, st, lr)
+        ref.append(mlp.flatten(p))
+    w1, _ = amr.mlp_train(dim, X, y, pw, w0, epochs=1, batch=n, lr=lr, seed=1)
+    step = w1.astype(np.float64) - w0.astype(np.float64)
+    big = np.abs(g1) > 1e-3 * np.max(np.abs(g1))          # away from a sign change of the gradient
+    assert np.all(np.abs(step) <= lr * (1.0 + 1e-3) + 1e-7)
+    assert np.allclose(step[big], (ref[0] - w0)[big], rtol=0, atol=1e-3 * lr + 1e-7)
+    w2, _ = amr.mlp_train(dim, X, y, pw, w0, epochs=2, batch=n, lr=lr, seed=1)
+    assert np.allclose((w2 - w0)[big], (ref[1] - w0)[big], rtol=0, atol=0.1 * lr + 1e-7)

@@ -115,3 +115,42 @@ def test_keep_margin_hysteresis():
     assert out[2.0][1] <= out[0.5][1] <= out[0.0][1]
     assert out[2.0][1] < out[None][1]
     assert not out[1e9][1]
+
+
+def test_adam_steps_from_the_definition():
+    # with a constant gradient the bias-corrected moments are g and g^2 at
+    # every step, so each update is -lr g / (|g| + eps); a zero gradient
+    # leaves the parameter where it is
+    rng = np.random.default_rng(4)
+    p = mlp_init(0, mlp.k_in(1))
+    g = {k: rng.normal(size=np.shape(v)) for k, v in p.items()}
+    g['b3'][:] = 0.0
+    st = {}
+    lr = 1e-3
+    for _ in range(3):
+        before = {k: np.array(v, copy=True) for k, v in p.items()}
+        mlp.adam(p, g, st, lr)
+        for k in p:
+            step = p[k] - before[k]
+            assert np.allclose(step, -lr * g[k] / (np.abs(g[k]) + 1e-8), rtol=1e-9, atol=1e-15), k
+    assert st['t'] == 3
+
+
+def test_weighted_bce_closed_form():
+    # all weights zero and output bias z: every logit is z, the loss is
+    # mean(pw y log(1 + e^-z) + (1 - y) log(1 + e^z)), its b3 gradient is
+    # mean(pw y (sigma(z) - 1) + (1 - y) sigma(z)), the other gradients vanish
+    p = {k: np.zeros_like(v) for k, v in mlp_init(0, mlp.k_in(2)).items()}
+    y = np.array([1.0, 0.0, 0.0, 0.0, 1.0, 0.0])
+    pw = mlp.bce_pos_weight(y)
+    assert pw == 2.0                                       # 4 negatives / 2 positives
+    X = np.random.default_rng(5).normal(size=(6, mlp.k_in(2)))
+    for z in (-3.0, 0.0, 0.7, 12.0):
+        p['b3'][:] = z
+        loss, g = mlp.loss_and_grad(p, X, y, pw)
+        s = 1.0 / (1.0 + np.exp(-z))
+        ref = np.mean(pw * y * np.log1p(np.exp(-z)) + (1.0 - y) * np.log1p(np.exp(z)))
+        assert loss == pytest.approx(ref, rel=1e-12)
+        assert g['b3'][0] == pytest.approx(np.mean(pw * y * (s - 1.0) + (1.0 - y) * s), rel=1e-12, abs=1e-15)
+        for k in ('W1', 'b1', 'W2', 'b2', 'W3'):
+            assert not np.any(g[k]), k
