@@ -67,7 +67,7 @@ struct amr_ctx {
     float* mlp_w = nullptr;
     long mlp_n = 0;
     int* ghost_tab = nullptr;
-    int n_ghost = 0;
+    int n_ghost = 0, n_ghost_face = 0;
     Grid grid{};
     // graph
     // captured step graphs by [CFL step][stage-1 ghost fill skipped]
@@ -355,7 +355,7 @@ int enqueue_step(amr_ctx* c, bool with_cfl, bool skip_fill0, long long* nk) {
         CK(mark(c->ev[s][0]), "event");
         for (int l = 0; l < c->L && !(s == 0 && skip_fill0); ++l) {
             CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], grid_size(c, c->tune[AMR_TUNE_GHOST_GRID]), c->stream, -1,
-                                      c->tune[AMR_TUNE_GHOST_CHUNK]),
+                                      c->tune[AMR_TUNE_GHOST_CHUNK], true),
                "ghost fill");
             ++k;
         }
@@ -401,7 +401,8 @@ int per_patch_step(amr_ctx* c, bool with_cfl) {
         T* dst = St<T>(c, s == 0 ? 1 : (s == 1 ? 2 : 0));
         for (int l = 0; l < c->L; ++l)
             for (int i = c->level_off_h[l]; i < c->level_off_h[l + 1]; ++i) {
-                CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], 8, c->stream, c->canon_slot[i]), "ghost fill");
+                CK(Kernels<T>::ghost_fill(g, src, l, tfrac[s], 8, c->stream, c->canon_slot[i], 512, true),
+                   "ghost fill");
                 ++c->kernels;
             }
         for (size_t i = 0; i < c->canon_slot.size(); ++i) {
@@ -829,7 +830,8 @@ int autotune_impl(amr_ctx* c) {
                 float t = 0.f;
                 err = timed([&]() {
                     for (int l = 0; l < c->L; ++l) {
-                        const cudaError_t e = Kernels<T>::ghost_fill(g, A, l, 0.0, grid_size(c, gr), c->stream, -1, ch);
+                        const cudaError_t e = Kernels<T>::ghost_fill(g, A, l, 0.0, grid_size(c, gr), c->stream, -1, ch,
+                                                                     true);
                         ++nk;
                         if (e != cudaSuccess) return e;
                     }
@@ -1064,16 +1066,25 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     std::memset(c->time_h, 0, sizeof(DevTime));
     CK(cudaMemcpyAsync(c->time_d, c->time_h, sizeof(DevTime), cudaMemcpyHostToDevice, c->stream), "time");
 
-    // ghost-cell table of a slot: packed slot coordinates (x | y << 10 | z << 20)
-    std::vector<int> gt;
+    // ghost-cell table of a slot: packed slot coordinates (x | y << 10 | z << 20),
+    // face ghosts (outside the interior along one dimension) first, then edge
+    // and corner ghosts, each in slot order. The stage reads face ghosts only
+    // (pencils along one dimension, prolongation slopes along one dimension);
+    // the flag stencils read all of them
+    std::vector<int> gt, gt_ec;
     for (int z = 0; z < g.SZ; ++z)
         for (int y = 0; y < g.SY; ++y)
             for (int x = 0; x < S; ++x) {
                 const bool gx = x < G || x >= G + patch_size;
                 const bool gy = dim >= 2 && (y < G || y >= G + patch_size);
                 const bool gz = dim == 3 && (z < G || z >= G + patch_size);
-                if (gx || gy || gz) gt.push_back(x | ((dim >= 2 ? y : G) << 10) | ((dim == 3 ? z : G) << 20));
+                const int nout = (int)gx + (int)gy + (int)gz;
+                const int pk = x | ((dim >= 2 ? y : G) << 10) | ((dim == 3 ? z : G) << 20);
+                if (nout == 1) gt.push_back(pk);
+                else if (nout > 1) gt_ec.push_back(pk);
             }
+    c->n_ghost_face = (int)gt.size();
+    gt.insert(gt.end(), gt_ec.begin(), gt_ec.end());
     c->n_ghost = (int)gt.size();
     c->ghost_tab = (int*)dalloc(c, gt.size() * sizeof(int));
     if (!c->ghost_tab) return fail(c, AMR_ERR_CUDA, "device allocation failed");
@@ -1095,6 +1106,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.new_list = c->meta_d + ml.new_list;
     g.ghost_tab = c->ghost_tab;
     g.n_ghost = c->n_ghost;
+    g.n_ghost_face = c->n_ghost_face;
     g.time = c->time_d;
     {
         cudaError_t e = c->precision == 64 ? Kernels<double>::prepare(g) : Kernels<float>::prepare(g);

@@ -72,7 +72,8 @@ struct Grid {
     const int* reflux_fine;     // [n_reflux * 6 * 4]: fine slots across each face (-1 if none)
     const int* new_list;        // slots created by the last regrid
     const int* ghost_tab;       // packed local (x,y,z)+3 of every ghost cell of a slot
-    int n_ghost;
+    int n_ghost;                // ghost cells of a slot; the first n_ghost_face lie outside the
+    int n_ghost_face;           //   interior along one dimension only (face ghosts)
     DevTime* time;
 };
 
@@ -85,8 +86,9 @@ struct Kernels {
     static cudaError_t prepare_mlp(const Grid& g);
     // ghost cells of every patch of `level` (same-level copy, prolongation,
     // physical boundaries) at time t + tfrac * dt
+    // faces_only: face ghosts only (all a stage reads), else every ghost cell
     static cudaError_t ghost_fill(const Grid& g, T* U, int level, double tfrac, int grid,
-                                  cudaStream_t s, int one_slot, int chunk = 512);
+                                  cudaStream_t s, int one_slot, int chunk = 512, bool faces_only = false);
     // RHS + SSP-RK3 stage of every patch (or one patch if one_slot >= 0)
     static cudaError_t rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces,
                                  int stage, int grid, cudaStream_t s, int one_slot);

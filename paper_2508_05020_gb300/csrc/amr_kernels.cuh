@@ -549,15 +549,16 @@ __device__ void ghost_value(const Grid& g, const T* U, const PatchMeta& m, int* 
 }
 
 // ---------------------------------------------------------------------------
-// K1-K3: ghost fill of every patch of one level. A work item is a patch and a
-// run of `chunk` of its ghost cells (slot order; the size is a launch
-// parameter chosen by the autotuner), taken by one warp, which stages the
-// patch's metadata in its own shared-memory copy; warps never wait for one
-// another.
+// K1-K3: ghost fill of every patch of one level: the first n_cells entries of
+// the slot's ghost table (face ghosts first, then edge and corner ghosts; a
+// stage fills the face ghosts only, the regrid all of them). A work item is a
+// patch and a run of `chunk` of those cells (the size is a launch parameter
+// chosen by the autotuner), taken by one warp, which stages the patch's
+// metadata in its own shared-memory copy; warps never wait for one another.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
-                                               double4 pre, double4 post, int chunk) {
+                                               double4 pre, double4 post, int chunk, int n_cells) {
     constexpr int NV = D + 2;
     __shared__ PatchMeta metas[256 / 32];
     if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
@@ -568,12 +569,12 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
     const double t = g.time->t + tfrac * g.time->dt;
     const double pr[4] = {pre.x, pre.y, pre.z, pre.w};
     const double po[4] = {post.x, post.y, post.z, post.w};
-    const int nchunk = (g.n_ghost + chunk - 1) / chunk;   // chunk: ghost cells per work item
+    const int nchunk = (n_cells + chunk - 1) / chunk;     // chunk: ghost cells per work item
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int item = blockIdx.x * (blockDim.x >> 5) + warp; item < npatch * nchunk; item += nw) {
         const int pi = item / nchunk;
         const int g0 = (item - pi * nchunk) * chunk;
-        const int g1 = min(g0 + chunk, g.n_ghost);
+        const int g1 = min(g0 + chunk, n_cells);
         const int slot = one_slot >= 0 ? one_slot : g.all_list[lo + pi];
         load_meta_warp(g, slot, m);
         for (int gi = g0 + lane; gi < g1; gi += 32) {
