@@ -6,6 +6,7 @@
 // FP64 path reproduces an IEEE evaluation of the same formulas on the host.
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <cstdint>
 #include "amr_internal.h"
 #include "amr.h"
@@ -97,16 +98,6 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     const T e0 = T(1.0e-6) + b0;
     const T e1 = T(1.0e-6) + b1;
     const T e2 = T(1.0e-6) + b2;
-    if constexpr (sizeof(T) == 4) {
-        // FP32: the normalised weights are unchanged when every alpha_k is
-        // multiplied by e0^2 e1^2 e2^2, which leaves a single division; used
-        // while the products stay far inside the FP32 range
-        const T s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
-        if (fmaxf(s0, fmaxf(s1, s2)) < T(1.0e12)) {
-            const T m0 = T(0.0625) * (s1 * s2), m1 = T(0.625) * (s0 * s2), m2 = T(0.3125) * (s0 * s1);
-            return Num<T>::div(m0 * q0 + m1 * q1 + m2 * q2, m0 + m1 + m2);
-        }
-    }
     const T a0 = Num<T>::div(T(0.0625), e0 * e0);
     const T a1 = Num<T>::div(T(0.625), e1 * e1);
     const T a2 = Num<T>::div(T(0.3125), e2 * e2);
@@ -116,23 +107,29 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
 // FP32: left- (nodes 0..4) and right-biased (nodes 5..1) WENO5-JS values of one
 // face together; the right stencil is the left one mirrored, so two candidate
 // values and two smoothness terms are shared between them. Same formulas as
-// weno5, evaluated with the single-division weights.
+// weno5. FAST: the normalised weights are unchanged when every alpha_k is
+// multiplied by e0^2 e1^2 e2^2, which leaves a single division, valid while
+// the products stay far inside the FP32 range (ok is cleared otherwise, and
+// the caller evaluates the face again without FAST); else three divisions.
+template <bool FAST>
 __device__ __forceinline__ void weno5_pair(float v0, float v1, float v2, float v3, float v4, float v5, float& left,
-                                           float& right) {
+                                           float& right, bool& ok) {
     const float c1312 = 13.0f / 12.0f;
     const float qA = (-v1 + 6.0f * v2 + 3.0f * v3) * 0.125f;   // left q1 = right q2
     const float qB = (3.0f * v2 + 6.0f * v3 - v4) * 0.125f;    // left q2 = right q1
     const float tA = v1 - 2.0f * v2 + v3, tB = v2 - 2.0f * v3 + v4;
     const float cA = c1312 * (tA * tA), cB = c1312 * (tB * tB);
-    auto combine = [](float q0, float q1, float q2, float b0, float b1, float b2) {
+    auto combine = [&ok](float q0, float q1, float q2, float b0, float b1, float b2) {
         const float e0 = 1.0e-6f + b0, e1 = 1.0e-6f + b1, e2 = 1.0e-6f + b2;
         const float s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
-        if (fmaxf(s0, fmaxf(s1, s2)) < 1.0e12f) {
+        if constexpr (FAST) {
+            ok = ok && fmaxf(s0, fmaxf(s1, s2)) < 1.0e12f;
             const float m0 = 0.0625f * (s1 * s2), m1 = 0.625f * (s0 * s2), m2 = 0.3125f * (s0 * s1);
             return __fdividef(m0 * q0 + m1 * q1 + m2 * q2, m0 + m1 + m2);
+        } else {
+            const float a0 = __fdividef(0.0625f, s0), a1 = __fdividef(0.625f, s1), a2 = __fdividef(0.3125f, s2);
+            return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
         }
-        const float a0 = __fdividef(0.0625f, s0), a1 = __fdividef(0.625f, s1), a2 = __fdividef(0.3125f, s2);
-        return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
     };
     {   // left: a = v0, b = v1, c = v2, d = v3, e = v4
         const float q0 = (3.0f * v0 - 10.0f * v1 + 15.0f * v2) * 0.125f;
@@ -150,10 +147,11 @@ __device__ __forceinline__ void weno5_pair(float v0, float v1, float v2, float v
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void weno5_lr(const T (&w)[6], T& left, T& right) {
+// left and right values of one characteristic field; FP32 see weno5_pair
+template <typename T, bool FAST>
+__device__ __forceinline__ void weno5_lr(const T (&w)[6], T& left, T& right, bool& ok) {
     if constexpr (sizeof(T) == 4) {
-        weno5_pair(w[0], w[1], w[2], w[3], w[4], w[5], left, right);
+        weno5_pair<FAST>(w[0], w[1], w[2], w[3], w[4], w[5], left, right, ok);
     } else {
         left = weno5(w[0], w[1], w[2], w[3], w[4]);
         right = weno5(w[5], w[4], w[3], w[2], w[1]);
@@ -184,19 +182,27 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
     const T z = rbar * cbar;
     const T kap = Num<T>::div(gm1, gamma * rbar);
     T wl[NF], wr[NF];
-    {
+    // FP32: every field with the single-division weights, and the whole face
+    // again with three divisions in the rare case one of them was out of range
+    auto interpolate = [&](auto fast) {
+        constexpr bool FAST = decltype(fast)::value;
+        bool ok = true;
         T w[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) w[k] = p[k] - z * un[k];
-        weno5_lr(w, wl[0], wr[0]);
+        weno5_lr<T, FAST>(w, wl[0], wr[0], ok);
 #pragma unroll
         for (int k = 0; k < 6; ++k) w[k] = Tt[k] - kap * p[k];
-        weno5_lr(w, wl[1], wr[1]);
+        weno5_lr<T, FAST>(w, wl[1], wr[1], ok);
 #pragma unroll
-        for (int j = 0; j < NT; ++j) weno5_lr(ut[j], wl[2 + j], wr[2 + j]);
+        for (int j = 0; j < NT; ++j) weno5_lr<T, FAST>(ut[j], wl[2 + j], wr[2 + j], ok);
 #pragma unroll
         for (int k = 0; k < 6; ++k) w[k] = p[k] + z * un[k];
-        weno5_lr(w, wl[NF - 1], wr[NF - 1]);
+        weno5_lr<T, FAST>(w, wl[NF - 1], wr[NF - 1], ok);
+        return ok;
+    };
+    if (!interpolate(std::true_type{})) {
+        if constexpr (sizeof(T) == 4) interpolate(std::false_type{});
     }
     const T z2 = T(2) * z;
     T pL = T(0.5) * (wl[0] + wl[NF - 1]);
