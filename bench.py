@@ -447,17 +447,26 @@ def e2e_measure(AMR, w, args, fe, weights=None):
     read back), and the final state is read back to host memory
     (amr_get_level). Same options and launch parameters as the timed run."""
     import numpy as np
+    import torch
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype={np.dtype(np.float64): torch.float64, np.dtype(np.int32): torch.int32}[a.dtype],
+                        pin_memory=True).numpy()
+        t[...] = a
+        return t
+
     amr = AMR(w, precision=args.precision, flagger=args.flagger, mlp_weights=weights, mlp_keep_margin=args.keep_margin,
               max_patches=args.max_patches, autotune=not args.no_autotune)
     lv, co, da = [], [], []
     for l in range(w['levels']):
         c, x = amr.get_level(l)
         lv.append(np.full(len(c), l, dtype=np.int32))
-        co.append(c)
+        co.append(c.astype(np.int32))
         da.append(x)
-    lv = np.concatenate(lv)
-    co = np.concatenate(co)
-    da = np.concatenate(da)
+    lv = pinned(np.concatenate(lv))                 # the inputs and outputs in pinned host memory
+    co = pinned(np.concatenate(co))
+    da = pinned(np.concatenate(da))
+    res = torch.empty(2 * da.size, dtype=torch.float64, pin_memory=True).numpy()   # room for the final state
     for _ in range(args.warmup):
         amr.advance(1)
         amr.diag()
@@ -467,8 +476,13 @@ def e2e_measure(AMR, w, args, fe, weights=None):
     for _ in range(args.steps):
         amr.advance(1)
         amr.diag()
+    off = 0
     for l in range(w['levels']):
-        amr.get_level(l)
+        c, _ = amr.get_level(l, data=False)
+        shape = (len(c), w['dim'] + 2) + (w['patch'],) * w['dim']
+        n = int(np.prod(shape))
+        amr.get_level(l, out=res[off:off + n].reshape(shape) if off + n <= res.size else None)
+        off += n
     el = time.perf_counter() - t0
     h1, d1, _ = amr.counters()
     amr.close()

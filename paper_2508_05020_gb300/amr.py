@@ -235,11 +235,20 @@ class AMR:
         """n_steps CFL steps, each followed by a regrid (amr_advance)."""
         self._check(self.lib.amr_advance(self.ctx, int(n_steps), 1 if regrid else 0))
 
-    def get_level(self, level, data=True):
+    def get_level(self, level, data=True, out=None):
+        """Patch coordinates and interiors of a level (amr_get_level). `out`: a
+        C-contiguous float64 array of the right shape to receive the
+        interiors (for instance in pinned host memory)."""
         n = C.c_int()
         self._check(self.lib.amr_get_level(self.ctx, level, C.byref(n), None, None))
         coords = np.zeros((n.value, self.dim), dtype=np.int32)
-        arr = np.zeros((n.value, self.nv) + (self.N,) * self.dim) if data else None
+        shape = (n.value, self.nv) + (self.N,) * self.dim
+        if out is not None:
+            if out.shape != shape or out.dtype != np.float64 or not out.flags['C_CONTIGUOUS']:
+                raise ValueError('out must be a C-contiguous float64 array of shape %s' % (shape,))
+            arr = out
+        else:
+            arr = np.zeros(shape) if data else None
         if n.value:
             self._check(self.lib.amr_get_level(self.ctx, level, C.byref(n), _ptr(coords), _ptr(arr)))
         return coords.astype(np.int64), arr
