@@ -38,14 +38,14 @@ FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 # dram__bytes_write.sum) on the default workload, valid while the sources
 # of the kernel (the regions below: EOS, WENO5, face fluxes, the kernel and
 # its launch) hash as recorded
-RHS_TRAFFIC = {'bytes': 413532416 + 154216192, 'workload': 'blast3d', 'base': 128, 'levels': 3,
+RHS_TRAFFIC = {'bytes': 413528064 + 154201088, 'workload': 'blast3d', 'base': 128, 'levels': 3,
                'regions': [('paper_2508_05020_gb300/csrc/amr_kernels.cuh', 'template <typename T> struct Num;',
                             '// Metadata of one patch staged'),
                            ('paper_2508_05020_gb300/csrc/amr_kernels.cuh', '// K4: fused right-hand side',
                             '// K5: coarse-fine flux correction'),
                            ('paper_2508_05020_gb300/csrc/amr_launch.cuh', 'template <typename T, int D, int N> struct RhsCfg',
                             'template <typename T>\ncudaError_t Kernels<T>::prepare')],
-               'hash': 'c24d88e1362b94b6'}
+               'hash': '271b6a34e3d0fce4'}
 
 
 def rhs_source_hash():
