@@ -32,12 +32,11 @@ UNIT = 'cell-updates/s'
 PEAKS_FILE = os.path.join(ROOT, 'MEASURED_PEAKS.json')
 FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 
-# DRAM bytes (read + write) of one k_rhs launch (SSP-RK3 stage 1, 1536 patches) from the ncu capture
-# summarised in profiles/k_rhs_blast3d_128_fp32.md, valid while the kernel sources hash as they did then
 # DRAM bytes of one stage-1 k_rhs launch (ncu, dram__bytes_read.sum +
-# dram__bytes_write.sum) on the default workload, valid while the sources
-# of the kernel (the regions below: EOS, WENO5, face fluxes, the kernel and
-# its launch) hash as recorded
+# dram__bytes_write.sum; the capture summarised in
+# profiles/k_rhs_blast3d_128_fp32.md) on the default workload, valid while the
+# sources of the kernel (the regions below: EOS, WENO5, face fluxes, the
+# kernel and its launch) hash as recorded
 RHS_TRAFFIC = {'bytes': 413528064 + 154201088, 'workload': 'blast3d', 'base': 128, 'levels': 3,
                'regions': [('paper_2508_05020_gb300/csrc/amr_kernels.cuh', 'template <typename T> struct Num;',
                             '// Metadata of one patch staged'),
