@@ -16,7 +16,8 @@ stays refined ahead of moving fronts. These data come from single-level runs
 at the finest resolution of each problem (a fixed set of cells, so that the
 flags of later steps line up with the stencils of the current one).
 
-With --embed diag the d-dimensional training stencils are planar waves of
+With --embed diag (which --lookahead K may accompany) the d-dimensional
+training stencils are planar waves of
 the 1D profiles along the axes and along the face and body diagonals (offset
 o of the 5^d stencil reads the profile at o . n for an integer direction n,
 the velocity is u n / |n|): fronts oblique to the grid, as a spherical blast
@@ -26,7 +27,7 @@ steps); the plain sensor compares the +-1 neighbours along each axis, which
 are the profile's +-1 neighbours for every such direction, so the label is
 the 1D flag of the profile.
 
-    python -m paper_2508_05020_gb300.train_indicator --out DIR [--lookahead K | --embed diag]
+    python -m paper_2508_05020_gb300.train_indicator --out DIR [--lookahead K] [--embed diag]
 """
 import argparse
 import json
@@ -97,10 +98,12 @@ def harvest_lookahead(name, k, max_steps=100000):
 PROFILE = 13                                               # cells of a harvested 1D window (+-6)
 
 
-def harvest_profiles(name, every, max_steps=100000, theta=0.05):
+def harvest_profiles(name, every, max_steps=100000, theta=0.05, lookahead=0):
     """13-cell (rho, u, p) windows around every interior cell of single-level
     runs at the problem's finest resolution, every `every` steps, and the
-    plain flag of the centre cell."""
+    plain flag of the centre cell (with lookahead K: the OR of its flags at
+    that step and the next K steps; the cells of the level are fixed, so a
+    window's later flags are those of the same cell)."""
     from paper_2508_05020_gb300.amr import AMR
     from synth import workload
     w0 = workload(name)
@@ -109,11 +112,12 @@ def harvest_profiles(name, every, max_steps=100000, theta=0.05):
     a = AMR(w, precision=64)
     gm1 = w['gamma'] - 1.0
     h = PROFILE // 2
-    win, lab = [], []
+    win, lab, at = [], [], []
+    flags = []                                       # flags of every step (lookahead)
     step = 0
     t = 0.0
     while t < w['t_end'] - 1e-12 and step < max_steps:
-        if step % every == 0:
+        if step % every == 0 or lookahead > 0:
             c, x = a.get_level(0)
             order = np.argsort(c[:, 0])
             U = np.concatenate([x[i] for i in order], axis=1)     # (3, cells)
@@ -127,12 +131,19 @@ def harvest_profiles(name, every, max_steps=100000, theta=0.05):
             for k in (0, 2):
                 fm, f0, fp = prof[:, h - 1, k], prof[:, h, k], prof[:, h + 1, k]
                 f |= np.abs(fp - fm) > theta * (fp + 2.0 * f0 + fm)
-            win.append(prof)
-            lab.append(f.astype(np.uint8))
+            flags.append(f)
+            if step % every == 0:
+                win.append(prof)
+                lab.append(f.astype(np.uint8))
+                at.append(len(flags) - 1)
         a.step(sync=False)
         step += 1
         t, _, _ = a.diag()
     a.close()
+    if lookahead > 0:
+        for i, s in enumerate(at):
+            later = flags[s:s + lookahead + 1]
+            lab[i] = np.logical_or.reduce(later).astype(np.uint8)
     return np.concatenate(win), np.concatenate(lab)
 
 
@@ -260,8 +271,8 @@ def main():
 
 def main_diag(args):
     t0 = time.time()
-    p1, l1 = harvest_profiles('sod', every=2)
-    p2, l2 = harvest_profiles('shu_osher', every=4)
+    p1, l1 = harvest_profiles('sod', every=2, lookahead=args.lookahead)
+    p2, l2 = harvest_profiles('shu_osher', every=4, lookahead=args.lookahead)
     prof = np.concatenate([p1, p2])
     y = np.concatenate([l1, l2])
     rng = np.random.default_rng(0)
@@ -270,7 +281,8 @@ def main_diag(args):
     te, tr = perm[:n_test], perm[n_test:]
     os.makedirs(args.out, exist_ok=True)
     report = {'profiles': int(len(prof)), 'positives': int(y.sum()), 'harvest_s': time.time() - t0,
-              'embed': 'axes and diagonals'}
+              'embed': 'axes and diagonals', 'lookahead': args.lookahead}
+    suffix = '_k%d' % args.lookahead if args.lookahead > 0 else ''
     from paper_2508_05020_gb300 import amr
     for dim in [int(x) for x in args.dims.split(',')]:
         t1 = time.time()
@@ -284,7 +296,7 @@ def main_diag(args):
         dsel = dirs[rng.integers(0, len(dirs), size=len(pick))]
         X = embedded_features(prof[pick], dim, dsel, 1.4)
         w, hist, pw = train_features(dim, X, y[pick].astype(np.float32), args.epochs, args.batch, args.lr)
-        np.save(os.path.join(args.out, 'indicator_d%d.npy' % dim), w)
+        np.save(os.path.join(args.out, 'indicator_d%d%s.npy' % (dim, suffix)), w)
         # held out: every direction of the test profiles
         tsel = te[: max(1, 200000 // len(dirs))]
         Xt = embedded_features(np.repeat(prof[tsel], len(dirs), axis=0), dim, np.tile(dirs, (len(tsel), 1)), 1.4)
@@ -296,7 +308,7 @@ def main_diag(args):
                                'heldout_all_directions': {'recall': tp / max(1, tp + fn),
                                                           'precision': tp / max(1, tp + fp), 'rows': int(len(yt))}}
         print(json.dumps({'dim': dim, **report['d%d' % dim]}), flush=True)
-    with open(os.path.join(args.out, 'indicator_report.json'), 'w') as f:
+    with open(os.path.join(args.out, 'indicator_report%s.json' % suffix), 'w') as f:
         json.dump(report, f, indent=1)
     print(json.dumps(report))
     return 0
