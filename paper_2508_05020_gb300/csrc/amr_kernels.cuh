@@ -480,10 +480,6 @@ __device__ void in_domain_value(const Grid& g, const T* U, const PatchMeta& m, c
     prolong_cell<T, D, N>(g, U, m, l, out);
 }
 
-// post- or pre-shock conserved state of the double Mach reflection
-template <typename T, int D>
-__device__ __forceinline__ void dmr_state(const Grid& g, bool behind, T* out);
-
 // Ghost value of local cell l of a patch: physical boundary rules applied from
 // the highest out-of-domain dimension down (the outcome of filling the
 // boundary dimension by dimension in the order x, y, z), then the in-domain
