@@ -41,19 +41,19 @@ def unmet(w, flagger, weights, every, steps):
     patch count."""
     from paper_2508_05020_gb300.amr import AMR
     a = AMR(w, precision=64, flagger=flagger, mlp_weights=weights)
-    judge = AMR(w, precision=64, flagger='plain')
+    plain_ref = AMR(w, precision=64, flagger='plain')
     miss, patches = [], []
     for i in range(steps):
         a.step()
         lv, co, da = state(a)
-        judge.set_state(lv, co, da, t=a.diag()[0])
-        r, _ = judge.requests()
+        plain_ref.set_state(lv, co, da, t=a.diag()[0])
+        r, _ = plain_ref.requests()
         miss.append(len(r))
         patches.append(int(sum(a.diag()[2])))
         if (i + 1) % every == 0:
             a.regrid()
     a.close()
-    judge.close()
+    plain_ref.close()
     return float(np.mean(miss)), float(np.mean(patches))
 
 
