@@ -49,3 +49,38 @@ def test_single_process_passthrough():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.combine_ranks(3.0, 7.0, None) == (3.0, 7.0)
+
+
+def test_roofline_accounting():
+    # the algorithmic FLOPs and cells of a launch follow from the hierarchy:
+    # leaves only (a patch with children is restricted, not advanced)
+    sys.path.insert(0, ROOT)
+    import bench
+    from synth import workload
+    w = workload('blast3d')
+    ppl = [512, 512, 512, 0, 0, 0, 0, 0]
+    assert bench.leaf_patches(w, ppl) == 512 - 64 + 512 - 64 + 512
+    cc = bench.cell_counts(w, ppl[:3])
+    assert cc['leaf_cells'] == 1408 * 4096 and cc['all_patch_cells'] == 1536 * 4096
+    assert cc['stage_updates_per_step'] == 3 * cc['leaf_cells']
+    assert cc['fine_equivalent'] == 512 ** 3
+
+    class Fake:
+        def diag(self):
+            return 0.0, None, ppl
+
+    flops = bench.load_json(bench.FLOPS_FILE, None)
+    f = flops['3']
+    got = bench.rhs_flops_per_launch(Fake(), w, flops)
+    assert got == 1408 * 3 * 16 * 16 * 17 * f['face'] + 1408 * 4096 * f['cell']
+    wc = workload('shear2d', dim=3, base_cells=(128, 128, 128), levels=3, patch=16)
+    got = bench.rhs_flops_per_launch(Fake(), wc, flops)
+    rows = 1408 * 3 * 16 * 16
+    assert got == rows * (19 * f['face_central'] + 17 * f['face_combine_central']) + 1408 * 4096 * f['cell']
+    assert bench.rhs_flops_per_launch(Fake(), workload('blast3d', flux='hllc'), flops) is None
+    # the recorded DRAM bytes apply to the default workload, and only while the
+    # kernel's sources hash as they did at capture (else null)
+    assert bench.rhs_traffic('blast3d', 0, 0) in (bench.RHS_TRAFFIC['bytes'], None)
+    assert (bench.rhs_traffic('blast3d', 0, 0) is None) == (bench.rhs_source_hash() != bench.RHS_TRAFFIC['hash'])
+    assert bench.rhs_traffic('blast3d', 64, 0) is None
+    assert bench.rhs_traffic('dmr', 0, 0) is None
