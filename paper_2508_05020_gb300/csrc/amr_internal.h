@@ -86,9 +86,12 @@ struct Kernels {
     static cudaError_t prepare_mlp(const Grid& g);
     // ghost cells of every patch of `level` (same-level copy, prolongation,
     // physical boundaries) at time t + tfrac * dt
-    // faces_only: face ghosts only (all a stage reads), else every ghost cell
+    // stage_only: the face ghosts without a same-level neighbour across their
+    // face (all a stage reads from a slot's ghost region: the RHS and the
+    // prolongation read same-level neighbours' interiors directly); else every
+    // ghost cell (what the flag stencils read)
     static cudaError_t ghost_fill(const Grid& g, T* U, int level, double tfrac, int grid,
-                                  cudaStream_t s, int one_slot, int chunk = 512, bool faces_only = false);
+                                  cudaStream_t s, int one_slot, int chunk = 512, bool stage_only = false);
     // RHS + SSP-RK3 stage of every patch (or one patch if one_slot >= 0)
     static cudaError_t rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces,
                                  int stage, int grid, cudaStream_t s, int one_slot);

@@ -384,7 +384,11 @@ __device__ __forceinline__ void load_meta_warp(const Grid& g, int slot, PatchMet
 // U_C + sum_d (+-1/4) s_d, dims in order; U_C for every child of C if any
 // child has rho <= 0 or p <= 0.
 // ---------------------------------------------------------------------------
-template <typename T, int D, int N>
+// NBR_READS (the ghost fill): C +- e_d outside Q is read from Q's same-level
+// neighbour when it exists, as a stage leaves that face ghost of Q unfilled;
+// otherwise (new patches in a regrid, which may create that neighbour in the
+// same launch) from Q's ghost cells, filled before the mesh changed.
+template <typename T, int D, int N, bool NBR_READS>
 __device__ void prolong_cell(const Grid& g, const T* U, const PatchMeta& m, const int* l, T* out) {
     constexpr int NV = D + 2;
     const int* c = m.c;
@@ -413,10 +417,21 @@ __device__ void prolong_cell(const Grid& g, const T* U, const PatchMeta& m, cons
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         const int ex = d == 0, ey = d == 1, ez = d == 2;
+        // C +- e_d outside Q: see NBR_READS
+        long long ip = slot_index(g, Q, 0, bz + ez, by + ey, bx + ex);
+        long long im = slot_index(g, Q, 0, bz - ez, by - ey, bx - ex);
+        if (NBR_READS && Lc[d] == N - 1) {
+            const int qn = g.nbr[Q * NBR + 13 + (d == 0 ? 1 : (d == 1 ? 3 : 9))];
+            if (qn >= 0) ip = slot_index(g, qn, 0, bz - (N - 1) * ez, by - (N - 1) * ey, bx - (N - 1) * ex);
+        }
+        if (NBR_READS && Lc[d] == 0) {
+            const int qn = g.nbr[Q * NBR + 13 - (d == 0 ? 1 : (d == 1 ? 3 : 9))];
+            if (qn >= 0) im = slot_index(g, qn, 0, bz + (N - 1) * ez, by + (N - 1) * ey, bx + (N - 1) * ex);
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const T up = U[slot_index(g, Q, v, bz + ez, by + ey, bx + ex)];
-            const T um = U[slot_index(g, Q, v, bz - ez, by - ey, bx - ex)];
+            const T up = U[ip + (long long)v * g.slot_elems];
+            const T um = U[im + (long long)v * g.slot_elems];
             const T a = up - UC[v];
             const T b = UC[v] - um;
             const T pick = fabs(a) <= fabs(b) ? a : b;
@@ -477,7 +492,7 @@ __device__ void in_domain_value(const Grid& g, const T* U, const PatchMeta& m, c
         for (int v = 0; v < NV; ++v) out[v] = U[slot_index(g, nb, v, sz, sy, sx)];
         return;
     }
-    prolong_cell<T, D, N>(g, U, m, l, out);
+    prolong_cell<T, D, N, true>(g, U, m, l, out);
 }
 
 // Ghost value of local cell l of a patch: physical boundary rules applied from
@@ -560,7 +575,8 @@ __device__ void ghost_value(const Grid& g, const T* U, const PatchMeta& m, int* 
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
-                                               double4 pre, double4 post, int chunk, int n_cells) {
+                                               double4 pre, double4 post, int chunk, int n_cells,
+                                               int stage_only) {
     constexpr int NV = D + 2;
     __shared__ PatchMeta metas[256 / 32];
     if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
@@ -583,6 +599,12 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
             const int pk = g.ghost_tab[gi];
             int l[3] = {(pk & 1023) - G, ((pk >> 10) & 1023) - G, ((pk >> 20) & 1023) - G};
             const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
+            if (stage_only) {                            // a face ghost: is there a same-level neighbour?
+                int o[3] = {0, 0, 0};
+#pragma unroll
+                for (int d = 0; d < D; ++d) o[d] = l[d] < 0 ? -1 : (l[d] >= N ? 1 : 0);
+                if (m.nbr[(o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1)] >= 0) continue;
+            }
             T val[NV];
             ghost_value<T, D, N>(g, U, m, l, t, val, pr, po);
 #pragma unroll
@@ -679,25 +701,68 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 for (int d = 0; d < D; ++d) q[(1 + d) * C::QN + qidx] = u[d];
                 q[(D + 1) * C::QN + qidx] = Tt;
             };
-            auto loadv = [&](T (&Uv)[NV][VE], int sz, int sy, int sx) {
+            auto loadv = [&](T (&Uv)[NV][VE], int src, int sz, int sy, int sx) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    const T* src = Us + slot_index(g, slot, v, sz, sy, sx);
+                    const T* p = Us + slot_index(g, src, v, sz, sy, sx);
                     if constexpr (sizeof(T) == 4) {
-                        const float4 t4 = *reinterpret_cast<const float4*>(src);
+                        const float4 t4 = *reinterpret_cast<const float4*>(p);
                         Uv[v][0] = t4.x; Uv[v][1] = t4.y; Uv[v][2] = t4.z; Uv[v][3] = t4.w;
                     } else {
-                        const double2 t2 = *reinterpret_cast<const double2*>(src);
+                        const double2 t2 = *reinterpret_cast<const double2*>(p);
                         Uv[v][0] = t2.x; Uv[v][1] = t2.y;
                     }
                 }
             };
-            // centre planes (3D) or the whole slot (1D/2D): full rows
+            // face ghosts come from the same-level neighbour across the face
+            // when it exists (the stage's ghost fill leaves them unfilled),
+            // else from the slot's own ghost cells: neighbour slot and the
+            // shift of the slot coordinate along that dimension
+            auto across = [&](int d, int side, int& src, int& shift) {
+                const int nb = g.nbr[slot * NBR + 13 + (side ? 1 : -1) * (d == 0 ? 1 : (d == 1 ? 3 : 9))];
+                src = nb >= 0 ? nb : slot;
+                shift = nb >= 0 ? (side ? -N : N) : 0;
+            };
+            int sxm, dxm, sxp, dxp;
+            across(0, 0, sxm, dxm);
+            across(0, 1, sxp, dxp);
+            // centre planes (3D) or the whole slot (1D/2D): full rows; a row
+            // outside the interior along y comes whole from its y source (its
+            // x ghosts are edge cells, which no face reads)
             constexpr int NXV = (C::QX + VE - 1) / VE;
             for (int iv = threadIdx.x; iv < NXV * C::QY * C::QZ; iv += NTH) {
                 const int xv = iv % NXV, qy = (iv / NXV) % C::QY, qz = iv / (NXV * C::QY);
+                const int sz = D == 3 ? z0 + G + qz : 0;
+                const int x0 = xv * VE;
                 T Uv[NV][VE];
-                loadv(Uv, D == 3 ? z0 + G + qz : 0, qy, xv * VE);
+                const int ly = qy - G;
+                if (D >= 2 && (ly < 0 || ly >= N)) {
+                    int src, sh;
+                    across(1, ly >= N, src, sh);
+                    loadv(Uv, src, sz, qy + sh, x0);
+                } else {
+                    loadv(Uv, slot, sz, qy, x0);
+                    if (x0 < G) {                            // x ghosts below the interior
+                        T Wv[NV][VE];
+                        loadv(Wv, sxm, sz, qy, x0 + dxm);
+#pragma unroll
+                        for (int e = 0; e < VE; ++e)
+                            if (x0 + e < G) {
+#pragma unroll
+                                for (int v = 0; v < NV; ++v) Uv[v][e] = Wv[v][e];
+                            }
+                    }
+                    if (x0 + VE > G + N) {                   // x ghosts above the interior
+                        T Wv[NV][VE];
+                        loadv(Wv, sxp, sz, qy, x0 + dxp);
+#pragma unroll
+                        for (int e = 0; e < VE; ++e)
+                            if (x0 + e >= G + N) {
+#pragma unroll
+                                for (int v = 0; v < NV; ++v) Uv[v][e] = Wv[v][e];
+                            }
+                    }
+                }
 #pragma unroll
                 for (int e = 0; e < VE; ++e) {
                     const int qx = xv * VE + e;
@@ -705,13 +770,21 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 }
             }
             if constexpr (D == 3) {
-                // halo planes: interior x in [G, G + N) from aligned vectors
+                // halo planes: interior x in [G, G + N) from aligned vectors,
+                // from the z source when the plane lies outside the interior
                 constexpr int HX0 = (G / VE) * VE;
                 constexpr int NHV = (G + N - HX0 + VE - 1) / VE;
+                int szm, dzm, szp, dzp;
+                across(2, 0, szm, dzm);
+                across(2, 1, szp, dzp);
                 for (int iv = threadIdx.x; iv < NHV * N * 2 * G; iv += NTH) {
                     const int xv = iv % NHV, hy = (iv / NHV) % N, zh = iv / (NHV * N);
+                    const int sz = z0 + (zh < G ? zh : zh + DZ);
+                    const int lz = sz - G;
+                    const int src = lz < 0 ? szm : (lz >= N ? szp : slot);
+                    const int shz = lz < 0 ? dzm : (lz >= N ? dzp : 0);
                     T Uv[NV][VE];
-                    loadv(Uv, z0 + (zh < G ? zh : zh + DZ), hy + G, HX0 + xv * VE);
+                    loadv(Uv, src, sz + shz, hy + G, HX0 + xv * VE);
 #pragma unroll
                     for (int e = 0; e < VE; ++e) {
                         const int x = HX0 + xv * VE + e;
@@ -1304,7 +1377,7 @@ __global__ void __launch_bounds__(256) k_prolong_new(Grid g, T* U, const int* li
         for (int ci = threadIdx.x; ci < NC; ci += blockDim.x) {
             int l[3] = {ci % N, D >= 2 ? (ci / N) % N : 0, D == 3 ? ci / (N * N) : 0};
             T val[NV];
-            prolong_cell<T, D, N>(g, U, m, l, val);
+            prolong_cell<T, D, N, false>(g, U, m, l, val);
             const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
 #pragma unroll
             for (int v = 0; v < NV; ++v) U[slot_index(g, slot, v, sz, sy, sx)] = val[v];
