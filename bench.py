@@ -37,14 +37,14 @@ FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 # profiles/k_rhs_blast3d_128_fp32.md) on the default workload, valid while the
 # sources of the kernel (the regions below: EOS, WENO5, face fluxes, the
 # kernel and its launch) hash as recorded
-RHS_TRAFFIC = {'bytes': 413528064 + 154201088, 'workload': 'blast3d', 'base': 128, 'levels': 3,
+RHS_TRAFFIC = {'bytes': 320362496 + 152754688, 'workload': 'blast3d', 'base': 128, 'levels': 3,
                'regions': [('paper_2508_05020_gb300/csrc/amr_kernels.cuh', 'template <typename T> struct Num;',
                             '// Metadata of one patch staged'),
                            ('paper_2508_05020_gb300/csrc/amr_kernels.cuh', '// K4: fused right-hand side',
                             '// K5: coarse-fine flux correction'),
                            ('paper_2508_05020_gb300/csrc/amr_launch.cuh', 'template <typename T, int D, int N> struct RhsCfg',
                             'template <typename T>\ncudaError_t Kernels<T>::prepare')],
-               'hash': '271b6a34e3d0fce4'}
+               'hash': '3a9f979e10e4a37b'}
 
 
 def rhs_source_hash():
