@@ -1066,26 +1066,38 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     std::memset(c->time_h, 0, sizeof(DevTime));
     CK(cudaMemcpyAsync(c->time_d, c->time_h, sizeof(DevTime), cudaMemcpyHostToDevice, c->stream), "time");
 
-    // ghost-cell table of a slot: packed slot coordinates (x | y << 10 | z << 20),
-    // face ghosts (outside the interior along one dimension) first, then edge
-    // and corner ghosts, each in slot order. The stage reads face ghosts only
-    // (pencils along one dimension, prolongation slopes along one dimension);
-    // the flag stencils read all of them
-    std::vector<int> gt, gt_ec;
+    // ghost-cell tables of a slot, packed slot coordinates (x | y << 10 | z << 20):
+    // every ghost cell in slot order (the regrid's fill, before the flag
+    // stencils), then the face ghosts (outside the interior along one
+    // dimension) box by box (x low, x high, y low, ...; G N^(d-1) cells each,
+    // slot order inside a box: a stage fills or skips a box whole)
+    std::vector<int> gt, gt_box;
     for (int z = 0; z < g.SZ; ++z)
         for (int y = 0; y < g.SY; ++y)
             for (int x = 0; x < S; ++x) {
                 const bool gx = x < G || x >= G + patch_size;
                 const bool gy = dim >= 2 && (y < G || y >= G + patch_size);
                 const bool gz = dim == 3 && (z < G || z >= G + patch_size);
-                const int nout = (int)gx + (int)gy + (int)gz;
-                const int pk = x | ((dim >= 2 ? y : G) << 10) | ((dim == 3 ? z : G) << 20);
-                if (nout == 1) gt.push_back(pk);
-                else if (nout > 1) gt_ec.push_back(pk);
+                if (gx || gy || gz) gt.push_back(x | ((dim >= 2 ? y : G) << 10) | ((dim == 3 ? z : G) << 20));
             }
-    c->n_ghost_face = (int)gt.size();
-    gt.insert(gt.end(), gt_ec.begin(), gt_ec.end());
+    for (int b = 0; b < 2 * dim; ++b)
+        for (int z = 0; z < g.SZ; ++z)
+            for (int y = 0; y < g.SY; ++y)
+                for (int x = 0; x < S; ++x) {
+                    const int cc[3] = {x, y, z};
+                    int nout = 0, dout = -1, sout = 0;
+                    for (int d = 0; d < dim; ++d)
+                        if (cc[d] < G || cc[d] >= G + patch_size) {
+                            ++nout;
+                            dout = d;
+                            sout = cc[d] >= G + patch_size;
+                        }
+                    if (nout == 1 && 2 * dout + sout == b)
+                        gt_box.push_back(x | ((dim >= 2 ? y : G) << 10) | ((dim == 3 ? z : G) << 20));
+                }
     c->n_ghost = (int)gt.size();
+    c->n_ghost_face = (int)gt_box.size();
+    gt.insert(gt.end(), gt_box.begin(), gt_box.end());
     c->ghost_tab = (int*)dalloc(c, gt.size() * sizeof(int));
     if (!c->ghost_tab) return fail(c, AMR_ERR_CUDA, "device allocation failed");
     CK(cudaMemcpyAsync(c->ghost_tab, gt.data(), gt.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "ghosts");

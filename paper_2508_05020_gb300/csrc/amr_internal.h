@@ -71,9 +71,10 @@ struct Grid {
     const int* reflux_list;     // leaf slots with at least one coarse-fine face
     const int* reflux_fine;     // [n_reflux * 6 * 4]: fine slots across each face (-1 if none)
     const int* new_list;        // slots created by the last regrid
-    const int* ghost_tab;       // packed local (x,y,z)+3 of every ghost cell of a slot
-    int n_ghost;                // ghost cells of a slot; the first n_ghost_face lie outside the
-    int n_ghost_face;           //   interior along one dimension only (face ghosts)
+    const int* ghost_tab;       // packed local (x,y,z)+3 of every ghost cell of a slot (slot order),
+                                //   followed by the n_ghost_face face ghosts box by box
+    int n_ghost;                // ghost cells of a slot
+    int n_ghost_face;           // of them outside the interior along one dimension only (face ghosts)
     DevTime* time;
 };
 

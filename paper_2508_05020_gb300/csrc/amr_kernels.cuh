@@ -566,12 +566,14 @@ __device__ void ghost_value(const Grid& g, const T* U, const PatchMeta& m, int* 
 }
 
 // ---------------------------------------------------------------------------
-// K1-K3: ghost fill of every patch of one level: the first n_cells entries of
-// the slot's ghost table (face ghosts first, then edge and corner ghosts; a
-// stage fills the face ghosts only, the regrid all of them). A work item is a
-// patch and a run of `chunk` of those cells (the size is a launch parameter
-// chosen by the autotuner), taken by one warp, which stages the patch's
-// metadata in its own shared-memory copy; warps never wait for one another.
+// K1-K3: ghost fill of every patch of one level. The regrid fills every ghost
+// cell (the slot-order table); a stage (stage_only) fills the face boxes that
+// have no same-level neighbour across them (coarse-fine and domain sides),
+// whose cells the RHS reads from the slot (the box-order table that follows
+// the first). A work item is a patch and a run of
+// `chunk` cells (the size is a launch parameter chosen by the autotuner),
+// taken by one warp, which stages the patch's metadata in its own
+// shared-memory copy; warps never wait for one another.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
@@ -587,24 +589,30 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
     const double t = g.time->t + tfrac * g.time->dt;
     const double pr[4] = {pre.x, pre.y, pre.z, pre.w};
     const double po[4] = {post.x, post.y, post.z, post.w};
-    const int nchunk = (n_cells + chunk - 1) / chunk;     // chunk: ghost cells per work item
+    // a stage walks the 2d face boxes of a patch (G N^(d-1) table entries
+    // each) and skips a box whole when a same-level neighbour lies across it
+    constexpr int BOX = G * (D == 1 ? 1 : (D == 2 ? N : N * N));
+    const int* tab = stage_only ? g.ghost_tab + g.n_ghost : g.ghost_tab;   // box order, or slot order
+    const int span = stage_only ? BOX : n_cells;          // table entries one run of items covers
+    const int nruns = stage_only ? 2 * D : 1;
+    const int nchunk = (span + chunk - 1) / chunk;        // chunk: ghost cells per work item
     const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int item = blockIdx.x * (blockDim.x >> 5) + warp; item < npatch * nchunk; item += nw) {
-        const int pi = item / nchunk;
-        const int g0 = (item - pi * nchunk) * chunk;
-        const int g1 = min(g0 + chunk, n_cells);
+    for (int item = blockIdx.x * (blockDim.x >> 5) + warp; item < npatch * nruns * nchunk; item += nw) {
+        const int pi = item / (nruns * nchunk);
+        const int rest = item - pi * nruns * nchunk;
+        const int run = rest / nchunk;
+        const int g0 = run * span + (rest - run * nchunk) * chunk;
+        const int g1 = min(g0 + chunk, run * span + span);
         const int slot = one_slot >= 0 ? one_slot : g.all_list[lo + pi];
+        if (stage_only) {
+            const int d = run >> 1;
+            if (g.nbr[slot * NBR + 13 + ((run & 1) ? 1 : -1) * (d == 0 ? 1 : (d == 1 ? 3 : 9))] >= 0) continue;
+        }
         load_meta_warp(g, slot, m);
         for (int gi = g0 + lane; gi < g1; gi += 32) {
-            const int pk = g.ghost_tab[gi];
+            const int pk = tab[gi];
             int l[3] = {(pk & 1023) - G, ((pk >> 10) & 1023) - G, ((pk >> 20) & 1023) - G};
             const int sx = l[0] + G, sy = D >= 2 ? l[1] + G : 0, sz = D == 3 ? l[2] + G : 0;
-            if (stage_only) {                            // a face ghost: is there a same-level neighbour?
-                int o[3] = {0, 0, 0};
-#pragma unroll
-                for (int d = 0; d < D; ++d) o[d] = l[d] < 0 ? -1 : (l[d] >= N ? 1 : 0);
-                if (m.nbr[(o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1)] >= 0) continue;
-            }
             T val[NV];
             ghost_value<T, D, N>(g, U, m, l, t, val, pr, po);
 #pragma unroll
