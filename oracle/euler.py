@@ -176,7 +176,7 @@ def face_flux(P, dim, gamma, flux='rusanov'):
     wr = [weno5_left(W[5][f], W[4][f], W[3][f], W[2][f], W[1][f]) for f in range(nf)]
     pL, unL, utL, TL = char_inverse(wl, z, kap)
     pR, unR, utR, TR = char_inverse(wr, z, kap)
-    bad = ~((pL > 0.0) & (TL > 0.0) & (pR > 0.0) & (TR > 0.0))
+    bad = np.logical_not((pL > 0.0) & (TL > 0.0) & (pR > 0.0) & (TR > 0.0))
     if np.any(bad):
         pL = np.where(bad, p2, pL)
         unL = np.where(bad, un2, unL)
@@ -232,7 +232,7 @@ def central_face_flux(P, dim, gamma):
     un = central_mid(P[0][1], P[1][1], P[2][1], P[3][1])
     ut = [central_mid(P[0][2][j], P[1][2][j], P[2][2][j], P[3][2][j]) for j in range(nt)]
     T = central_mid(P[0][3], P[1][3], P[2][3], P[3][3])
-    bad = ~((p > 0.0) & (T > 0.0))
+    bad = np.logical_not((p > 0.0) & (T > 0.0))
     if np.any(bad):
         p = np.where(bad, 0.5 * (P[1][0] + P[2][0]), p)
         un = np.where(bad, 0.5 * (P[1][1] + P[2][1]), un)

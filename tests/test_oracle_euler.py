@@ -446,3 +446,26 @@ def test_shear_layer_initial_state():
     # 5 periods of the transverse perturbation across the domain
     v_layer = v_all[int(round((0.15 + 0.3) / 0.6 * n - 0.5))]
     assert np.sum(np.diff(np.sign(v_layer)) != 0) in (9, 10, 11)
+
+
+def test_central_positivity_guard():
+    # a pressure dip that the cubic overshoots below zero: the face takes the
+    # mean of the two nodes beside it, and the flux is the Euler flux there
+    P = [(1.0, 0.1, [0.0], 1.0), (1e-3, 0.2, [0.1], 1e-3), (1e-3, 0.3, [0.2], 1e-3), (1.0, 0.4, [0.3], 1.0)]
+    F = euler.central_face_flux(P, 2, 1.4)
+    p, un, ut, T = 1e-3, 0.25, 0.15, 1e-3
+    rho = p / T
+    E = p / 0.4 + 0.5 * rho * (un * un + ut * ut)
+    ref = [rho * un, rho * un * un + p, rho * un * ut, (E + p) * un]
+    assert np.allclose(F, ref, rtol=1e-14, atol=0)
+    # away from the dip the cubic mid-point values are used unchanged: on
+    # quadratic node data f(-1..2) they are f(1/2), not the mean of f(0), f(1)
+    q = lambda a, b, c: [a + b * x + c * x * x for x in (-1.0, 0.0, 1.0, 2.0)]
+    pp, uu, tt, TT = q(1.1, 0.15, 0.05), q(0.2, 0.1, 0.02), q(0.1, 0.1, -0.01), q(1.05, 0.05, 0.03)
+    P2 = [(pp[k], uu[k], [tt[k]], TT[k]) for k in range(4)]
+    F2 = euler.central_face_flux(P2, 2, 1.4)
+    pm, um, tm, Tm = 1.1 + 0.075 + 0.0125, 0.2 + 0.05 + 0.005, 0.1 + 0.05 - 0.0025, 1.05 + 0.025 + 0.0075
+    assert abs(pm - 0.5 * (pp[1] + pp[2])) > 1e-3
+    rm = pm / Tm
+    Em = pm / 0.4 + 0.5 * rm * (um * um + tm * tm)
+    assert np.allclose(F2, [rm * um, rm * um * um + pm, rm * um * tm, (Em + pm) * um], rtol=1e-13)
