@@ -159,8 +159,10 @@ def run_reference(args, rank, world):
     line = {'impl': 'reference', 'metric': METRIC, 'value': val, 'unit': UNIT, 'n_gpus': world,
             'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1000.0 * total / len(per_step),
             'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
-            'data': 'synthetic', 'config': {'workload': 'blast3d 16^3 base (bounded sample of 128^3), 3 levels, '
-                                            '16^3 patches, FP64 CPU oracle'},
+            'data': 'synthetic', 'config': {'workload': 'blast3d base 128x128x128, 3 levels, 16^3 patches, FP32, '
+                                                        'mlp flags, rusanov flux',
+                                            'reference_sample': 'the FP64 CPU oracle (plain flags) on the same '
+                                                                'problem at 16^3 base cells per timed step'},
             'cpu_baseline': {'value': val, 'unit': UNIT, 'cores': 1, 'kind': 'oracle', 'sample': desc},
             'e2e': {'value': val, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
     print(json.dumps(line), flush=True)
