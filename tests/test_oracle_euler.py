@@ -469,3 +469,19 @@ def test_central_positivity_guard():
     rm = pm / Tm
     Em = pm / 0.4 + 0.5 * rm * (um * um + tm * tm)
     assert np.allclose(F2, [rm * um, rm * um * um + pm, rm * um * tm, (Em + pm) * um], rtol=1e-13)
+
+
+def test_ssp_rk3_is_third_order_in_time():
+    # the same spatial discretisation (central schemes, 32 cells) at three
+    # step sizes against a 1024-step reference: halving dt divides the
+    # difference by 8; a wrong stage weight of the Shu-Osher form drops the
+    # order to 2 or 1
+    def run(k, T=0.1):
+        w = workload('density_wave', base_cells=(32, 1, 1), patch=16, flux='central')
+        o = Oracle(w)
+        for _ in range(k):
+            o.step(dt=T / k)
+        return o.leaf_field(0)[0, 0]
+    ref = run(1024)
+    e = [np.max(np.abs(run(k) - ref)) for k in (16, 32, 64)]
+    assert 7.5 < e[0] / e[1] < 8.5 and 7.5 < e[1] / e[2] < 8.5, e
