@@ -6,10 +6,13 @@
  * patch has the same N^d cells plus 3 ghost layers per side, level-0 patches
  * form a Cartesian layout and each is the root of a binary tree / quadtree /
  * octree with refinement ratio 2 (Sec. 4.3). One call to amr_step advances
- * every patch of every level by one SSP-RK3 step (Sec. 3.2) with the
- * characteristic WENO5-JS interpolation and the Rusanov flux (Eqs. 10-12);
- * amr_regrid applies the refinement requests under rules R1/R2 with
- * Algorithm 1 and the coarsening rule of Sec. 4.3.
+ * the hierarchy by one SSP-RK3 step (Sec. 3.2), all levels with the same dt:
+ * every leaf patch with the characteristic WENO5-JS interpolation and the
+ * Rusanov flux (Eqs. 10-12; options: the HLLC flux, or the central schemes
+ * of Eqs. 8-9 for shock-free flows), every patch with children by
+ * restriction from them after each stage; amr_regrid applies the refinement
+ * requests under rules R1/R2 with Algorithm 1 and the coarsening rule of
+ * Sec. 4.3.
  *
  * Conventions for every entry point:
  *   - return value: AMR_OK (0) or a negative AMR_ERR_* code; no exception or
@@ -149,7 +152,8 @@ void amr_default_options(amr_options_t* opt);
 int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int base_cells[3],
              int levels, int ratio, int patch_size, int ic_id, const amr_options_t* opt);
 
-/* One SSP-RK3 step (Sec. 3.2) of every patch of every level. dt <= 0 takes
+/* One SSP-RK3 step (Sec. 3.2) of the hierarchy (leaves advanced, patches with
+ * children restricted from them after each stage). dt <= 0 takes
  * dt = CFL / max over leaf cells of sum_d (|u_d| + c) / dx_d (clipped to
  * t_end); dt > 0 is used as given. dt_used (may be NULL) receives the step;
  * passing NULL avoids a device-to-host synchronisation. */
