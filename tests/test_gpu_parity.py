@@ -96,6 +96,11 @@ def run_both(w, steps, regrid=True, **kw):
     # 32-cell patches in 2D, a single level in 3D
     ('riemann2d', dict(base_cells=(128, 128, 1), patch=32, levels=2), 3, 0.0),
     ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=1), 2, 0.0),
+    # cells of unequal size per dimension (dy = dx / 2; dz = dx / 2): every
+    # other workload has square cells, so a cell size taken from the wrong
+    # dimension would go unseen there
+    ('riemann2d', dict(base_cells=(32, 64, 1), patch=8), 4, 0.0),
+    ('blast3d', dict(base_cells=(16, 16, 32), patch=8, levels=2), 2, 0.0),
 ])
 def test_fp64_matches_oracle(name, kw, steps, tol):
     w = workload(name, **kw)

@@ -524,3 +524,50 @@ def test_mirror_and_transpose_symmetry(flux):
     M = mirror(G)
     for v in range(4):
         assert np.max(np.abs(G[v] - M[v])) <= 1e-13 * np.max(np.abs(G[v])), v
+
+
+@pytest.mark.parametrize('flux', ['rusanov', 'hllc', 'central'])
+def test_planar_tube_reduces_to_the_1d_scheme(flux):
+    # the Sod tube laid along x, y or z of a 2D or 3D box, uniform across the
+    # other axes (periodic there, with a cell size 4 times the tube's), run
+    # with the 1D run's dt sequence: every line along the tube carries the 1D
+    # scheme's values exactly (the transverse flux differences vanish, the
+    # tangential velocities stay zero and add nothing to the energy). A wrong
+    # normal component, cell size or stencil axis in any dimension breaks it
+    w1 = workload('sod', levels=1, flux=flux)
+    o1 = Oracle(w1)
+    n = w1['base_cells'][0]
+    prof0 = np.stack([o1.leaf_field(v)[0, 0] for v in range(3)])
+    dts = [o1.step() for _ in range(12)]
+    prof = np.stack([o1.leaf_field(v)[0, 0] for v in range(3)])
+
+    for dim, axis in ((2, 0), (2, 1), (3, 0), (3, 1), (3, 2)):
+        base = [8 if d < dim else 1 for d in range(3)]
+        base[axis] = n
+        hi = [0.5 if d < dim else 1.0 for d in range(3)]
+        hi[axis] = 1.0
+        bc = tuple(('outflow', 'outflow') if d == axis or d >= dim else ('periodic', 'periodic')
+                   for d in range(3))
+        w = workload('constant', dim=dim, base_cells=tuple(base), lo=(0.0, 0.0, 0.0), hi=tuple(hi), bc=bc,
+                     levels=1, patch=8, flux=flux)
+        o = Oracle(w)
+        shape = [1, 1, 1]
+        shape[2 - axis] = n
+
+        def planar(P):
+            F = np.zeros((dim + 2,) + tuple(o.w['base_cells'][d] for d in (2, 1, 0)))
+            F[0] = P[0].reshape(shape)
+            F[1 + axis] = P[1].reshape(shape)
+            F[dim + 1] = P[2].reshape(shape)
+            return F
+
+        F = planar(prof0)
+        N = w['patch']
+        for k in o.mesh.canonical():
+            sl = tuple(slice(k[1][d] * N, (k[1][d] + 1) * N) if d < dim else slice(None) for d in (2, 1, 0))
+            o.U[k][o.inner()] = F[(slice(None),) + sl]
+        for dt in dts:
+            o.step(dt)
+        expect = planar(prof)
+        for v in range(dim + 2):
+            assert np.array_equal(o.leaf_field(v), expect[v]), (dim, axis, v)
