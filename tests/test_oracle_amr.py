@@ -12,9 +12,12 @@ def rel_change(s, s0):
     return np.abs(s - s0) / np.maximum(np.abs(s0), 1.0)
 
 
-def test_conservation_periodic_with_regrid():
-    # the implosion problem of Sec. 6 (Eq. 13) on a periodic box, 3 levels
-    w = workload('implosion', base_cells=(32, 32, 1), patch=8, levels=3)
+@pytest.mark.parametrize('base', [(32, 32, 1), (32, 16, 1)])
+def test_conservation_periodic_with_regrid(base):
+    # the implosion problem of Sec. 6 (Eq. 13) on a periodic box, 3 levels;
+    # with 32 x 16 base cells dy = 2 dx, so the coarse-fine corrections of the
+    # two dimensions differ in their cell size
+    w = workload('implosion', base_cells=base, patch=8, levels=3)
     o = Oracle(w)
     s0 = o.cons_sums()
     meshes = set()
@@ -217,3 +220,15 @@ def test_cfl_matches_definition():
     assert dt == pytest.approx(0.5 / (np.sqrt(1.4) * 64.0), rel=1e-14)
     rho, u, p, T = euler.primitives(o.U[(0, (0, 0, 0))][o.inner()], 1, 1.4)
     assert np.allclose(p, 1.0)
+
+
+@pytest.mark.parametrize('dim', [2, 3])
+def test_cfl_sums_over_dimensions_with_their_cell_sizes(dim):
+    # uniform rho = 1, u = (0.3, -0.2, 0.1), p = 1 on the unit box with 8, 16
+    # and 32 cells along x, y, z: dt = CFL / sum_d (|u_d| + c) n_d, c = sqrt(1.4)
+    base = (8, 16, 32 if dim == 3 else 1)
+    bc = tuple(('periodic', 'periodic') for _ in range(3))
+    o = Oracle(workload('constant', dim=dim, base_cells=base, patch=8, levels=1, bc=bc))
+    c = np.sqrt(1.4)
+    lam = sum((abs(v) + c) * n for v, n in zip((0.3, -0.2, 0.1)[:dim], base[:dim]))
+    assert o.cfl_dt() == pytest.approx(0.5 / lam, rel=1e-14)
