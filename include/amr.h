@@ -210,6 +210,32 @@ int amr_restore(amr_ctx* ctx, const char* path);
 int amr_get_requests(amr_ctx* ctx, int* n_refine, int* refine_keys,
                      int* n_coarsen, int* coarsen_keys);
 
+/* The mesh half of a regrid on a caller's hierarchy, on the host alone (no
+ * context, no GPU; Sec. 4.3). Starting from the hierarchy `keys` (n rows of
+ * (level, cx, cy, cz), any order, coordinates of unused dimensions 0),
+ * Algorithm 1 is applied to each refinement request in canonical order (a
+ * request for a patch that is absent, has children or lies on level
+ * max_level is skipped), then the coarsening rule of Sec. 4.3 to the
+ * candidates, repeated until it accepts none (children created by this call
+ * stay): the steps amr_regrid takes once it has its requests, so a host-side
+ * planner can foresee a regrid's outcome.
+ * dim 1..3; base_patches: level-0 patches per dimension (entries beyond dim
+ * ignored); periodic: 0 or 1 per dimension; max_level: the finest level
+ * (levels - 1, at most 7), with base_patches[d] << max_level below 2^20.
+ * refine_keys, candidate_keys: rows of 4 ints like keys. The resulting
+ * hierarchy is written to out_keys (cap_out rows of 4 ints, canonical order);
+ * *n_out receives its size, n_created and n_deleted (may be NULL) the
+ * numbers of patches created and deleted. Caller-owned host arrays; nothing
+ * is kept. Returns AMR_ERR_ARG for invalid sizes, a NULL array with a
+ * positive count, or a key outside the level range or the domain;
+ * AMR_ERR_MESH if `keys` repeats a key or breaks R1, R2 or the tree
+ * structure; AMR_ERR_POOL if the result has more than cap_out rows (*n_out
+ * set, out_keys untouched). */
+int amr_mesh_close(int dim, const int base_patches[3], const int periodic[3], int max_level,
+                   int n, const int* keys, int n_refine, const int* refine_keys,
+                   int n_candidates, const int* candidate_keys,
+                   int cap_out, int* n_out, int* out_keys, int* n_created, int* n_deleted);
+
 /* Weights of the learned indicator of dimension dim (flat float32, order
  * W1 (64 x K), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), K = 5^d (d+2)). */
 int amr_set_mlp(amr_ctx* ctx, const float* weights, long n_weights);

@@ -69,6 +69,9 @@ SIGNATURES = [
     ('amr_set_state', C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
     ('amr_get_requests', C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.POINTER(C.c_int),
                                    C.c_void_p]),
+    ('amr_mesh_close', C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                 C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p,
+                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ('amr_checkpoint', C.c_int, [C.c_void_p, C.c_char_p]),
     ('amr_restore', C.c_int, [C.c_void_p, C.c_char_p]),
     ('amr_set_mlp', C.c_int, [C.c_void_p, C.c_void_p, C.c_long]),
@@ -338,6 +341,38 @@ class AMR:
                 cc = list(c) + [0] * (3 - self.dim)
                 out.append((l, tuple(cc)))
         return out
+
+
+# ---------------------------------------------------------------------------
+# host-only mesh planning
+# ---------------------------------------------------------------------------
+def _key_rows(keys):
+    a = np.ascontiguousarray(np.asarray(keys, dtype=np.int32).reshape(-1, 4))
+    return a, a.shape[0]
+
+
+def mesh_close(dim, base_patches, periodic, max_level, keys, refine=(), candidates=()):
+    """The mesh half of a regrid on the host (amr_mesh_close): Algorithm 1 on
+    the refinement requests, then the coarsening rule on the candidates.
+    keys, refine, candidates: rows (level, cx, cy, cz). Returns (hierarchy as
+    an (n, 4) int32 array in canonical order, patches created, deleted)."""
+    lib = load()
+    bp = np.array([int(base_patches[d]) if d < len(base_patches) else 1 for d in range(3)], dtype=np.int32)
+    per = np.array([1 if d < len(periodic) and periodic[d] else 0 for d in range(3)], dtype=np.int32)
+    k, n = _key_rows(keys)
+    r, nr = _key_rows(refine)
+    cnd, nc = _key_rows(candidates)
+    n_out, n_cr, n_del = C.c_int(0), C.c_int(0), C.c_int(0)
+    cap = max(n, 1) * 2
+    while True:
+        out = np.zeros((cap, 4), dtype=np.int32)
+        rc = lib.amr_mesh_close(dim, _ptr(bp), _ptr(per), max_level, n, _ptr(k), nr, _ptr(r), nc, _ptr(cnd), cap,
+                                C.byref(n_out), _ptr(out), C.byref(n_cr), C.byref(n_del))
+        if rc == -2 and n_out.value > cap:                  # AMR_ERR_POOL: room for the result
+            cap = n_out.value
+            continue
+        _check_free(rc, 'amr_mesh_close')
+        return out[:n_out.value], n_cr.value, n_del.value
 
 
 # ---------------------------------------------------------------------------

@@ -1,6 +1,8 @@
 // Host-side patch hierarchy: Algorithm 1 and the coarsening rule of Sec. 4.3.
 #include "amr_mesh.h"
 
+#include "amr.h"
+
 #include <algorithm>
 #include <sstream>
 
@@ -173,3 +175,69 @@ std::vector<Key> Mesh::coarsen(const std::vector<Key>& candidates, const std::un
 }
 
 }  // namespace amr
+
+// ---------------------------------------------------------------------------
+// amr_mesh_close: the host half of a regrid on a caller's hierarchy.
+// ---------------------------------------------------------------------------
+namespace {
+
+// a (level, cx, cy, cz) row inside the level range and the domain (not wrapped)
+bool key_of_row(const amr::Mesh& m, const int* r, amr::Key& k) {
+    k = amr::Key{r[0], r[1], r[2], r[3]};
+    if (k.l < 0 || k.l > m.max_level) return false;
+    const int c[3] = {k.x, k.y, k.z};
+    for (int d = 0; d < 3; ++d)
+        if (c[d] < 0 || c[d] >= m.extent(k.l, d)) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" int amr_mesh_close(int dim, const int base_patches[3], const int periodic[3], int max_level, int n,
+                              const int* keys, int n_refine, const int* refine_keys, int n_candidates,
+                              const int* candidate_keys, int cap_out, int* n_out, int* out_keys, int* n_created,
+                              int* n_deleted) {
+    using amr::Key;
+    if (dim < 1 || dim > 3 || !base_patches || !periodic || max_level < 0 || max_level > 7 || n < 0 ||
+        n_refine < 0 || n_candidates < 0 || cap_out < 0 || !n_out)
+        return AMR_ERR_ARG;
+    if ((n > 0 && !keys) || (n_refine > 0 && !refine_keys) || (n_candidates > 0 && !candidate_keys) ||
+        (cap_out > 0 && !out_keys))
+        return AMR_ERR_ARG;
+    int base[3] = {1, 1, 1};
+    bool per[3] = {false, false, false};
+    for (int d = 0; d < dim; ++d) {
+        if (base_patches[d] < 1 || ((long long)base_patches[d] << max_level) >= (1LL << 20)) return AMR_ERR_ARG;
+        base[d] = base_patches[d];
+        per[d] = periodic[d] != 0;
+    }
+    amr::Mesh m(dim, base, per, max_level);
+    m.patches.clear();
+    for (int i = 0; i < n; ++i) {
+        Key k;
+        if (!key_of_row(m, keys + 4 * (size_t)i, k)) return AMR_ERR_ARG;
+        if (!m.patches.insert(amr::pack(k)).second) return AMR_ERR_MESH;
+    }
+    if (!m.check().empty()) return AMR_ERR_MESH;
+    std::vector<Key> req(n_refine), cand(n_candidates);
+    for (int i = 0; i < n_refine; ++i)
+        if (!key_of_row(m, refine_keys + 4 * (size_t)i, req[i])) return AMR_ERR_ARG;
+    for (int i = 0; i < n_candidates; ++i)
+        if (!key_of_row(m, candidate_keys + 4 * (size_t)i, cand[i])) return AMR_ERR_ARG;
+    const std::vector<Key> created = m.refine(req);
+    std::unordered_set<uint64_t> just;
+    for (const auto& k : created) just.insert(amr::pack(k));
+    const std::vector<Key> deleted = m.coarsen(cand, just);
+    *n_out = (int)m.patches.size();
+    if (n_created) *n_created = (int)created.size();
+    if (n_deleted) *n_deleted = (int)deleted.size();
+    if ((long long)m.patches.size() > cap_out) return AMR_ERR_POOL;
+    const std::vector<Key> all = m.canonical();
+    for (size_t i = 0; i < all.size(); ++i) {
+        out_keys[4 * i + 0] = all[i].l;
+        out_keys[4 * i + 1] = all[i].x;
+        out_keys[4 * i + 2] = all[i].y;
+        out_keys[4 * i + 3] = all[i].z;
+    }
+    return AMR_OK;
+}
