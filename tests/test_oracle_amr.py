@@ -232,3 +232,41 @@ def test_cfl_sums_over_dimensions_with_their_cell_sizes(dim):
     c = np.sqrt(1.4)
     lam = sum((abs(v) + c) * n for v, n in zip((0.3, -0.2, 0.1)[:dim], base[:dim]))
     assert o.cfl_dt() == pytest.approx(0.5 / lam, rel=1e-14)
+
+
+def test_four_quadrant_keeps_its_diagonal_symmetry_through_regrids():
+    # the four-quadrant states are symmetric under x <-> y (with u <-> v) and
+    # so are the outflow boundaries: flags, Algorithm 1 and the coarsening rule
+    # (both independent of the order of their inputs) give a symmetric mesh
+    # at every regrid, and the fields stay symmetric to round-off (the
+    # prolongation, the face corrections and the restriction visit x before y)
+    w = workload('riemann2d', base_cells=(32, 32, 1), patch=8, levels=3)
+    o = Oracle(w)
+    for _ in range(8):
+        o.step()
+        o.regrid()
+        assert {(l, (c[1], c[0], c[2])) for l, c in o.mesh.patches} == o.mesh.patches
+        F = [o.leaf_field(v)[0] for v in range(4)]
+        for a, b in ((0, 0), (3, 3), (1, 2)):
+            assert np.max(np.abs(F[a] - F[b].T)) <= 1e-13 * np.max(np.abs(F[a]))
+    assert 0 < len(o.mesh.level_list(2)) < 4 * 4 * 16          # partly refined
+
+
+def test_unperturbed_blast_keeps_the_cube_symmetries():
+    # the blast without its density perturbation is symmetric under every
+    # exchange of two axes (with the momentum components exchanged alike); on
+    # 3^3 base patches, partly refined, the mesh keeps every symmetry exactly
+    # and the fields to round-off
+    w = workload('blast3d', base_cells=(24, 24, 24), patch=8, levels=2, amp=0.0)
+    o = Oracle(w)
+    for _ in range(3):
+        o.step()
+        o.regrid()
+        for perm in ((1, 0, 2), (0, 2, 1), (2, 1, 0)):
+            assert {(l, tuple(c[perm[d]] for d in range(3))) for l, c in o.mesh.patches} == o.mesh.patches
+        F = [o.leaf_field(v) for v in range(5)]                  # axes (z, y, x)
+        for axes, (ma, mb) in (((0, 2, 1), (1, 2)), ((2, 1, 0), (1, 3)), ((1, 0, 2), (2, 3))):
+            for a in range(5):
+                b = mb if a == ma else (ma if a == mb else a)
+                assert np.max(np.abs(F[a] - np.transpose(F[b], axes))) <= 1e-13 * np.max(np.abs(F[a])), (axes, a)
+    assert 27 < len(o.mesh.patches) < 27 * 9
