@@ -655,3 +655,45 @@ def test_tangential_component_placement(flux):
         for d in range(dim):
             if d not in (axis, taxis):
                 assert not np.any(o.leaf_field(1 + d))
+
+
+def test_dmr_boundaries_follow_the_moving_shock():
+    # the shock of the double Mach reflection starts on x = 1/6 + y / sqrt(3)
+    # and runs along its normal (cos 30, -sin 30) at the speed W that mass
+    # conservation across it gives, rho1 W = rho2 (W - |u2|): on the top
+    # boundary y = 1 it sits at x = 1/6 + 1/sqrt(3) + W t / cos 30, with the
+    # post-shock state behind it and the pre-shock state ahead; the bottom
+    # takes the post-shock state left of the wedge tip x = 1/6 only
+    pre, post = dmr_states(1.4)
+    u2 = math.hypot(post[1], post[2])
+    W = post[0] * u2 / (post[0] - pre[0])
+    assert W == pytest.approx(10.0 * math.sqrt(1.4 * 1.0 / 1.4), rel=1e-13)       # Mach 10 into c = 1
+    o = Oracle(workload('dmr', base_cells=(64, 16, 1), patch=8, levels=1))
+
+    def state(kind, x, y, t):
+        X = [np.array([x]), np.array([y]), np.zeros(1)]
+        st, use = o._dirichlet(kind, X, t)
+        rho, u, p, _ = euler.primitives(st, 2, 1.4)
+        return bool(use[0]), (float(rho[0]), float(u[0][0]), float(u[1][0]), float(p[0]))
+
+    for t in (0.0, 0.013, 0.1, 0.2):
+        xs = 1.0 / 6.0 + 1.0 / math.sqrt(3.0) + W * t / math.cos(math.pi / 6.0)
+        for dx, want in ((-1e-9, post), (1e-9, pre)):
+            use, st = state('dmr_top', xs + dx, 1.0, t)
+            assert use and st == pytest.approx(want, rel=1e-12, abs=1e-12), (t, dx)
+        use, st = state('dmr_inflow', 0.0, 0.5, t)
+        assert use and st == pytest.approx(post, rel=1e-12, abs=1e-12)
+    for x, want in ((1.0 / 6.0 - 1e-9, True), (1.0 / 6.0 + 1e-9, False)):
+        use, st = state('dmr_bottom', x, 0.0, 0.1)
+        assert use == want
+        if use:
+            assert st == pytest.approx(post, rel=1e-12, abs=1e-12)
+    # the initial condition: post-shock exactly left of the shock line
+    c, x = o.get_level(0)
+    N = o.N
+    for i in range(len(c)):
+        for jy in range(N):
+            for jx in range(N):
+                X = (c[i][0] * N + jx + 0.5) * o.dx[0][0]
+                Y = (c[i][1] * N + jy + 0.5) * o.dx[0][1]
+                assert x[i, 0, jy, jx] == (post[0] if X < 1.0 / 6.0 + Y / math.sqrt(3.0) else pre[0])
