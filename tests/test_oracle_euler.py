@@ -697,3 +697,37 @@ def test_dmr_boundaries_follow_the_moving_shock():
                 X = (c[i][0] * N + jx + 0.5) * o.dx[0][0]
                 Y = (c[i][1] * N + jy + 0.5) * o.dx[0][1]
                 assert x[i, 0, jy, jx] == (post[0] if X < 1.0 / 6.0 + Y / math.sqrt(3.0) else pre[0])
+
+
+def ic_state(name, x, y=0.5):
+    from oracle.amr import initial_primitive
+    w = workload(name)
+    X = [np.array([[[x]]]), np.array([[[y]]]), np.array([[[0.5]]])]
+    Gi = [np.zeros((1, 1, 1), dtype=np.int64)] * 3
+    rho, u, p = initial_primitive(w, X, Gi, 0)
+    return float(rho.ravel()[0]), [float(v.ravel()[0]) for v in u], float(p.ravel()[0])
+
+
+def test_shock_states_of_the_initial_conditions():
+    # Shu-Osher: the state left of x = -4 is the post-shock state of a Mach-3
+    # shock running into (rho, u, p) = (1, 0, 1) (normal-shock relations), to
+    # the printed digits; right of it the density wave 1 + 0.2 sin(5 x)
+    g, M = 1.4, 3.0
+    r2 = (g + 1.0) * M * M / ((g - 1.0) * M * M + 2.0)
+    p2 = (2.0 * g * M * M - (g - 1.0)) / (g + 1.0)
+    u2 = M * math.sqrt(g) * (1.0 - 1.0 / r2)
+    rho, u, p = ic_state('shu_osher', -4.5)
+    assert (rho, u[0], p) == pytest.approx((r2, u2, p2), rel=1e-6)
+    rho, u, p = ic_state('shu_osher', 1.3)
+    assert (rho, u[0], p) == (1.0 + 0.2 * math.sin(6.5), 0.0, 1.0)
+    # four-quadrant problem: each pair of adjacent quadrants is joined by a
+    # shock, so across each interface the tangential velocity is continuous and
+    # the states lie on each other's Hugoniot curve,
+    # (du_n)^2 = (p_a - p_b) (1/rho_b - 1/rho_a), to the printed digits
+    Q = {q: ic_state('riemann2d', 0.25 + 0.5 * q[0], 0.25 + 0.5 * q[1]) for q in ((0, 0), (1, 0), (0, 1), (1, 1))}
+    for a, b, d in (((1, 1), (0, 1), 0), ((1, 0), (0, 0), 0), ((1, 1), (1, 0), 1), ((0, 1), (0, 0), 1)):
+        (ra, ua, pa), (rb, ub, pb) = Q[a], Q[b]
+        assert ua[1 - d] == ub[1 - d]
+        lhs = (ua[d] - ub[d]) ** 2
+        rhs = (pa - pb) * (1.0 / rb - 1.0 / ra)
+        assert lhs > 0.1 and rhs == pytest.approx(lhs, rel=2e-3), (a, b)
