@@ -731,3 +731,16 @@ def test_shock_states_of_the_initial_conditions():
         lhs = (ua[d] - ub[d]) ** 2
         rhs = (pa - pb) * (1.0 / rb - 1.0 / ra)
         assert lhs > 0.1 and rhs == pytest.approx(lhs, rel=2e-3), (a, b)
+
+
+def test_implosion_matches_the_printed_setup():
+    g = json.load(open(os.path.join(GOLD, 'implosion_ic.json')))
+    w = workload('implosion')
+    assert [[w['lo'][d], w['hi'][d]] for d in range(2)] == g['domain']
+    assert [w['base_cells'][d] * 2 ** (w['levels'] - 1) for d in range(2)] == g['mesh']
+    assert w['cfl'] == g['cfl'] and w['bc'][0] == w['bc'][1] == ('periodic', 'periodic')
+    for x, y, side in ((0.0, 0.0, 'inside'), (0.07, -0.0799, 'inside'), (-0.1, 0.0501, 'outside'),
+                       (0.29, 0.29, 'outside'), (0.0, -0.149, 'inside'), (0.151, 0.0, 'outside')):
+        rho, u, p = ic_state('implosion', x, y)
+        assert (rho, p) == (g[side]['rho'], g[side]['p']), (x, y)
+        assert u == [g['velocity']] * 2
