@@ -710,6 +710,10 @@ int set_state_impl(amr_ctx* c, int n, const int* levels, const int* coords, cons
         Key k{levels[i], coords[i * c->dim], c->dim >= 2 ? coords[i * c->dim + 1] : 0,
               c->dim == 3 ? coords[i * c->dim + 2] : 0};
         if (k.l < 0 || k.l >= c->L) return fail(c, AMR_ERR_MESH, "level out of range");
+        for (int d = 0; d < c->dim; ++d) {                  // before packing: keys hold 20-bit coordinates
+            const int x = coords[i * c->dim + d];
+            if (x < 0 || x >= m2.extent(k.l, d)) return fail(c, AMR_ERR_MESH, "patch outside the domain");
+        }
         if (!m2.patches.insert(pack(k)).second) return fail(c, AMR_ERR_MESH, "duplicate patch");
         keys.push_back(k);
     }

@@ -290,6 +290,16 @@ def test_invalid_arguments_rejected():
         g.set_state(np.array([0] * 16 + [1]), np.array([[i % 4, i // 4] for i in range(16)] + [[0, 0]]),
                     np.ones((17, 4, 8, 8)))
     assert 'MESH' in str(e.value)
+    # a coordinate outside the domain, negative or beyond the 20-bit key field
+    before = g.get_level(0)
+    for bad in ([-1, 0], [4, 0], [0, 1 << 20]):
+        coords = np.array([[i % 4, i // 4] for i in range(16)])
+        coords[5] = bad
+        with pytest.raises(AMRError) as e:
+            g.set_state(np.zeros(16, dtype=np.int64), coords, np.ones((16, 4, 8, 8)))
+        assert 'MESH' in str(e.value), bad
+    after = g.get_level(0)
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
     g.close()
 
 
