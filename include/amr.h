@@ -148,7 +148,12 @@ void amr_default_options(amr_options_t* opt);
  * ic_id; then levels-1 rounds of flag -> regrid with the initial condition
  * re-sampled on new patches. ratio must be 2 (child[4] in Sec. 4.2);
  * base_cells[d] must be multiples of patch_size, patch_size in {8, 16, 32}
- * (3D: {8, 16}); levels in [1, 8]. gamma > 1. *out receives the context. */
+ * (3D: {8, 16}); levels in [1, 8]; (base_cells[d] / patch_size) << (levels - 1)
+ * below 2^20; with max_patches <= 0, every level fully refined at most
+ * 2^31 - 1 patches. gamma > 1. *out receives the context (also on failure,
+ * for amr_last_error; destroy it). Invalid arguments give AMR_ERR_ARG before
+ * any CUDA call; without a usable CUDA device the call returns AMR_ERR_CUDA
+ * (there is no CPU fallback). */
 int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int base_cells[3],
              int levels, int ratio, int patch_size, int ic_id, const amr_options_t* opt);
 

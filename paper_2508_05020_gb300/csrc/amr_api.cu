@@ -942,6 +942,10 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     if (!(c->opt.cfl > 0.0)) return bad("cfl must be positive");
     if (c->opt.flagger != AMR_FLAG_PLAIN && c->opt.flagger != AMR_FLAG_MLP) return bad("unknown flagger");
     if (c->opt.mode != AMR_MODE_BATCHED && c->opt.mode != AMR_MODE_PER_PATCH) return bad("unknown mode");
+    if (c->opt.flux != AMR_FLUX_RUSANOV && c->opt.flux != AMR_FLUX_HLLC && c->opt.flux != AMR_FLUX_CENTRAL)
+        return bad("unknown flux");
+    if (!(c->opt.mlp_keep_margin >= 0.0) || !(c->opt.mlp_keep_margin < 1.0e30))
+        return bad("mlp_keep_margin must be in [0, 1e30)");
     int bp[3] = {1, 1, 1};
     bool periodic[3] = {false, false, false};
     for (int d = 0; d < dim; ++d) {
@@ -953,6 +957,8 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
         if (dom->bc_lo[d] >= AMR_BC_DMR_INFLOW || dom->bc_hi[d] >= AMR_BC_DMR_INFLOW)
             if (dim != 2) return bad("double-Mach boundaries are 2D only");
         bp[d] = base_cells[d] / patch_size;
+        if (((long long)bp[d] << (levels - 1)) >= (1LL << 20))       // keys hold 20-bit patch coordinates
+            return bad("more than 2^20 - 1 patches along a dimension of the finest level");
         periodic[d] = dom->bc_lo[d] == AMR_BC_PERIODIC;
     }
     c->dim = dim;
@@ -966,15 +972,18 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     c->use_graph = c->opt.use_graph;
     c->flagger = c->opt.flagger;
     for (int d = 0; d < 3; ++d) c->base_cells[d] = d < dim ? base_cells[d] : 1;
-    c->mesh = Mesh(dim, bp, periodic, levels - 1);
+    // pool capacity, checked before the level-0 layout is built
     long long full = 0;
     for (int l = 0; l < levels; ++l) {
         long long n = 1;
         for (int d = 0; d < dim; ++d) n *= (long long)bp[d] << l;
         full += n;
     }
+    if (c->opt.max_patches <= 0 && full > 0x7fffffffLL)
+        return bad("every level fully refined exceeds 2^31 - 1 patches: set max_patches");
     c->cap = c->opt.max_patches > 0 ? (int)std::min<long long>(c->opt.max_patches, full) : (int)full;
-    if ((long long)c->mesh.patches.size() > c->cap) return bad("pool smaller than the base level");
+    if ((long long)bp[0] * bp[1] * bp[2] > c->cap) return bad("pool smaller than the base level");
+    c->mesh = Mesh(dim, bp, periodic, levels - 1);
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -1025,10 +1034,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.theta_rho = c->opt.theta_rho;
     g.theta_p = c->opt.theta_p;
     g.ic = ic_id;
-    if (c->opt.flux != AMR_FLUX_RUSANOV && c->opt.flux != AMR_FLUX_HLLC && c->opt.flux != AMR_FLUX_CENTRAL)
-        return bad("unknown flux");
     g.flux = c->opt.flux;
-    if (!(c->opt.mlp_keep_margin >= 0.0) || !(c->opt.mlp_keep_margin < 1.0e30)) return bad("mlp_keep_margin");
     g.mlp_keep = (float)c->opt.mlp_keep_margin;
     g.seed = c->opt.seed;
     g.amp = c->opt.amp;
