@@ -2,6 +2,7 @@
 // step sequence (batched persistent kernels in a CUDA graph, or one launch per
 // patch per operation) and regrid.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -20,6 +21,15 @@
 #include "amr_mesh.h"
 
 using namespace amr;
+
+// NVTX range over a scope: the host side of an entry point or a regrid phase,
+// shown on the timeline of a profiler that records NVTX (no effect otherwise)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 struct amr_ctx {
     // configuration
@@ -605,10 +615,14 @@ int regrid_finish(amr_ctx* c, bool resample_ic, bool* void_step, bool* changed) 
     c->regrid_ms[1] = c->regrid_ms[2] = 0.0;
     if (req.empty() && cand.empty()) return AMR_OK;
     Mesh m2 = c->mesh;
-    std::vector<Key> created = m2.refine(req);
-    std::unordered_set<uint64_t> just;
-    for (const auto& k : created) just.insert(pack(k));
-    std::vector<Key> deleted = m2.coarsen(cand, just);
+    std::vector<Key> created, deleted;
+    {
+        Range closure("regrid: closure and coarsening");
+        created = m2.refine(req);
+        std::unordered_set<uint64_t> just;
+        for (const auto& k : created) just.insert(pack(k));
+        deleted = m2.coarsen(cand, just);
+    }
     if (created.empty() && deleted.empty())                // the same candidates give the same answer
         return set_rejected(c, req.empty() ? (int)cand.size() : -1);
     if ((long long)m2.patches.size() > c->cap)
@@ -617,6 +631,7 @@ int regrid_finish(amr_ctx* c, bool resample_ic, bool* void_step, bool* changed) 
     if (changed) *changed = true;
     r = set_rejected(c, -1);
     if (r) return r;
+    Range tables("regrid: tables and new patches");
     c->mesh.patches.swap(m2.patches);
     assign_slots(c, created, deleted);
     const auto t2 = std::chrono::steady_clock::now();
@@ -1185,18 +1200,21 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
 
 int amr_step(amr_ctx* c, double dt, double* dt_used) {
     GUARD(c);
+    Range range("amr_step");
     if (std::isnan(dt)) return fail(c, AMR_ERR_ARG, "dt is NaN");
     return c->precision == 64 ? step_impl<double>(c, dt, dt_used) : step_impl<float>(c, dt, dt_used);
 }
 
 int amr_regrid(amr_ctx* c) {
     GUARD(c);
+    Range range("amr_regrid");
     if (c->L == 1) return AMR_OK;
     return c->precision == 64 ? regrid_impl<double>(c, false) : regrid_impl<float>(c, false);
 }
 
 int amr_advance(amr_ctx* c, int n_steps, int regrid) {
     GUARD(c);
+    Range range("amr_advance");
     if (n_steps < 0) return fail(c, AMR_ERR_ARG, "negative step count");
     if (regrid && c->L > 1 && c->mode == AMR_MODE_BATCHED)
         return c->precision == 64 ? advance_impl<double>(c, n_steps) : advance_impl<float>(c, n_steps);
