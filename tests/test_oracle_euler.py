@@ -639,7 +639,7 @@ def test_tangential_component_placement(flux):
     # (the unused component stays zero and adds nothing to the kinetic
     # energy). A tangential flux written to the wrong momentum component, or
     # a normal and a tangential swapped, breaks it
-    n, steps = 64, 15
+    n, steps = 32, 12
     ref = tube_with_shear(2, 0, 1, n, flux)
     dts = [ref.step() for _ in range(steps)]
     expect = [ref.leaf_field(v)[0, 0] for v in range(4)]         # rho, m_n, m_t, E along the tube
