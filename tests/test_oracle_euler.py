@@ -744,3 +744,35 @@ def test_implosion_matches_the_printed_setup():
         rho, u, p = ic_state('implosion', x, y)
         assert (rho, p) == (g[side]['rho'], g[side]['p']), (x, y)
         assert u == [g['velocity']] * 2
+
+
+def test_blast_initial_state():
+    # p = 100 inside r < 0.1 about the box centre and 0.1 outside, fluid at
+    # rest; the density perturbation 1 + 0.01 (2 xi - 1) is keyed to the
+    # base-level cell containing the point, so every level sees the same
+    # value there, and xi is SplitMix64 (seed 0) of that cell's linear index
+    from oracle.amr import initial_primitive
+    w = workload('blast3d')
+    nb = w['base_cells']
+
+    def at(x, y, z, level):
+        X = [np.array([[[x]]]), np.array([[[y]]]), np.array([[[z]]])]
+        Gi = [np.array([[[int(c * nb[d] * 2 ** level)]]]) for d, c in enumerate((x, y, z))]
+        rho, u, p = initial_primitive(w, X, Gi, level)
+        return float(rho.ravel()[0]), [float(v.ravel()[0]) for v in u], float(p.ravel()[0])
+
+    for r, want in ((0.0999, 100.0), (0.1001, 0.1)):
+        for d in range(3):
+            pt = [0.5, 0.5, 0.5]
+            pt[d] += r
+            assert at(*pt, 0)[2] == want
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        pt = rng.uniform(0.0, 1.0, 3)
+        r0, u0, _ = at(*pt, 0)
+        assert u0 == [0.0, 0.0, 0.0]
+        ib = [int(pt[d] * nb[d]) for d in range(3)]
+        xi = splitmix64(0, np.array([(ib[2] * nb[1] + ib[1]) * nb[0] + ib[0]]))[0]
+        assert r0 == 1.0 + 0.01 * (2.0 * xi - 1.0)
+        for level in (1, 2):
+            assert at(*pt, level)[0] == r0
