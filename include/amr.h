@@ -241,6 +241,36 @@ int amr_mesh_close(int dim, const int base_patches[3], const int periodic[3], in
                    int n_candidates, const int* candidate_keys,
                    int cap_out, int* n_out, int* out_keys, int* n_created, int* n_deleted);
 
+/* The metadata tables the kernels read (Sec. 4.2: a patch's level,
+ * coordinates, neighbours, parent and children), built for a caller's
+ * hierarchy on the host alone (no context, no GPU), for inspection and
+ * testing. keys: n >= 1 rows of (level, cx, cy, cz) forming a valid hierarchy
+ * (as for amr_mesh_close); the patch of canonical index s gets slot s. The
+ * tables are n_ints ints, in this order (cap = n):
+ *   level[cap], coord[3 cap] (x, y, z per slot),
+ *   nbr[27 cap] (entry (oz+1) 9 + (oy+1) 3 + (ox+1): the slot of the
+ *     same-level patch at that offset, wrapped across periodic sides; -1 if
+ *     absent, -2 outside the domain; the centre entry is the patch itself),
+ *   parent[cap] (-1 on level 0), child[8 cap] (the children in (z, y, x)
+ *     order, x fastest; -1 for a leaf and beyond 2^d),
+ *   pflag[cap] (bit 0: has children; bit 8 + 2 d + side, side 0 low / 1
+ *     high: the face takes part in a coarse-fine correction, i.e. a leaf whose
+ *     neighbour across it has children, or a patch above level 0 with no
+ *     same-level neighbour across it inside the domain),
+ *   all_list[cap] (slots in canonical order), level_off[9] (start of each
+ *     level in all_list; the total for levels beyond the last),
+ *   leaf_list[cap] (leaf slots, canonical order), counts[4] (patches,
+ *     leaves, correction items, new patches = 0),
+ *   reflux_list[cap] (leaves with a face next to a patch with children,
+ *     canonical order), reflux_fine[24 cap] (per correction item and face
+ *     2 d + side, the slots of the 2^(d-1) finer patches across it in (z, y, x)
+ *     order; -1 elsewhere), new_list[cap].
+ * Entries past the counts are unspecified. *n_ints receives the size;
+ * tables may be NULL (size only). Returns AMR_ERR_ARG or AMR_ERR_MESH as
+ * amr_mesh_close does. */
+int amr_mesh_tables(int dim, const int base_patches[3], const int periodic[3], int max_level,
+                    int n, const int* keys, int* tables, long long* n_ints);
+
 /* Weights of the learned indicator of dimension dim (flat float32, order
  * W1 (64 x K), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), K = 5^d (d+2)). */
 int amr_set_mlp(amr_ctx* ctx, const float* weights, long n_weights);

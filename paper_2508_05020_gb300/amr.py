@@ -72,6 +72,8 @@ SIGNATURES = [
     ('amr_mesh_close', C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                  C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p,
                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ('amr_mesh_tables', C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                  C.POINTER(C.c_longlong)]),
     ('amr_checkpoint', C.c_int, [C.c_void_p, C.c_char_p]),
     ('amr_restore', C.c_int, [C.c_void_p, C.c_char_p]),
     ('amr_set_mlp', C.c_int, [C.c_void_p, C.c_void_p, C.c_long]),
@@ -373,6 +375,30 @@ def mesh_close(dim, base_patches, periodic, max_level, keys, refine=(), candidat
             continue
         _check_free(rc, 'amr_mesh_close')
         return out[:n_out.value], n_cr.value, n_del.value
+
+
+def mesh_tables(dim, base_patches, periodic, max_level, keys):
+    """The metadata tables of a hierarchy (amr_mesh_tables; slot = canonical
+    index), split into a dict of named int32 arrays by the layout of
+    include/amr.h."""
+    lib = load()
+    bp = np.array([int(base_patches[d]) if d < len(base_patches) else 1 for d in range(3)], dtype=np.int32)
+    per = np.array([1 if d < len(periodic) and periodic[d] else 0 for d in range(3)], dtype=np.int32)
+    k, n = _key_rows(keys)
+    size = C.c_longlong(0)
+    _check_free(lib.amr_mesh_tables(dim, _ptr(bp), _ptr(per), max_level, n, _ptr(k), None, C.byref(size)),
+                'amr_mesh_tables')
+    out = np.zeros(size.value, dtype=np.int32)
+    _check_free(lib.amr_mesh_tables(dim, _ptr(bp), _ptr(per), max_level, n, _ptr(k), _ptr(out), C.byref(size)),
+                'amr_mesh_tables')
+    parts, o = {}, 0
+    for name, width in (('level', n), ('coord', 3 * n), ('nbr', 27 * n), ('parent', n), ('child', 8 * n),
+                        ('pflag', n), ('all_list', n), ('level_off', 9), ('leaf_list', n), ('counts', 4),
+                        ('reflux_list', n), ('reflux_fine', 24 * n), ('new_list', n)):
+        parts[name] = out[o:o + width]
+        o += width
+    assert o == out.size
+    return parts
 
 
 # ---------------------------------------------------------------------------

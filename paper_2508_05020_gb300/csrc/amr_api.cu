@@ -186,8 +186,9 @@ int slot_lookup(const amr_ctx* c, const Key& k) {
     return it == c->slot_of.end() ? -1 : it->second;
 }
 
-// Rebuild every metadata table and work list from the host mesh and upload them.
-int rebuild_tables(amr_ctx* c, const std::vector<Key>& created) {
+// Every metadata table and work list of the host mirror (meta_h and the host
+// lists) from the host mesh and slot map; host work only.
+void fill_tables(amr_ctx* c, const std::vector<Key>& created) {
     const MetaLayout ml(c->cap);
     int* h = c->meta_h;
     const Mesh& m = c->mesh;
@@ -231,9 +232,10 @@ int rebuild_tables(amr_ctx* c, const std::vector<Key>& created) {
         // neighbour keeps its face flux for the coarse side
         bool any_ref = false;
         int fine[6][4];
+        for (int f = 0; f < 6; ++f)
+            for (int j = 0; j < 4; ++j) fine[f][j] = -1;       // faces of unused dimensions stay -1 too
         for (int d = 0; d < c->dim; ++d)
             for (int side = 0; side < 2; ++side) {
-                for (int j = 0; j < 4; ++j) fine[2 * d + side][j] = -1;
                 Key q = k;
                 int* qc[3] = {&q.x, &q.y, &q.z};
                 *qc[d] += side ? 1 : -1;
@@ -286,6 +288,12 @@ int rebuild_tables(amr_ctx* c, const std::vector<Key>& created) {
     h[ml.counts + 1] = c->n_leaf;
     h[ml.counts + 2] = n_ref;
     h[ml.counts + 3] = (int)cr.size();
+}
+
+// Rebuild every metadata table and work list from the host mesh and upload them.
+int rebuild_tables(amr_ctx* c, const std::vector<Key>& created) {
+    fill_tables(c, created);
+    const MetaLayout ml(c->cap);
     const size_t bytes = ml.total * sizeof(int);
     CK(cudaMemcpyAsync(c->meta_d, c->meta_h, bytes, cudaMemcpyHostToDevice, c->stream), "upload tables");
     c->h2d += (long long)bytes;
@@ -1527,5 +1535,46 @@ void amr_destroy(amr_ctx* c) {
 }
 
 const char* amr_last_error(const amr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int amr_mesh_tables(int dim, const int base_patches[3], const int periodic[3], int max_level, int n,
+                    const int* keys, int* tables, long long* n_ints) {
+    if (dim < 1 || dim > 3 || !base_patches || !periodic || max_level < 0 || max_level >= MAXL || n < 1 ||
+        !keys || !n_ints)
+        return AMR_ERR_ARG;
+    int bp[3] = {1, 1, 1};
+    bool per[3] = {false, false, false};
+    for (int d = 0; d < dim; ++d) {
+        if (base_patches[d] < 1 || ((long long)base_patches[d] << max_level) >= (1LL << 20)) return AMR_ERR_ARG;
+        bp[d] = base_patches[d];
+        per[d] = periodic[d] != 0;
+    }
+    amr_ctx t;                                  // host fields only: no device memory, no stream
+    t.dim = dim;
+    t.L = max_level + 1;
+    t.cap = n;
+    t.mesh = Mesh(dim, bp, per, max_level);
+    t.mesh.patches.clear();
+    for (int i = 0; i < n; ++i) {
+        const int* r = keys + 4 * (size_t)i;
+        const Key k{r[0], r[1], r[2], r[3]};
+        if (k.l < 0 || k.l > max_level) return AMR_ERR_ARG;
+        const int cc[3] = {k.x, k.y, k.z};
+        for (int d = 0; d < 3; ++d)
+            if (cc[d] < 0 || cc[d] >= t.mesh.extent(k.l, d)) return AMR_ERR_ARG;
+        if (!t.mesh.patches.insert(pack(k)).second) return AMR_ERR_MESH;
+    }
+    if (!t.mesh.check().empty()) return AMR_ERR_MESH;
+    const MetaLayout ml(n);
+    *n_ints = (long long)ml.total;
+    if (!tables) return AMR_OK;
+    const std::vector<Key> all = t.mesh.canonical();
+    for (int i = 0; i < n; ++i) t.slot_of[pack(all[i])] = i;    // slot = canonical index
+    std::vector<int> h(ml.total, 0);
+    t.meta_h = h.data();
+    fill_tables(&t, {});
+    t.meta_h = nullptr;
+    std::copy(h.begin(), h.end(), tables);
+    return AMR_OK;
+}
 
 }  // extern "C"

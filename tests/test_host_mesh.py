@@ -141,3 +141,86 @@ def test_output_capacity_and_counts(lib):
                           C.byref(n_out), lib._ptr(out), None, None)
     assert rc == 0
     assert out.tolist() == keys_1d((0, 0), (0, 1), (0, 2), (0, 3), (1, 2), (1, 3))
+
+
+def expected_tables(m):
+    """The tables of include/amr.h for the oracle mesh m, slot = canonical
+    index, written from the definitions: neighbours by offset (wrapped
+    across periodic sides, -2 outside), parent, children, face flags and the
+    finer patches across each face of a leaf next to a refined patch."""
+    keys = sorted(m.patches, key=canon)
+    slot = {k: i for i, k in enumerate(keys)}
+    n, dim = len(keys), m.dim
+    nbr = np.full((n, 27), -9)
+    child = np.full((n, 8), -1)
+    parent = np.full(n, -1)
+    pflag = np.zeros(n, dtype=np.int64)
+    rl, rf = [], []
+    for s, k in enumerate(keys):
+        l, c = k
+        for oz in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for ox in (-1, 0, 1):
+                    o = (ox, oy, oz)
+                    e = (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)
+                    if any(o[d] != 0 for d in range(dim, 3)):
+                        nbr[s, e] = -2                                     # unused dimensions
+                        continue
+                    q = m.wrap(l, tuple(c[d] + o[d] for d in range(3)))
+                    nbr[s, e] = -2 if q is None else slot.get((l, q), -1)
+        if l > 0:
+            parent[s] = slot[Mesh.parent(k)]
+        if m.has_children(k):
+            pflag[s] |= 1
+            for j, x in enumerate(m.children(k)):
+                child[s, j] = slot[x]
+        faces = np.full((6, 4), -1)
+        item = False
+        for d in range(dim):
+            for side in (0, 1):
+                q = m.wrap(l, tuple(c[e] + ((1 if side else -1) if e == d else 0) for e in range(3)))
+                if q is None:
+                    continue
+                if m.is_leaf(k) and (l, q) in m.patches and m.has_children((l, q)):
+                    pflag[s] |= 1 << (8 + 2 * d + side)
+                    item = True
+                    # the children of q touching the shared face, in canonical order
+                    touch = [x for x in m.children((l, q)) if x[1][d] == 2 * q[d] + (0 if side else 1)]
+                    for j, x in enumerate(sorted(touch, key=canon)):
+                        faces[2 * d + side, j] = slot[x]
+                if l > 0 and (l, q) not in m.patches:
+                    pflag[s] |= 1 << (8 + 2 * d + side)
+        if item:
+            rl.append(s)
+            rf.append(faces)
+    leaves = [slot[k] for k in keys if m.is_leaf(k)]
+    off = [sum(1 for k in keys if k[0] < l) for l in range(9)]
+    return dict(level=[k[0] for k in keys], coord=[x for k in keys for x in k[1]], nbr=nbr, parent=parent,
+                child=child, pflag=pflag, all_list=list(range(n)), level_off=off, leaf_list=leaves,
+                counts=[n, len(leaves), len(rl), 0], reflux_list=rl, reflux_fine=rf)
+
+
+@pytest.mark.parametrize('dim,base,periodic,max_level', CASES)
+def test_metadata_tables_match_their_definitions(lib, dim, base, periodic, max_level):
+    rng = random.Random(29 * dim + max_level)
+    items = 0
+    for trial in range(15 if dim < 3 else 6):
+        m = random_mesh(rng, dim, base, periodic, max_level, rng.randint(0, 8))
+        keys = rows(m.patches)
+        rng.shuffle(keys)
+        t = lib.mesh_tables(dim, base, periodic, max_level, keys)
+        e = expected_tables(m)
+        n = len(m.patches)
+        for name in ('level', 'coord', 'parent', 'pflag', 'all_list', 'level_off', 'counts'):
+            assert t[name].tolist() == list(np.asarray(e[name]).tolist()), name
+        assert np.array_equal(t['nbr'].reshape(n, 27), e['nbr'])
+        assert np.array_equal(t['child'].reshape(n, 8), e['child'])
+        nl, nr = e['counts'][1], e['counts'][2]
+        assert t['leaf_list'][:nl].tolist() == e['leaf_list']
+        assert t['reflux_list'][:nr].tolist() == e['reflux_list']
+        fine = t['reflux_fine'].reshape(n, 6, 4)[:nr]
+        for i in range(nr):
+            assert np.array_equal(fine[i], e['reflux_fine'][i]), i
+        items += nr
+    if max_level > 0:
+        assert items > 0
