@@ -56,6 +56,10 @@ class _NpShim:
         return bool(x)
 
     @staticmethod
+    def logical_not(x):
+        return not x
+
+    @staticmethod
     def where(c, a, b):
         return a if c else b
 
