@@ -106,3 +106,18 @@ def test_plain_sensor_flags_a_planar_wave_like_its_profile(ti, dim):
             core = tuple([slice(None)] * (3 - dim) + [slice(2, 10)] * dim)
             sl = tuple(slice(key[1][d] * 8, key[1][d] * 8 + 8) for d in reversed(range(dim)))
             assert np.array_equal(f[core].reshape(k[sl].shape), flag1[k[sl]]), (n, key)
+
+
+def test_evaluation_weight_specs():
+    from paper_2508_05020_gb300 import eval_indicator as ev
+    specs = ev.parse_weights(['net=paper_2508_05020_gb300/weights/indicator_d{d}.npy',
+                              'lookahead=paper_2508_05020_gb300/weights/indicator_d{d}_k4.npy'])
+    assert [s[0] for s in specs] == ['net', 'lookahead']
+    for dim in (1, 2, 3):
+        for _, p in specs:
+            w = ev.load_weights(p, dim)
+            assert w is not None and w.dtype == np.float32 and w.size == 64 * mlp.k_in(dim) + 64 * 64 + 3 * 64 + 1
+    assert ev.load_weights('paper_2508_05020_gb300/weights/none_d{d}.npy', 1) is None
+    for bad in ('net', '=x_d{d}.npy', 'net=indicator.npy'):
+        with pytest.raises(ValueError):
+            ev.parse_weights([bad])
