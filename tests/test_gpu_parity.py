@@ -194,6 +194,32 @@ def test_requests_bit_exact_given_identical_state():
     g.close()
 
 
+@pytest.mark.parametrize('name,kw,precision', [
+    ('dmr', dict(base_cells=(64, 16, 1), patch=8, levels=3), 64),
+    ('blast3d', dict(base_cells=(24, 24, 24), patch=8, levels=2), 32),
+])
+def test_host_plan_predicts_the_regrid(name, kw, precision):
+    # amr_mesh_close, given the hierarchy and the requests the device found,
+    # gives the patch list amr_regrid then produces (both cases change their
+    # mesh at every step in the oracle)
+    from paper_2508_05020_gb300.amr import mesh_close
+    w = workload(name, **kw)
+    g = amr(w, precision=precision)
+    bp = [w['base_cells'][d] // w['patch'] for d in range(w['dim'])]
+    per = [w['bc'][d][0] == 'periodic' for d in range(w['dim'])]
+    changed = 0
+    for _ in range(4):
+        g.step()
+        keys = [[l] + list(c) for l, c in g.patch_keys()]
+        rq, cd = g.requests()
+        plan, n_created, n_deleted = mesh_close(w['dim'], bp, per, w['levels'] - 1, keys, rq, cd)
+        g.regrid()
+        assert plan.tolist() == [[l] + list(c) for l, c in g.patch_keys()]
+        changed += (n_created + n_deleted) > 0
+    assert changed > 0
+    g.close()
+
+
 def test_conservation_periodic_fp64():
     w = workload('implosion', base_cells=(64, 64, 1), patch=16, levels=3)
     g = amr(w)
