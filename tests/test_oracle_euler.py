@@ -776,3 +776,33 @@ def test_blast_initial_state():
         assert r0 == 1.0 + 0.01 * (2.0 * xi - 1.0)
         for level in (1, 2):
             assert at(*pt, level)[0] == r0
+
+
+@pytest.mark.parametrize('nt', [0, 2])
+def test_nonpositive_reconstruction_falls_back_to_first_order(nt):
+    # pencils with near-vacuum pressures and large velocity jumps: where the
+    # reconstructed p or T of either side is not positive the face takes the
+    # states of its two nodes, so its flux is Eqs. 11-12 of those two states;
+    # elsewhere the WENO states stay (the flux differs from that one)
+    rng = np.random.default_rng(0)
+    fell, kept = 0, 0
+    for _ in range(400):
+        p = np.exp(rng.uniform(-12.0, 1.0, 6))
+        T = np.exp(rng.uniform(-3.0, 1.0, 6))
+        un = rng.uniform(-3.0, 3.0, 6)
+        ut = rng.uniform(-1.0, 1.0, (6, nt))
+        P = [(p[k], un[k], list(ut[k]), T[k]) for k in range(6)]
+        z, kap = euler.frozen_state(p[2], T[2], p[3], T[3], 1.4)
+        W = [euler.char_forward(P[k], z, kap) for k in range(6)]
+        wl = [euler.weno5_left(*[W[k][f] for k in range(5)]) for f in range(nt + 3)]
+        wr = [euler.weno5_left(*[W[k][f] for k in (5, 4, 3, 2, 1)]) for f in range(nt + 3)]
+        pL, _, _, TL = euler.char_inverse(wl, z, kap)
+        pR, _, _, TR = euler.char_inverse(wr, z, kap)
+        F = euler.face_flux(P, nt + 1, 1.4)
+        first = rusanov_ref((p[2] / T[2], un[2], list(ut[2]), p[2]), (p[3] / T[3], un[3], list(ut[3]), p[3]), 1.4)
+        if not (pL > 0.0 and TL > 0.0 and pR > 0.0 and TR > 0.0):
+            assert np.allclose(F, first, rtol=1e-12, atol=1e-14)
+            fell += 1
+        elif not np.allclose(F, first, rtol=1e-6, atol=1e-9):
+            kept += 1
+    assert fell >= 20 and kept >= 20
