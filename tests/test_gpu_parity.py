@@ -220,6 +220,37 @@ def test_host_plan_predicts_the_regrid(name, kw, precision):
     g.close()
 
 
+@pytest.mark.parametrize('flux', ['rusanov', 'hllc'])
+def test_fp64_positivity_fallback_bitwise(flux):
+    # a periodic 1D state with pressures down to e^-6 and velocity jumps up to
+    # 6: 13 faces of its first stage reconstruct a non-positive p or T and take
+    # the first-order states of their two nodes; one step of 1/100 of the CFL
+    # step keeps every state positive. The GPU reproduces the oracle bit for bit
+    from oracle import euler
+    w = workload('sod', base_cells=(64, 1, 1), levels=1, flux=flux,
+                 bc=(('periodic', 'periodic'), ('outflow', 'outflow'), ('outflow', 'outflow')))
+    r = oracle(w)
+    rng = np.random.default_rng(5)
+    n = 64
+    p = np.exp(rng.uniform(-6.0, 1.0, n))
+    T = np.exp(rng.uniform(-3.0, 1.0, n))
+    u = rng.uniform(-3.0, 3.0, n)
+    U = np.stack(euler.conserved_from_primitive(p / T, [u], p, 1.4))
+    keys = r.mesh.canonical()
+    for k in keys:
+        c = k[1][0]
+        r.U[k][r.inner()] = U[:, c * 16:(c + 1) * 16].reshape(r.U[k][r.inner()].shape)
+    g = amr(w)
+    g.set_state(np.zeros(len(keys), dtype=np.int64), np.array([[k[1][0]] for k in keys]),
+                np.stack([r.U[k][r.inner()].reshape((3, 16)) for k in keys]), t=0.0)
+    compare(g, r, tol=0.0)
+    dt = 0.01 * r.cfl_dt()
+    r.step(dt)
+    g.step(dt=dt)
+    compare(g, r, tol=0.0)
+    g.close()
+
+
 def test_conservation_periodic_fp64():
     w = workload('implosion', base_cells=(64, 64, 1), patch=16, levels=3)
     g = amr(w)
