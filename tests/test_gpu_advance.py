@@ -39,26 +39,3 @@ def test_advance_equals_step_regrid(name, base, precision):
     a.close()
     b.close()
 
-
-def test_two_runs_are_bitwise_identical():
-    # the launch configuration the bench times (FP32, learned flags with the
-    # keep margin, autotuned grids, amr_advance in a CUDA graph) run twice
-    # from the same start: identical hierarchies and values, bit for bit.
-    # The persistent flag kernel takes its work items from a global counter
-    # and the grid-stride kernels take tuned grids, so a race between blocks
-    # or an order-dependent reduction would show here
-    import os
-    from paper_2508_05020_gb300.amr import AMR
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    wf = np.load(os.path.join(root, 'paper_2508_05020_gb300', 'weights', 'indicator_d3.npy')).astype(np.float32)
-    w = workload('blast3d', base_cells=(32, 32, 32), patch=16, levels=3)
-    runs = []
-    for _ in range(2):
-        g = AMR(w, precision=32, flagger='mlp', mlp_weights=wf, autotune=True, mlp_keep_margin=12.0)
-        g.advance(4)
-        runs.append((g.diag()[0], [g.get_level(l) for l in range(w['levels'])]))
-        g.close()
-    (ta, la), (tb, lb) = runs
-    assert ta == tb
-    for (ca, xa), (cb, xb) in zip(la, lb):
-        assert np.array_equal(ca, cb) and np.array_equal(xa, xb)
