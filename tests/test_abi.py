@@ -50,3 +50,42 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(amr, 'LIB_PATH', str(tmp_path / 'nope.so'))
     with pytest.raises(ImportError):
         amr.load()
+
+
+C_PROGRAM = r'''
+#include "amr.h"
+#include <stdio.h>
+int main(void) {
+    amr_options_t o;
+    int base[3] = {4, 4, 1}, per[3] = {0, 0, 0}, keys[16 * 4], out[64 * 4], n_out = 0, i, rc;
+    int req[4] = {0, 1, 1, 0};
+    amr_default_options(&o);
+    for (i = 0; i < 16; ++i) {
+        keys[4 * i] = 0; keys[4 * i + 1] = i % 4; keys[4 * i + 2] = i / 4; keys[4 * i + 3] = 0;
+    }
+    rc = amr_mesh_close(2, base, per, 2, 16, keys, 1, req, 0, NULL, 64, &n_out, out, NULL, NULL);
+    printf("%d %d %d %.2f\n", rc, n_out, o.precision, o.cfl);
+    return rc;
+}
+'''
+
+
+def test_header_is_plain_c_and_links(libpath, tmp_path):
+    # include/amr.h compiles as strict C99 and a C program links against the
+    # library and calls it (host-only entry points: no GPU needed)
+    import shutil
+    if not shutil.which('gcc'):
+        pytest.skip('no C compiler')
+    src = tmp_path / 't.c'
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / 't'
+    libdir = os.path.dirname(libpath)
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(shutil.which('nvcc') or
+                                                                              '/usr/local/cuda/bin/nvcc'))), 'lib64')
+    r = subprocess.run(['gcc', '-std=c99', '-Wall', '-Wextra', '-pedantic', '-Werror', '-I', os.path.join(ROOT, 'include'),
+                        str(src), '-L', libdir, '-lamr', '-Wl,-rpath,' + libdir, '-Wl,-rpath-link,' + cuda_lib,
+                        '-o', str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ, LD_LIBRARY_PATH=cuda_lib + os.pathsep + os.environ.get('LD_LIBRARY_PATH', ''))
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env)
+    assert r.returncode == 0 and r.stdout.split() == ['0', '20', '64', '0.50'], (r.stdout, r.stderr)
