@@ -270,3 +270,23 @@ def test_unperturbed_blast_keeps_the_cube_symmetries():
                 b = mb if a == ma else (ma if a == mb else a)
                 assert np.max(np.abs(F[a] - np.transpose(F[b], axes))) <= 1e-13 * np.max(np.abs(F[a])), (axes, a)
     assert 27 < len(o.mesh.patches) < 27 * 9
+
+
+def test_stage_times_of_ssp_rk3(monkeypatch):
+    # the Shu-Osher stages evaluate the right-hand side at t, t + dt and
+    # t + dt/2 (the abscissae of SSP-RK3), so time-dependent boundaries are
+    # filled at those times: the ghost fills of one step see exactly them
+    o = Oracle(workload('dmr', base_cells=(32, 8, 1), patch=8, levels=1))
+    o.t = 0.0125
+    seen = []
+    real = Oracle.fill_ghosts
+
+    def spy(self, U, t):
+        seen.append(t)
+        return real(self, U, t)
+
+    monkeypatch.setattr(Oracle, 'fill_ghosts', spy)
+    dt = 1e-3
+    o.step(dt)
+    assert seen == [0.0125, 0.0125 + dt, 0.0125 + 0.5 * dt]
+    assert o.t == 0.0125 + dt
