@@ -454,7 +454,7 @@ class Oracle:
         faces = {}
         for k in keys:
             R, faces[k] = euler.patch_rhs(src[k], self.dim, self.N, G, self.dx[k[0]], self.gamma,
-                                          self.w.get('flux', 'rusanov'))
+                                          self.w.get('flux', 'rusanov'), self.w.get('theta_switch', 0.05))
             Us = src[k][inner]
             if s == 0:
                 new = Us + dt * R

@@ -247,6 +247,39 @@ def central_face_flux(P, dim, gamma):
     return [mn, mn * un + p] + [mn * ut[j] for j in range(nt)] + [(E + p) * un]
 
 
+def hybrid_face_flux(P, dim, gamma, theta):
+    """Per-face choice between the shock-free central scheme and the
+    shock-capturing one (Sec. 3.2: the central schemes are for flows without
+    shocks, characteristic WENO5 with the Rusanov flux for flows with them; the
+    switch between them face by face is this build's extension).
+
+    P is the 6-node pencil i-2 .. i+3 of `face_flux`. Shock sensor: the
+    relative jump of the refinement criterion, |phi_{k+1} - phi_{k-1}| >
+    theta (phi_{k+1} + 2 phi_k + phi_{k-1}) for phi in (rho = p / T, p),
+    tested along the pencil at the four nodes k = i-1 .. i+2 whose neighbours
+    lie in the pencil. Where no node trips it, the face takes the central
+    scheme's conservative face value G_{i+1/2} = (26 F_{i+1/2} - F_{i-1/2} -
+    F_{i+3/2}) / 24 of Eq. 9 (the central face fluxes from nodes i-1..i+2,
+    i-2..i+1 and i..i+3); elsewhere the WENO5 + Rusanov flux of `face_flux`.
+    Either way the face carries one value, so the divergence stays a difference
+    of face values (conservative), and both need only nodes i-2 .. i+3.
+    Returns the face value in pencil order and the boolean `smooth` mask.
+    """
+    rho = [P[k][0] / P[k][3] for k in range(6)]
+    shock = None
+    for phi in (rho, [P[k][0] for k in range(6)]):
+        for k in range(1, 5):
+            s = np.abs(phi[k + 1] - phi[k - 1]) > theta * (phi[k + 1] + 2.0 * phi[k] + phi[k - 1])
+            shock = s if shock is None else (shock | s)
+    smooth = np.logical_not(shock)
+    Fm = central_face_flux(P[1:5], dim, gamma)
+    Fl = central_face_flux(P[0:4], dim, gamma)
+    Fh = central_face_flux(P[2:6], dim, gamma)
+    Gc = [(26.0 * Fm[v] - Fl[v] - Fh[v]) / 24.0 for v in range(dim + 2)]
+    Fw = face_flux(P, dim, gamma, 'rusanov')
+    return [np.where(smooth, Gc[v], Fw[v]) for v in range(dim + 2)], smooth
+
+
 def pencil_to_global(F, dim, d):
     """Map a flux in pencil order (mass, normal, tangentials, energy) back to
     the global order (mass, m_0 .. m_{d-1}, energy) for a face normal to d."""
@@ -260,7 +293,7 @@ def pencil_to_global(F, dim, d):
     return out
 
 
-def patch_rhs(A, dim, N, g, dx, gamma, flux='rusanov'):
+def patch_rhs(A, dim, N, g, dx, gamma, flux='rusanov', theta_switch=0.05):
     """Right-hand side R = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d on a patch interior
     (Sec. 3.2, Eq. 10: divergence of the Riemann fluxes; dims in order x, y, z).
 
@@ -271,6 +304,10 @@ def patch_rhs(A, dim, N, g, dx, gamma, flux='rusanov'):
     in its conservative form: the difference of the face values
     G_{i+1/2} = (26 F_{i+1/2} - F_{i-1/2} - F_{i+3/2}) / 24, so that sums over
     patches telescope and the coarse-fine correction acts on G.
+
+    With flux='hybrid' every face i+1/2 (i = -1 .. N-1) takes the value of
+    `hybrid_face_flux` with threshold theta_switch: the central G where the
+    shock sensor is quiet, the WENO5 + Rusanov flux elsewhere.
 
     A: slot array (nv, Z, Y, X) with g ghost layers in every active dimension
     (array axis 3 - d holds dimension d). Returns (R, faces) where R has the
@@ -309,7 +346,10 @@ def patch_rhs(A, dim, N, g, dx, gamma, flux='rusanov'):
                 sl[ax] = slice(k, k + N + 1)   # faces i+1/2, i = -1..N-1
                 sl = tuple(sl[1:])
                 P.append((p[sl], u[d][sl], [u[e][sl] for e in tdims], T[sl]))
-            Fp = face_flux(P, dim, gamma, flux)
+            if flux == 'hybrid':
+                Fp, _ = hybrid_face_flux(P, dim, gamma, theta_switch)
+            else:
+                Fp = face_flux(P, dim, gamma, flux)
             F = pencil_to_global(Fp, dim, d)
             F = np.stack(F)                      # (nv, ..., N+1 along ax)
         hi = [slice(None)] * 4

@@ -18,9 +18,13 @@ ic             initial-condition name
 cfl            CFL number
 t_end          final time (the time step is clipped to it)
 theta_rho/p    thresholds of the relative-jump refinement sensor
-flux           numerical flux at faces: 'rusanov' (Sec. 3.2), 'hllc' (an option) or
+flux           numerical flux at faces: 'rusanov' (Sec. 3.2), 'hllc' (an option),
                'central' (the shock-free central interpolation and 4th-order
-               staggered divergence of Sec. 3.2, Eqs. 8-9)
+               staggered divergence of Sec. 3.2, Eqs. 8-9) or 'hybrid' (the
+               central face value where a shock sensor is quiet, WENO5 +
+               Rusanov elsewhere, face by face)
+theta_switch   threshold of the hybrid flux's shock sensor (relative jump of rho
+               and p along the pencil; 0.05)
 seed           seed of the +-1 % density perturbation (blast only)
 amp            amplitude of that perturbation (blast only; 0.01)
 
@@ -100,6 +104,7 @@ def workload(name, **overrides):
     w = copy.deepcopy(WORKLOADS[name])
     w['name'] = name
     w.setdefault('flux', 'rusanov')
+    w.setdefault('theta_switch', 0.05)
     for k, v in overrides.items():
         if k not in w:
             raise KeyError(k)
