@@ -118,15 +118,25 @@ typedef struct {
                              option the method leaves open: Toro's HLLC from the same face states) or
                              AMR_FLUX_CENTRAL (Sec. 3.2's shock-free schemes: 4th-order central mid-point
                              interpolation of p, u, T (Eq. 8), the Euler flux of that edge state, and the
-                             4th-order staggered divergence (Eq. 9) in conservative form) */
+                             4th-order staggered divergence (Eq. 9) in conservative form) or
+                             AMR_FLUX_HYBRID (face by face: the central scheme's conservative face
+                             value where a shock sensor is quiet, WENO5 + Rusanov elsewhere; Sec. 3.2
+                             gives the central schemes for shock-free flows and WENO for flows with
+                             shocks, the per-face switch is this library's extension) */
     double mlp_keep_margin;  /* H >= 0, learned flagger only: a patch requests refinement if a band
                                 cell's logit is > 0 and blocks the coarsening of its parent if one
                                 is > -H (hysteresis between the two decisions; 0: the same test) */
+    double theta_switch;  /* AMR_FLUX_HYBRID only: a face i+1/2 takes the WENO5 + Rusanov flux if, at
+                             any pencil node k = i-1 .. i+2 and for phi = rho (= p / T) or p,
+                             |phi_{k+1} - phi_{k-1}| > theta_switch (phi_{k+1} + 2 phi_k + phi_{k-1})
+                             (the relative jump of the refinement sensor along the face normal);
+                             else the central value. Default 0.05 */
 } amr_options_t;
 
 #define AMR_FLUX_RUSANOV 0
 #define AMR_FLUX_HLLC 1
 #define AMR_FLUX_CENTRAL 2
+#define AMR_FLUX_HYBRID 3
 
 /* Launch parameters of the batched step (amr_get_tuning), in this order:
  * CTAs per SM of the ghost fill, ghost cells per ghost-fill work item, CTAs per
@@ -164,11 +174,18 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
  * passing NULL avoids a device-to-host synchronisation. */
 int amr_step(amr_ctx* ctx, double dt, double* dt_used);
 
-/* n_steps CFL steps (amr_step with dt <= 0), each followed by amr_regrid when
- * regrid != 0: the production loop, with no return to the caller between
- * steps. Stops at the first error and returns it (the steps before it stand);
- * n_steps < 0 is AMR_ERR_ARG. The only host synchronisation is the regrid's
- * read-back of the refinement requests. */
+/* n_steps CFL steps (amr_step with dt <= 0): the production loop, with no
+ * return to the caller between steps. regrid is the regrid interval K: 0
+ * never regrids; K >= 1 runs amr_regrid after every K-th step taken by
+ * amr_advance since the context's last regrid (the count carries over
+ * between calls and restarts at every regrid, amr_regrid included, so
+ * repeated amr_advance(ctx, 1, K) calls regrid as one amr_advance(ctx, n, K)
+ * does); K = 1 regrids after every step. The refinement criterion is not
+ * evaluated between regrids, so with K > 1 a feature can move up to K steps
+ * before the mesh follows it (Sec. 4.3 leaves the regrid frequency to the
+ * runtime program). Stops at the first error and returns it (the steps before
+ * it stand); n_steps < 0 or regrid < 0 is AMR_ERR_ARG. The only host
+ * synchronisation is each regrid's read-back of the refinement requests. */
 int amr_advance(amr_ctx* ctx, int n_steps, int regrid);
 
 /* Flag (plain sensor or learned indicator), close the requests under R2
@@ -214,6 +231,17 @@ int amr_restore(amr_ctx* ctx, const char* path);
  * Two-call protocol on each list (NULL list: size only). */
 int amr_get_requests(amr_ctx* ctx, int* n_refine, int* refine_keys,
                      int* n_coarsen, int* coarsen_keys);
+
+/* The refinement requests the plain relative-jump sensor makes on the current
+ * hierarchy and state, whatever flagger the context regrids with: the leaf
+ * patches below the finest level that the plain criterion would refine but
+ * that are not refined. With the learned indicator, or with a regrid interval
+ * above 1 (amr_advance), this counts how far the mesh lags the plain
+ * criterion (unmet requests; the paper leaves the refinement criterion and its
+ * frequency to the runtime program, Sec. 4.2-4.3). Fills the ghost cells of
+ * the current state as a regrid does; changes neither the hierarchy nor the
+ * interiors. *n_refine receives the count; NULL is AMR_ERR_ARG. */
+int amr_plain_requests(amr_ctx* ctx, int* n_refine);
 
 /* The mesh half of a regrid on a caller's hierarchy, on the host alone (no
  * context, no GPU; Sec. 4.3). Starting from the hierarchy `keys` (n rows of
@@ -361,8 +389,8 @@ int amr_mlp_train(int dim, const float* X, const float* y, long n, float pos_wei
  *
  * For callers that cannot allocate device memory: code running inside a
  * task-based runtime that owns all device memory and only maps buffers for
- * its tasks, code that issues work while a CUDA stream capture is in progress,
- * and real-time loops where an allocation could synchronise the device.
+ * its tasks, and real-time loops where an allocation could synchronise the
+ * device.
  * X (n x K floats), y (n floats), weights (flat layout of amr_set_mlp), grad
  * (same layout, output) and loss (one float, output) are DEVICE pointers owned
  * by the caller; work is issued on `stream` (a cudaStream_t, NULL = legacy
@@ -371,8 +399,10 @@ int amr_mlp_train(int dim, const float* X, const float* y, long n, float pos_wei
  * held until the process exits), so n is limited to
  * AMR_MLP_NOALLOC_MAX_ROWS; larger n returns AMR_ERR_ARG. The call allocates
  * nothing. Its first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call outside any
- * stream capture. Every call shares the one array: calls that overlap on the
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture. The cached address belongs to the device's primary
+ * context: after cudaDeviceReset it is stale, so do not call this function
+ * in a process that has reset the device. Every call shares the one array: calls that overlap on the
  * GPU (other streams, other host threads) race and give wrong results.
  * Returns AMR_OK, AMR_ERR_ARG or AMR_ERR_CUDA. */
 #define AMR_MLP_NOALLOC_MAX_ROWS 2048

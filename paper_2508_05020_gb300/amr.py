@@ -40,9 +40,9 @@ class Options(C.Structure):
                 ('dev_alloc', ALLOC_FN), ('dev_free', FREE_FN), ('user', C.c_void_p),
                 ('stream', C.c_void_p), ('mlp_weights', C.c_void_p), ('mlp_n_weights', C.c_long),
                 ('autotune', C.c_int), ('flux', C.c_int),
-                ('mlp_keep_margin', C.c_double)]
+                ('mlp_keep_margin', C.c_double), ('theta_switch', C.c_double)]
 
-FLUX = {'rusanov': 0, 'hllc': 1, 'central': 2}
+FLUX = {'rusanov': 0, 'hllc': 1, 'central': 2, 'hybrid': 3}
 
 TUNE_NAMES = ('ghost_ctas_per_sm', 'ghost_cells_per_item', 'rhs_ctas_per_sm', 'reflux_ctas_per_sm',
               'restrict_ctas_per_sm', 'cfl_ctas_per_sm', 'flag_ctas_per_sm')
@@ -78,6 +78,7 @@ SIGNATURES = [
     ('amr_restore', C.c_int, [C.c_void_p, C.c_char_p]),
     ('amr_set_mlp', C.c_int, [C.c_void_p, C.c_void_p, C.c_long]),
     ('amr_flag_stats', C.c_int, [C.c_void_p, C.c_void_p]),
+    ('amr_plain_requests', C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ('amr_harvest', C.c_int, [C.c_void_p, C.POINTER(C.c_long), C.c_void_p, C.c_void_p]),
     ('amr_get_counters', C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_longlong)]),
@@ -143,7 +144,7 @@ class _TorchMemory:
 
 def make_options(precision=64, cfl=0.5, t_end=0.0, flagger='plain', theta_rho=0.05, theta_p=0.05,
                  max_patches=0, seed=0, amp=0.01, mode='batched', use_graph=True, torch_memory=True,
-                 autotune=False, flux='rusanov', mlp_keep_margin=0.0):
+                 autotune=False, flux='rusanov', mlp_keep_margin=0.0, theta_switch=0.05):
     """Options struct plus the objects that must outlive it."""
     lib = load()
     o = Options()
@@ -162,6 +163,7 @@ def make_options(precision=64, cfl=0.5, t_end=0.0, flagger='plain', theta_rho=0.
     o.autotune = 1 if autotune else 0
     o.flux = FLUX[flux]
     o.mlp_keep_margin = mlp_keep_margin
+    o.theta_switch = theta_switch
     keep = []
     if torch_memory:
         import torch
@@ -195,7 +197,7 @@ class AMR:
         self.opt, self._keep = make_options(precision, w['cfl'], w['t_end'], flagger, w['theta_rho'],
                                             w['theta_p'], max_patches, w.get('seed', 0), w.get('amp', 0.01),
                                             mode, use_graph, torch_memory, autotune, w.get('flux', 'rusanov'),
-                                            mlp_keep_margin)
+                                            mlp_keep_margin, w.get('theta_switch', 0.05))
         if mlp_weights is not None:
             self._w_host = np.ascontiguousarray(mlp_weights, dtype=np.float32)
             self.opt.mlp_weights = _ptr(self._w_host)
@@ -237,8 +239,10 @@ class AMR:
         self._check(self.lib.amr_regrid(self.ctx))
 
     def advance(self, n_steps, regrid=True):
-        """n_steps CFL steps, each followed by a regrid (amr_advance)."""
-        self._check(self.lib.amr_advance(self.ctx, int(n_steps), 1 if regrid else 0))
+        """n_steps CFL steps (amr_advance). regrid: True (after every step),
+        False (never) or the regrid interval K (after every K-th step)."""
+        k = (1 if regrid else 0) if isinstance(regrid, bool) else int(regrid)
+        self._check(self.lib.amr_advance(self.ctx, int(n_steps), k))
 
     def get_level(self, level, data=True, out=None):
         """Patch coordinates and interiors of a level (amr_get_level). `out`: a
@@ -291,6 +295,14 @@ class AMR:
     def set_mlp(self, weights):
         wv = np.ascontiguousarray(weights, dtype=np.float32)
         self._check(self.lib.amr_set_mlp(self.ctx, _ptr(wv), wv.size))
+
+    def plain_requests(self):
+        """Refinement requests of the plain sensor on the current hierarchy
+        (amr_plain_requests): the unmet requests of a learned or infrequent
+        regrid."""
+        n = C.c_int()
+        self._check(self.lib.amr_plain_requests(self.ctx, C.byref(n)))
+        return n.value
 
     def flag_stats(self):
         out = np.zeros(4, dtype=np.int64)

@@ -86,6 +86,8 @@ struct amr_ctx {
     // the ghosts of U0 hold the values the first stage's ghost fill would
     // write (a regrid filled them at the current time and left the mesh as it was)
     bool ghosts_valid = false;
+    // steps amr_advance has taken since the last regrid (amr_regrid or its own)
+    int since_regrid = 0;
     cudaEvent_t ev_req = nullptr;         // end of a regrid's request read-back
     std::chrono::steady_clock::time_point rg_t0{};
     // per-class CUDA-event timing of the last step (ghost, rhs, reflux, restrict, cfl);
@@ -664,18 +666,24 @@ int regrid_impl(amr_ctx* c, bool resample_ic) {
     return regrid_finish<T>(c, resample_ic, nullptr, nullptr);
 }
 
-// n steps, each followed by a regrid. The next step is issued before the
-// host has read the regrid's requests; if there were any, that step's kernels
-// found DevTime::cancel set and did nothing, and it is issued again once the
-// hierarchy has been updated.
+// n steps, a regrid after every K-th step since the last regrid. Before a
+// regrid's requests are read on the host the next step is already issued; if
+// there were requests, that step's kernels found DevTime::cancel set and did
+// nothing, and it is issued again once the hierarchy has been updated. Steps
+// between regrids are issued back to back without any host synchronisation.
 template <typename T>
-int advance_impl(amr_ctx* c, int n) {
+int advance_impl(amr_ctx* c, int n, int K) {
     if (n == 0) return AMR_OK;
     int r = step_impl<T>(c, 0.0, nullptr);
     if (r) return r;
     for (int i = 0; i < n; ++i) {
-        if ((r = regrid_enqueue<T>(c))) return r;
         const bool more = i + 1 < n;
+        if (++c->since_regrid < K) {
+            if (more && (r = step_impl<T>(c, 0.0, nullptr))) return r;
+            continue;
+        }
+        c->since_regrid = 0;
+        if ((r = regrid_enqueue<T>(c))) return r;
         if (more && (r = step_impl<T>(c, 0.0, nullptr))) return r;
         bool had = false, changed = false;                 // had: the step issued ahead is void
         if ((r = regrid_finish<T>(c, false, &had, &changed))) return r;
@@ -938,6 +946,7 @@ void amr_default_options(amr_options_t* opt) {
     opt->amp = 0.01;
     opt->mode = AMR_MODE_BATCHED;
     opt->use_graph = 1;
+    opt->theta_switch = 0.05;
 }
 
 int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int base_cells[3], int levels, int ratio,
@@ -965,8 +974,10 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     if (!(c->opt.cfl > 0.0)) return bad("cfl must be positive");
     if (c->opt.flagger != AMR_FLAG_PLAIN && c->opt.flagger != AMR_FLAG_MLP) return bad("unknown flagger");
     if (c->opt.mode != AMR_MODE_BATCHED && c->opt.mode != AMR_MODE_PER_PATCH) return bad("unknown mode");
-    if (c->opt.flux != AMR_FLUX_RUSANOV && c->opt.flux != AMR_FLUX_HLLC && c->opt.flux != AMR_FLUX_CENTRAL)
+    if (c->opt.flux != AMR_FLUX_RUSANOV && c->opt.flux != AMR_FLUX_HLLC && c->opt.flux != AMR_FLUX_CENTRAL &&
+        c->opt.flux != AMR_FLUX_HYBRID)
         return bad("unknown flux");
+    if (c->opt.theta_switch != c->opt.theta_switch) return bad("theta_switch is NaN");
     if (!(c->opt.mlp_keep_margin >= 0.0) || !(c->opt.mlp_keep_margin < 1.0e30))
         return bad("mlp_keep_margin must be in [0, 1e30)");
     int bp[3] = {1, 1, 1};
@@ -1058,7 +1069,10 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.theta_p = c->opt.theta_p;
     g.ic = ic_id;
     g.flux = c->opt.flux;
+    g.theta_sw = c->opt.theta_switch;
     g.mlp_keep = (float)c->opt.mlp_keep_margin;
+    g.tc_wait = TC_WAIT_CYCLES;
+    g.tc_test = 0;
     g.seed = c->opt.seed;
     g.amp = c->opt.amp;
     dmr_states(gamma, g.dmr_pre, g.dmr_post);
@@ -1217,6 +1231,7 @@ int amr_regrid(amr_ctx* c) {
     GUARD(c);
     Range range("amr_regrid");
     if (c->L == 1) return AMR_OK;
+    c->since_regrid = 0;
     return c->precision == 64 ? regrid_impl<double>(c, false) : regrid_impl<float>(c, false);
 }
 
@@ -1224,12 +1239,14 @@ int amr_advance(amr_ctx* c, int n_steps, int regrid) {
     GUARD(c);
     Range range("amr_advance");
     if (n_steps < 0) return fail(c, AMR_ERR_ARG, "negative step count");
+    if (regrid < 0) return fail(c, AMR_ERR_ARG, "negative regrid interval");
     if (regrid && c->L > 1 && c->mode == AMR_MODE_BATCHED)
-        return c->precision == 64 ? advance_impl<double>(c, n_steps) : advance_impl<float>(c, n_steps);
+        return c->precision == 64 ? advance_impl<double>(c, n_steps, regrid) : advance_impl<float>(c, n_steps, regrid);
     for (int i = 0; i < n_steps; ++i) {
         int r = c->precision == 64 ? step_impl<double>(c, 0.0, nullptr) : step_impl<float>(c, 0.0, nullptr);
         if (r) return r;
-        if (regrid && c->L > 1) {
+        if (regrid && c->L > 1 && ++c->since_regrid >= regrid) {
+            c->since_regrid = 0;
             r = c->precision == 64 ? regrid_impl<double>(c, false) : regrid_impl<float>(c, false);
             if (r) return r;
         }
@@ -1359,6 +1376,36 @@ int amr_get_requests(amr_ctx* c, int* n_refine, int* refine_keys, int* n_coarsen
             coarsen_keys[4 * i + 2] = cand[i].y;
             coarsen_keys[4 * i + 3] = cand[i].z;
         }
+    return AMR_OK;
+}
+
+// Test hook of the timeout path of the learned-flag kernel, deliberately not
+// declared in include/amr.h: `cycles` (> 0) replaces the limit of every role
+// wait of its tensor-core pipeline (the tear-down's wait for in-flight MMAs
+// keeps the full limit), and `withhold` != 0 makes its MMA thread withhold the
+// epilogue's accumulator signal, so that one of those waits cannot complete
+// and the kernel must take its abort path (AMR_ERR_TIMEOUT at the next
+// regrid). A context that reported the timeout refuses further work.
+extern "C" int amr_test_tc_wait(amr_ctx* c, long long cycles, int withhold) {
+    GUARD(c);
+    if (cycles <= 0) return fail(c, AMR_ERR_ARG, "wait limit must be positive");
+    c->grid.tc_wait = cycles;
+    c->grid.tc_test = withhold ? 1 : 0;
+    return AMR_OK;
+}
+
+int amr_plain_requests(amr_ctx* c, int* n_refine) {
+    GUARD(c);
+    if (!n_refine) return fail(c, AMR_ERR_ARG, "count pointer required");
+    *n_refine = 0;
+    if (c->L == 1) return AMR_OK;
+    std::vector<Key> req, cand;
+    const int flagger = c->flagger;
+    c->flagger = AMR_FLAG_PLAIN;
+    const int r = c->precision == 64 ? compute_requests<double>(c, req, cand) : compute_requests<float>(c, req, cand);
+    c->flagger = flagger;
+    if (r) return r;
+    *n_refine = (int)req.size();
     return AMR_OK;
 }
 

@@ -22,6 +22,10 @@ constexpr int ERR_NONFINITE = 1;
 constexpr int ERR_MESH = 2;
 constexpr int ERR_TIMEOUT = 4;        // a bounded device wait gave up
 
+// limit of a bounded wait of the tensor-core pipeline, in SM clock cycles
+// (about two seconds)
+constexpr long long TC_WAIT_CYCLES = 1ll << 32;
+
 // Per-step scalars kept on the device so that a captured step needs no host input.
 struct DevTime {
     double t;                   // time at the start of the step
@@ -49,8 +53,13 @@ struct Grid {
     double cfl, t_end;
     double theta_rho, theta_p;
     int ic;
-    int flux;                   // AMR_FLUX_RUSANOV or AMR_FLUX_HLLC
+    int flux;                   // AMR_FLUX_*
+    double theta_sw;            // AMR_FLUX_HYBRID: threshold of the face's shock sensor
     float mlp_keep;             // learned flagger: a logit above -mlp_keep sets the keep bit
+    long long tc_wait;          // learned flagger: limit of a role's pipeline wait (SM cycles)
+    int tc_test;                // learned flagger, tests of the timeout path only: nonzero makes
+                                //   the MMA thread withhold the epilogue's accumulator signal, so
+                                //   the epilogue's first wait cannot complete
     unsigned long long seed;
     double amp;
     int base_cells[3];

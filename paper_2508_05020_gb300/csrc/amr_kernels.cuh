@@ -301,21 +301,24 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
 // not positive there, the mean of nodes 2 and 3. The flux is the Euler flux of
 // that one edge state (no dissipation). Output in pencil order.
 // ---------------------------------------------------------------------------
-template <typename T, int NT>
+// OFF shifts the four nodes by -1, 0 or +1 (the faces i - 1/2, i + 1/2,
+// i + 3/2 of the hybrid flux below).
+template <typename T, int NT, int OFF = 0>
 __device__ __forceinline__ void central_flux(const T (&p)[6], const T (&un)[6], const T (&ut)[NT > 0 ? NT : 1][6],
                                              const T (&Tt)[6], T gm1, T (&F)[NT + 3]) {
     constexpr int NF = NT + 3;
-    auto mid = [](const T (&v)[6]) { return (T(9) * (v[2] + v[3]) - (v[1] + v[4])) * T(0.0625); };
+    constexpr int A = 1 + OFF, B = 2 + OFF, C = 3 + OFF, D = 4 + OFF;
+    auto mid = [](const T (&v)[6]) { return (T(9) * (v[B] + v[C]) - (v[A] + v[D])) * T(0.0625); };
     T pf = mid(p), unf = mid(un), Tf = mid(Tt);
     T utf[NT > 0 ? NT : 1];
 #pragma unroll
     for (int j = 0; j < NT; ++j) utf[j] = mid(ut[j]);
     if (!(pf > T(0)) || !(Tf > T(0))) {
-        pf = T(0.5) * (p[2] + p[3]);
-        unf = T(0.5) * (un[2] + un[3]);
-        Tf = T(0.5) * (Tt[2] + Tt[3]);
+        pf = T(0.5) * (p[B] + p[C]);
+        unf = T(0.5) * (un[B] + un[C]);
+        Tf = T(0.5) * (Tt[B] + Tt[C]);
 #pragma unroll
-        for (int j = 0; j < NT; ++j) utf[j] = T(0.5) * (ut[j][2] + ut[j][3]);
+        for (int j = 0; j < NT; ++j) utf[j] = T(0.5) * (ut[j][B] + ut[j][C]);
     }
     const T rho = Num<T>::div(pf, Tf);
     T usq = unf * unf;
@@ -328,6 +331,43 @@ __device__ __forceinline__ void central_flux(const T (&p)[6], const T (&un)[6], 
 #pragma unroll
     for (int j = 0; j < NT; ++j) F[2 + j] = mn * utf[j];
     F[NF - 1] = (E + pf) * unf;
+}
+
+// ---------------------------------------------------------------------------
+// Hybrid face value between pencil nodes 2 and 3 (Sec. 3.2: central schemes
+// for shock-free flow, characteristic WENO5 + Rusanov for shocks; the choice
+// face by face is an extension). Shock sensor: at nodes 1..4 and for phi in
+// (rho = p / T, p), |phi_{k+1} - phi_{k-1}| > theta (phi_{k+1} + 2 phi_k +
+// phi_{k-1}). Quiet: the central scheme's conservative face value
+// (26 F_c(i+1/2) - F_c(i-1/2) - F_c(i+3/2)) / 24 (Eq. 9) from the central
+// fluxes of nodes 1..4, 0..3 and 2..5; else the WENO5 + Rusanov flux.
+// ---------------------------------------------------------------------------
+template <typename T, int NT>
+__device__ __forceinline__ void hybrid_flux(const T (&p)[6], const T (&un)[6], const T (&ut)[NT > 0 ? NT : 1][6],
+                                            const T (&Tt)[6], T gamma, T gm1, T theta, T (&F)[NT + 3]) {
+    constexpr int NF = NT + 3;
+    T rho[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rho[k] = Num<T>::div(p[k], Tt[k]);
+    bool shock = false;
+#pragma unroll
+    for (int k = 1; k < 5; ++k) {
+        shock = shock || fabs(rho[k + 1] - rho[k - 1]) > theta * (rho[k + 1] + T(2) * rho[k] + rho[k - 1]);
+        shock = shock || fabs(p[k + 1] - p[k - 1]) > theta * (p[k + 1] + T(2) * p[k] + p[k - 1]);
+    }
+    if (shock) {
+        face_flux<T, NT, AMR_FLUX_RUSANOV>(p, un, ut, Tt, gamma, gm1, F);
+        return;
+    }
+    T Fl[NF], Fm[NF], Fh[NF];
+    central_flux<T, NT, -1>(p, un, ut, Tt, gm1, Fl);
+    central_flux<T, NT, 0>(p, un, ut, Tt, gm1, Fm);
+    central_flux<T, NT, 1>(p, un, ut, Tt, gm1, Fh);
+#pragma unroll
+    for (int v = 0; v < NF; ++v) {
+        const T gsum = T(26) * Fm[v] - Fl[v] - Fh[v];
+        F[v] = sizeof(T) == 4 ? gsum * T(1.0 / 24.0) : gsum / T(24);
+    }
 }
 
 // Metadata of one patch staged in shared memory by the CTA that serves it:
@@ -860,6 +900,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 }
                 T Fp[NT + 3];
                 if constexpr (CEN) central_flux<T, NT>(pp, un, ut, Tt, gm1, Fp);
+                else if constexpr (FLUX == AMR_FLUX_HYBRID) hybrid_flux<T, NT>(pp, un, ut, Tt, gamma, gm1, T(g.theta_sw), Fp);
                 else face_flux<T, NT, FLUX>(pp, un, ut, Tt, gamma, gm1, Fp);
                 // pencil order -> global variable order
                 T Fg[NV];

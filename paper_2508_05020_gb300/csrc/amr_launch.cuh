@@ -41,6 +41,10 @@ static cudaError_t rhs_launch(const Grid& g, const T* Us, const T* U0, T* Uout, 
         k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_CENTRAL>
             <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_CENTRAL>(), s>>>(g, Us, U0, Uout, faces, stage,
                                                                                    one_slot);
+    else if (g.flux == AMR_FLUX_HYBRID)
+        k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HYBRID>
+            <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HYBRID>(), s>>>(g, Us, U0, Uout, faces, stage,
+                                                                                  one_slot);
     else if (g.flux == AMR_FLUX_HLLC)
         k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>
             <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HLLC>(), s>>>(g, Us, U0, Uout, faces, stage,
@@ -62,6 +66,10 @@ static cudaError_t rhs_prepare() {
     e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HLLC>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HYBRID>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HYBRID>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_CENTRAL>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -300,8 +300,6 @@ __device__ float mlp_tile_tc(TcState& st, const MlpTcSmem<D>& s, __nv_bfloat16* 
 // ---------------------------------------------------------------------------
 namespace amr {
 
-constexpr long long TC_WAIT_CYCLES = 1ll << 32;     // about two seconds of SM clock
-
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
 }
@@ -321,22 +319,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     return done != 0;
 }
 
-// wait for the completion of phase `parity`; false once *abort is set or on
-// timeout (which sets *abort)
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t mbar, uint32_t parity, volatile int* abort) {
+// wait for the completion of phase `parity`; false once *abort is set or
+// after `limit` SM cycles (which sets *abort)
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t mbar, uint32_t parity, volatile int* abort, long long limit) {
     if (mbar_try(mbar, parity)) return true;               // the common case: no clock read
     const long long t0 = clock64();
     for (unsigned it = 1;; ++it) {
         if (mbar_try(mbar, parity)) return true;
         if (*abort) return false;
-        if ((it & 63u) == 0u && clock64() - t0 > TC_WAIT_CYCLES) {
+        if ((it & 63u) == 0u && clock64() - t0 > limit) {
             *abort = 1;
             return false;
         }
     }
 }
 
-// the same wait without the abort word (tear-down: in-flight MMAs)
+// the same wait without the abort word and at the full limit (tear-down:
+// in-flight MMAs)
 __device__ __forceinline__ bool mbar_wait_cycles(uint32_t mbar, uint32_t parity) {
     const long long t0 = clock64();
     for (unsigned it = 0;; ++it) {

@@ -1,6 +1,6 @@
-"""The reference arm of bench.py (the oracle timed on the host cores) prints
-one JSON line with the keys of the bench contract, on the main arm's metric
-and workload (no GPU)."""
+"""The reference arm of bench.py (the oracle timed on all host cores, one
+replica per core) prints one JSON line with the keys of the bench contract,
+on the main arm's metric, naming the sample it ran (no GPU)."""
 import json
 import os
 import subprocess
@@ -22,7 +22,10 @@ def test_reference_arm_line():
     assert line['impl'] == 'reference' and line['n_gpus'] == 1 and line['steps'] == 1 and line['warmup'] == 0
     assert line['higher_is_better'] is True and line['vs_baseline'] is None and line['data'] == 'synthetic'
     assert line['value'] > 0 and line['unit'] == 'cell-updates/s'
-    assert line['config']['workload'].startswith('blast3d base 128x128x128, 3 levels, 16^3 patches')
+    # the workload names what ran (the oracle on a 16^3-base sample), and what it samples
+    assert line['config']['workload'].startswith('blast3d base 16x16x16, 3 levels, 16^3 patches, FP64, plain flags')
+    assert line['config']['sample_of'].startswith('blast3d base 128x128x128, 3 levels, 16^3 patches')
+    assert line['config']['leaf_cell_updates_per_s'] > 0
     cb = line['cpu_baseline']
     assert cb['kind'] == 'oracle' and cb['cores'] >= 1 and cb['value'] == line['value'] and cb['sample']
     e2e = line['e2e']

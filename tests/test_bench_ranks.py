@@ -84,3 +84,20 @@ def test_roofline_accounting():
     assert (bench.rhs_traffic('blast3d', 0, 0) is None) == (bench.rhs_source_hash() != bench.RHS_TRAFFIC['hash'])
     assert bench.rhs_traffic('blast3d', 64, 0) is None
     assert bench.rhs_traffic('dmr', 0, 0) is None
+
+
+def test_run_planning_and_traffic_scaling():
+    # chunks of a run to t_end: capped, and one step at a time near the end so
+    # that no step is spent after t_end (the last one is clipped to it)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.plan_chunk(0.0, 1e-5, 25) == 0
+    assert bench.plan_chunk(1.0, 1e-5, 25) == 25
+    assert bench.plan_chunk(10.5e-5, 1e-5, 25) == 8
+    assert bench.plan_chunk(2.5e-5, 1e-5, 25) == 1
+    assert bench.plan_chunk(1.0, 0.0, 25) == 1
+    # the captured launch's DRAM bytes, scaled per leaf patch to another launch
+    if bench.rhs_traffic('blast3d', 0, 0) is not None:
+        b = bench.RHS_TRAFFIC['bytes']
+        assert bench.rhs_traffic('blast3d', 0, 0, bench.RHS_TRAFFIC['leaves']) == b
+        assert bench.rhs_traffic('blast3d', 0, 0, 2 * bench.RHS_TRAFFIC['leaves']) == 2 * b

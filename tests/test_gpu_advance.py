@@ -39,3 +39,53 @@ def test_advance_equals_step_regrid(name, base, precision):
     a.close()
     b.close()
 
+
+@pytest.mark.parametrize('name,base,precision,flagger,K', [('riemann2d', (64, 64, 1), 64, 'plain', 3),
+                                                           ('blast3d', (32, 32, 32), 32, 'mlp', 4)])
+def test_regrid_interval_equals_step_calls(name, base, precision, flagger, K):
+    """amr_advance(n, K): a regrid after every K-th step, the count carried
+    across calls and restarted by amr_regrid; the same as issuing the steps
+    and regrids one call at a time, bit for bit."""
+    import os
+    from paper_2508_05020_gb300.amr import AMR, AMRError
+    w = workload(name, base_cells=base)
+    kw = {}
+    if flagger == 'mlp':
+        kw = dict(flagger='mlp', mlp_keep_margin=12.0,
+                  mlp_weights=np.load(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                   'paper_2508_05020_gb300', 'weights',
+                                                   'indicator_d%d_k4.npy' % w['dim'])).astype(np.float32))
+    a = AMR(w, precision=precision, **kw)
+    b = AMR(w, precision=precision, **kw)
+    c = AMR(w, precision=precision, **kw)
+    n = 3 * K + 2
+    for i in range(n):
+        a.step()
+        if (i + 1) % K == 0:
+            a.regrid()
+    b.advance(n, regrid=K)
+    for _ in range(n):                              # one step per call: the interval carries over
+        c.advance(1, regrid=K)
+    assert a.diag()[0] == b.diag()[0] == c.diag()[0]
+    for l in range(a.L):
+        ca, xa = a.get_level(l)
+        for o in (b, c):
+            co, xo = o.get_level(l)
+            assert np.array_equal(ca, co) and np.array_equal(xa, xo)
+    # amr_regrid restarts the count: K - 1 more steps take no regrid, the K-th does
+    a.regrid()
+    b.regrid()
+    for i in range(K):
+        a.step()
+    a.regrid()
+    b.advance(K - 1, regrid=K)
+    b.advance(1, regrid=K)
+    assert a.diag()[0] == b.diag()[0]
+    for l in range(a.L):
+        ca, xa = a.get_level(l)
+        cb, xb = b.get_level(l)
+        assert np.array_equal(ca, cb) and np.array_equal(xa, xb)
+    with pytest.raises(AMRError):
+        b.advance(1, regrid=-1)
+    for o in (a, b, c):
+        o.close()

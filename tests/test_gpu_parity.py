@@ -93,6 +93,15 @@ def run_both(w, steps, regrid=True, **kw):
     ('sod', dict(flux='central'), 8, 0.0),
     ('shear2d', dict(base_cells=(32, 32, 1), patch=8, levels=3), 4, TOL64),
     ('shear2d', dict(base_cells=(64, 64, 1), patch=16, levels=3), 2, TOL64),
+    # the hybrid flux: the central value where the shock sensor is quiet,
+    # WENO5 + Rusanov at shocks, face by face
+    ('sod', dict(flux='hybrid'), 25, 0.0),
+    ('riemann2d', dict(base_cells=(32, 32, 1), patch=8, flux='hybrid'), 4, 0.0),
+    ('dmr', dict(base_cells=(64, 16, 1), patch=8, levels=3, flux='hybrid'), 3, 0.0),
+    ('implosion', dict(base_cells=(32, 32, 1), patch=8, levels=3, flux='hybrid'), 4, 0.0),
+    ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2, flux='hybrid'), 2, 0.0),
+    ('blast3d', dict(base_cells=(32, 32, 32), patch=16, levels=2, flux='hybrid'), 1, 0.0),
+    ('shu_osher', dict(flux='hybrid', theta_switch=0.02), 6, TOL64),
     # 32-cell patches in 2D, a single level in 3D
     ('riemann2d', dict(base_cells=(128, 128, 1), patch=32, levels=2), 3, 0.0),
     ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=1), 2, 0.0),
@@ -149,6 +158,9 @@ def l1_rho_rel(gpu, ref):
     ('riemann2d', dict(base_cells=(32, 32, 1), patch=8, flux='hllc'), 6),
     ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2, flux='hllc'), 2),
     ('blast3d', dict(base_cells=(32, 32, 32), patch=16, levels=2), 1),
+    ('riemann2d', dict(base_cells=(32, 32, 1), patch=8, flux='hybrid'), 6),
+    ('blast3d', dict(base_cells=(16, 16, 16), patch=8, levels=2, flux='hybrid'), 2),
+    ('blast3d', dict(base_cells=(32, 32, 32), patch=16, levels=2, flux='hybrid'), 1),
 ])
 def test_fp32_l1_against_oracle(name, kw, steps):
     # same mesh sequence: both sides regrid from their own flags; a flag near
@@ -308,10 +320,11 @@ def smooth3d_hierarchy(patch, levels, flux):
     return w, r
 
 
-@pytest.mark.parametrize('patch,levels', [(8, 3), (16, 2)])
-def test_fp64_central_3d_bitwise_given_identical_state(patch, levels):
-    # every dimension's pencils see variation (the z pencils included)
-    w, r = smooth3d_hierarchy(patch, levels, 'central')
+@pytest.mark.parametrize('patch,levels,flux', [(8, 3, 'central'), (16, 2, 'central'), (16, 2, 'hybrid')])
+def test_fp64_central_3d_bitwise_given_identical_state(patch, levels, flux):
+    # every dimension's pencils see variation (the z pencils included); the
+    # hybrid flux takes the central value at every face of this smooth field
+    w, r = smooth3d_hierarchy(patch, levels, flux)
     n = [len(r.mesh.level_list(l)) for l in range(levels)]
     assert n[-1] > 0 and (levels == 2 or n[-1] < 8 * n[-2]), n
     g = amr(w)
