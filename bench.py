@@ -388,6 +388,17 @@ class Run:
             if self.sample_every and not self.done():
                 self.unmet.append(self.amr.plain_requests())
 
+    def advance_until_left(self, n_left):
+        """Advance until about n_left steps remain before t_end (the step dt
+        drifts, so the estimate is renewed after every chunk)."""
+        while not self.done():
+            extra = self.steps_left() - n_left
+            if extra < 1.0:
+                break
+            self.seg(max(1, min(self.sample_every or 100, int(extra))))
+            if self.sample_every and not self.done():
+                self.unmet.append(self.amr.plain_requests())
+
     def steps_left(self):
         return (self.t_end - self.t) / self.dt_est if self.dt_est > 0 else float('inf')
 
@@ -563,7 +574,7 @@ def main():
              for v in range(nv)]
     # 3. just before t_end, then the rest of the run
     if has_end:
-        run.advance_to(w['t_end'] - (W + K + 2) * max(run.dt_est, 0.0))
+        run.advance_until_left(W + K + 2)
         if run.steps_left() >= W + K:
             window('t_end')
         run.advance_to(w['t_end'])
