@@ -52,7 +52,7 @@ RHS_TRAFFIC = {'bytes': 320362496 + 152754688, 'leaves': 1408, 'workload': 'blas
                             '// Metadata of one patch staged'),
                            ('paper_2508_05020_gb300/csrc/amr_kernels.cuh', '// K4: fused right-hand side',
                             '// K5: coarse-fine flux correction'),
-                           ('paper_2508_05020_gb300/csrc/amr_launch.cuh', 'template <typename T, int D, int N> struct RhsCfg',
+                           ('paper_2508_05020_gb300/csrc/amr_launch.cuh', 'template <typename T, int D, int N, int V = 0> struct RhsCfg',
                             'template <typename T>\ncudaError_t Kernels<T>::prepare')],
                'hash': '3a9f979e10e4a37b'}
 
@@ -478,6 +478,11 @@ def main():
                     help='start of the headline window as a fraction of t_end (workloads without t_end: 0)')
     ap.add_argument('--sample-every', type=int, default=25, help='steps between unmet-request samples (0: none)')
     ap.add_argument('--max-patches', type=int, default=0, help='pool capacity (0: every level fully refined)')
+    ap.add_argument('--checkpoint', default=None,
+                    help='write the state reached at the start of the headline window to this file (amr_checkpoint)')
+    ap.add_argument('--restore', default=None,
+                    help='start from this checkpoint (amr_restore) instead of t = 0: the headline window only, no '
+                         'other window and no whole-run figures (for profiling the mid-run state)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-autotune', action='store_true', help='default launch parameters instead of tuned ones')
@@ -529,11 +534,18 @@ def main():
                          'leaf_cell_updates_per_s': 0.5 * (leaves + run.leaves) * N ** w['dim'] * K / (ms / 1000.0),
                          'leaf_patches': run.leaves}
 
-    # 1. t = 0
-    window('t0')
-    # 2. the headline window at window * t_end: state saved for the e2e and FP64 legs
-    if has_end:
-        run.advance_to(args.window * w['t_end'])
+    if args.restore:                          # profiling: straight to the saved state
+        amr.restore(args.restore)
+        run.t = run._refresh()
+        has_end = False
+    else:
+        # 1. t = 0
+        window('t0')
+        # 2. the headline window at window * t_end: state saved for the e2e and FP64 legs
+        if has_end:
+            run.advance_to(args.window * w['t_end'])
+        if args.checkpoint:
+            amr.checkpoint(args.checkpoint)
     mid_state = host_state(amr) if (rank == 0 and (not args.no_e2e or not args.no_compare)) else None
     t_h = run.t
     amr.set_timing(True)
@@ -578,7 +590,7 @@ def main():
         if run.steps_left() >= W + K:
             window('t_end')
         run.advance_to(w['t_end'])
-    whole = run.summary(fe, N)
+    whole = run.summary(fe, N) if not args.restore else None
     learned = None
     if args.flagger == 'mlp':
         c = amr.flag_stats()                      # learned vs plain sensor on the final state, per band cell
@@ -615,7 +627,9 @@ def main():
             'config': {'workload': wl,
                        'timed_window': ('the %d steps after %d warm-up steps from t = %.4g (%.2f t_end), reached by '
                                         'running the problem from t = 0' % (K, W, t_h, t_h / w['t_end']))
-                       if has_end else 'the %d steps after %d warm-up steps from t = 0' % (K, W),
+                       if has_end else ('the %d steps after %d warm-up steps from the checkpoint %s (t = %.4g)'
+                                        % (K, W, args.restore, t_h) if args.restore
+                                        else 'the %d steps after %d warm-up steps from t = 0' % (K, W)),
                        'fine_equivalent_cells': fe, 'patches_per_level': [int(x) for x in ppl],
                        'l2': 'inputs larger than L2 (state arrays of several GB)',
                        'parallelism': 'replicas (dp%d, no data-path collective)' % world,

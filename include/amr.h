@@ -149,7 +149,12 @@ typedef struct {
 #define AMR_TUNE_RESTRICT_GRID 4
 #define AMR_TUNE_CFL_GRID 5
 #define AMR_TUNE_FLAG_GRID 6
-#define AMR_TUNE_N 7
+#define AMR_TUNE_RHS_SHAPE 7    /* tile shape of the fused RHS: index of the compiled (z-chunk depth,
+                                   threads per CTA, resident CTAs per SM) candidate, 0 where only one is
+                                   compiled (FP32 3D 16^3 patches, Rusanov flux: 0 = four planes, 256
+                                   threads, 2 CTAs; 1 = two planes, 256 threads, 3 CTAs; 2 = eight planes,
+                                   512 threads, 1 CTA) */
+#define AMR_TUNE_N 8
 
 void amr_default_options(amr_options_t* opt);
 
@@ -329,8 +334,9 @@ int amr_harvest(amr_ctx* ctx, long* n, double* samples, uint8_t* labels);
 #define AMR_TIMING_SLOTS 10
 int amr_set_timing(amr_ctx* ctx, int enable);
 
-/* Autotuner of the batched step's launch parameters (the tile-free kernels'
- * grids and the ghost-fill work-item size): on the current hierarchy, every
+/* Autotuner of the batched step's launch parameters (the kernels' grids, the
+ * ghost-fill work-item size and the fused RHS's tile shape, "tile shapes and
+ * schedules chosen by an autotuner"): on the current hierarchy, every
  * candidate of each kernel class is timed with CUDA events (best of 3 after a
  * warm-up) on scratch copies of the state (the stage arrays), and the fastest
  * is kept; the captured step graphs are dropped so that the next step uses
@@ -342,6 +348,12 @@ int amr_autotune(amr_ctx* ctx);
  * ms is not NULL, the best time in milliseconds the last autotune measured
  * for each (0: not measured; the two ghost-fill entries share one time). */
 int amr_get_tuning(amr_ctx* ctx, int params[AMR_TUNE_N], float ms[AMR_TUNE_N]);
+/* Set the launch parameters (AMR_TUNE_N ints in AMR_TUNE_* order, as
+ * amr_get_tuning returns them), for instance to reuse an earlier autotune's
+ * choice. CTAs per SM in [1, 64], ghost cells per work item in [32, 4096],
+ * the RHS tile shape below the number of compiled candidates; otherwise
+ * AMR_ERR_ARG and nothing changes. Results do not depend on the choice. */
+int amr_set_tuning(amr_ctx* ctx, const int params[AMR_TUNE_N]);
 int amr_get_timing(amr_ctx* ctx, double ms[AMR_TIMING_SLOTS], int launches[AMR_TIMING_SLOTS]);
 
 /* Counters since amr_init: host-to-device and device-to-host bytes copied,

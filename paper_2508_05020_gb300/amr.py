@@ -45,7 +45,7 @@ class Options(C.Structure):
 FLUX = {'rusanov': 0, 'hllc': 1, 'central': 2, 'hybrid': 3}
 
 TUNE_NAMES = ('ghost_ctas_per_sm', 'ghost_cells_per_item', 'rhs_ctas_per_sm', 'reflux_ctas_per_sm',
-              'restrict_ctas_per_sm', 'cfl_ctas_per_sm', 'flag_ctas_per_sm')
+              'restrict_ctas_per_sm', 'cfl_ctas_per_sm', 'flag_ctas_per_sm', 'rhs_tile_shape')
 
 
 class AMRError(RuntimeError):
@@ -85,6 +85,7 @@ SIGNATURES = [
     ('amr_set_timing', C.c_int, [C.c_void_p, C.c_int]),
     ('amr_autotune', C.c_int, [C.c_void_p]),
     ('amr_get_tuning', C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ('amr_set_tuning', C.c_int, [C.c_void_p, C.c_void_p]),
     ('amr_get_timing', C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ('amr_destroy', None, [C.c_void_p]),
     ('amr_last_error', C.c_char_p, [C.c_void_p]),
@@ -331,6 +332,14 @@ class AMR:
         ms = np.zeros(len(TUNE_NAMES), dtype=np.float32)
         self._check(self.lib.amr_get_tuning(self.ctx, _ptr(p), _ptr(ms)))
         return dict(zip(TUNE_NAMES, p.tolist())), dict(zip(TUNE_NAMES, ms.tolist()))
+
+    def set_tuning(self, params):
+        """Set the launch parameters (a dict by TUNE_NAMES, as tuning() returns
+        them; missing names keep their value) (amr_set_tuning)."""
+        cur, _ = self.tuning()
+        cur.update(params)
+        p = np.array([cur[k] for k in TUNE_NAMES], dtype=np.int32)
+        self._check(self.lib.amr_set_tuning(self.ctx, _ptr(p)))
 
     def set_timing(self, enable=True):
         self._check(self.lib.amr_set_timing(self.ctx, 1 if enable else 0))

@@ -41,8 +41,8 @@ struct amr_ctx {
     int nsm = 1;
     // launch parameters of the batched step (CTAs per SM; ghost cells per work
     // item), the defaults or the autotuner's choice (AMR_TUNE_* order)
-    int tune[AMR_TUNE_N] = {16, 128, 2, 4, 8, 8, 4};
-    float tune_ms[AMR_TUNE_N] = {0, 0, 0, 0, 0, 0, 0};
+    int tune[AMR_TUNE_N] = {16, 128, 2, 4, 8, 8, 4, 0};
+    float tune_ms[AMR_TUNE_N] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     // hierarchy
@@ -881,12 +881,34 @@ int autotune_impl(amr_ctx* c) {
             }
         c->tune_ms[AMR_TUNE_GHOST_GRID] = c->tune_ms[AMR_TUNE_GHOST_CHUNK] = bestv;
     }
-    if (err == cudaSuccess) {                            // fused RHS, stage 1: A -> B
-        const int cands[] = {1, 2, 3, 4};
-        err = tune_one(AMR_TUNE_RHS_GRID, cands, 4, [&](int gr) {
-            ++nk;
-            return Kernels<T>::rhs_stage(g, A, St<T>(c, 0), B, faces, 0, grid_size(c, gr), c->stream, -1);
-        });
+    if (err == cudaSuccess) {                            // fused RHS: tile shape x grid, timed on a stage
+        // that reads only its input (A -> B) and one that also reads U0 and
+        // writes in place (B, U0 = A -> A, as the step's last stage does)
+        const int shapes = Kernels<T>::rhs_shapes(g);
+        float bestv = 1e30f;
+        int best_shape = 0, best_grid = c->tune[AMR_TUNE_RHS_GRID];
+        for (int sh = 0; sh < shapes && err == cudaSuccess; ++sh) {
+            c->grid.rhs_shape = sh;
+            for (int gr = 1; gr <= 4 && err == cudaSuccess; ++gr) {
+                float t = 0.f;
+                err = timed([&]() {
+                    nk += 2;
+                    const cudaError_t e =
+                        Kernels<T>::rhs_stage(g, A, St<T>(c, 0), B, faces, 0, grid_size(c, gr), c->stream, -1);
+                    if (e != cudaSuccess) return e;
+                    return Kernels<T>::rhs_stage(g, B, A, A, faces, 2, grid_size(c, gr), c->stream, -1);
+                }, t);
+                if (t < bestv) {
+                    bestv = t;
+                    best_shape = sh;
+                    best_grid = gr;
+                }
+            }
+        }
+        c->tune[AMR_TUNE_RHS_SHAPE] = best_shape;
+        c->tune[AMR_TUNE_RHS_GRID] = best_grid;
+        c->grid.rhs_shape = best_shape;
+        c->tune_ms[AMR_TUNE_RHS_SHAPE] = c->tune_ms[AMR_TUNE_RHS_GRID] = bestv;
     }
     if (err == cudaSuccess) {                            // reflux of stage 1 into B
         const int cands[] = {1, 2, 4, 8, 16};
@@ -1070,6 +1092,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.ic = ic_id;
     g.flux = c->opt.flux;
     g.theta_sw = c->opt.theta_switch;
+    g.rhs_shape = 0;
     g.mlp_keep = (float)c->opt.mlp_keep_margin;
     g.tc_wait = TC_WAIT_CYCLES;
     g.tc_test = 0;
@@ -1487,6 +1510,25 @@ int amr_harvest(amr_ctx* c, long* n, double* samples, uint8_t* labels) {
 int amr_autotune(amr_ctx* c) {
     GUARD(c);
     return c->precision == 64 ? autotune_impl<double>(c) : autotune_impl<float>(c);
+}
+
+int amr_set_tuning(amr_ctx* c, const int params[AMR_TUNE_N]) {
+    GUARD(c);
+    if (!params) return fail(c, AMR_ERR_ARG, "no parameters");
+    for (int i = 0; i < AMR_TUNE_N; ++i) {
+        const int v = params[i];
+        bool ok;
+        if (i == AMR_TUNE_GHOST_CHUNK) ok = v >= 32 && v <= 4096;
+        else if (i == AMR_TUNE_RHS_SHAPE)
+            ok = v >= 0 && v < (c->precision == 64 ? Kernels<double>::rhs_shapes(c->grid)
+                                                   : Kernels<float>::rhs_shapes(c->grid));
+        else ok = v >= 1 && v <= 64;
+        if (!ok) return fail(c, AMR_ERR_ARG, "launch parameter out of range");
+    }
+    for (int i = 0; i < AMR_TUNE_N; ++i) c->tune[i] = params[i];
+    c->grid.rhs_shape = c->tune[AMR_TUNE_RHS_SHAPE];
+    drop_graphs(c);
+    return AMR_OK;
 }
 
 int amr_get_tuning(amr_ctx* c, int params[AMR_TUNE_N], float ms[AMR_TUNE_N]) {

@@ -55,6 +55,7 @@ struct Grid {
     int ic;
     int flux;                   // AMR_FLUX_*
     double theta_sw;            // AMR_FLUX_HYBRID: threshold of the face's shock sensor
+    int rhs_shape;              // tile-shape candidate of the fused RHS (AMR_TUNE_RHS_SHAPE)
     float mlp_keep;             // learned flagger: a logit above -mlp_keep sets the keep bit
     long long tc_wait;          // learned flagger: limit of a role's pipeline wait (SM cycles)
     int tc_test;                // learned flagger, tests of the timeout path only: nonzero makes
@@ -102,6 +103,8 @@ struct Kernels {
     // ghost cell (what the flag stencils read)
     static cudaError_t ghost_fill(const Grid& g, T* U, int level, double tfrac, int grid,
                                   cudaStream_t s, int one_slot, int chunk = 512, bool stage_only = false);
+    // compiled tile-shape candidates of the fused RHS for this grid and flux
+    static int rhs_shapes(const Grid& g);
     // RHS + SSP-RK3 stage of every patch (or one patch if one_slot >= 0)
     static cudaError_t rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces,
                                  int stage, int grid, cudaStream_t s, int one_slot);

@@ -54,6 +54,17 @@ template <typename T, int D>
 __device__ __forceinline__ void primitives(const T* U, T gm1, T& rho, T* u, T& p, T& Tt) {
     rho = U[0];
     T usq = T(0);
+    if constexpr (sizeof(T) == 4) {                  // FP32: one reciprocal for the D + 1 quotients
+        const float r = __fdividef(1.0f, rho);
+#pragma unroll
+        for (int d = 0; d < D; ++d) u[d] = U[1 + d] * r;
+        usq = u[0] * u[0];
+#pragma unroll
+        for (int d = 1; d < D; ++d) usq = usq + u[d] * u[d];
+        p = gm1 * (U[D + 1] - T(0.5) * rho * usq);
+        Tt = p * r;
+        return;
+    }
 #pragma unroll
     for (int d = 0; d < D; ++d) u[d] = Num<T>::div(U[1 + d], rho);
     usq = u[0] * u[0];
@@ -144,6 +155,57 @@ __device__ __forceinline__ void weno5_pair(float v0, float v1, float v2, float v
         const float s1 = v4 - v2, s2 = 3.0f * v3 - 4.0f * v2 + v1;
         right = combine(q0, qB, qA, c1312 * (t0 * t0) + 0.25f * (s0 * s0), cB + 0.25f * (s1 * s1),
                         cA + 0.25f * (s2 * s2));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packed FP32 (Blackwell f32x2): two independent lanes per instruction.
+// ---------------------------------------------------------------------------
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 f2(float x, float y) { return {make_float2(x, y)}; }
+__device__ __forceinline__ F2 f2s(float s) { return {make_float2(s, s)}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, float s) { return {__fmul2_rn(a.v, make_float2(s, s))}; }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 fma2(F2 a, float s, F2 c) { return {__ffma2_rn(a.v, make_float2(s, s), c.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+
+// weno5_pair<FAST> on two characteristic fields at once (lane x and lane y):
+// the same candidates, smoothness indicators and single-division weights,
+// evaluated with packed instructions; ok is cleared when a weight product of
+// either lane would leave the FP32 range
+__device__ __forceinline__ void weno5_pair_x2(F2 v0, F2 v1, F2 v2, F2 v3, F2 v4, F2 v5, F2& left, F2& right,
+                                              bool& ok) {
+    const float c1312 = 13.0f / 12.0f;
+    const F2 qA = fma2(v3, 0.375f, fma2(v2, 0.75f, v1 * -0.125f));     // left q1 = right q2
+    const F2 qB = fma2(v4, -0.125f, fma2(v3, 0.75f, v2 * 0.375f));     // left q2 = right q1
+    const F2 tA = fma2(v2, -2.0f, v1 + v3), tB = fma2(v3, -2.0f, v2 + v4);
+    const F2 cA = tA * (tA * c1312), cB = tB * (tB * c1312);
+    auto combine = [&ok](F2 q0, F2 q1, F2 q2, F2 b0, F2 b1, F2 b2) {
+        const F2 eps = f2s(1.0e-6f);
+        const F2 e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+        const F2 s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
+        ok = ok && fmaxf(s0.v.x, fmaxf(s1.v.x, s2.v.x)) < 1.0e12f && fmaxf(s0.v.y, fmaxf(s1.v.y, s2.v.y)) < 1.0e12f;
+        const F2 m0 = (s1 * s2) * 0.0625f, m1 = (s0 * s2) * 0.625f, m2 = (s0 * s1) * 0.3125f;
+        const F2 num = fma2(m2, q2, fma2(m1, q1, m0 * q0));
+        const F2 den = m0 + m1 + m2;
+        return f2(__fdividef(num.v.x, den.v.x), __fdividef(num.v.y, den.v.y));
+    };
+    auto beta = [c1312](F2 t, F2 s) { return fma2(t, t * c1312, s * (s * 0.25f)); };
+    {   // left: a = v0, b = v1, c = v2, d = v3, e = v4
+        const F2 q0 = fma2(v2, 1.875f, fma2(v1, -1.25f, v0 * 0.375f));
+        const F2 t0 = fma2(v1, -2.0f, v0 + v2), s0 = fma2(v1, -4.0f, fma2(v2, 3.0f, v0));
+        const F2 s1 = v1 - v3, s2 = fma2(v3, -4.0f, fma2(v2, 3.0f, v4));
+        left = combine(q0, qA, qB, beta(t0, s0), fma2(s1, s1 * 0.25f, cA), fma2(s2, s2 * 0.25f, cB));
+    }
+    {   // right: a = v5, b = v4, c = v3, d = v2, e = v1
+        const F2 q0 = fma2(v3, 1.875f, fma2(v4, -1.25f, v5 * 0.375f));
+        const F2 t0 = fma2(v4, -2.0f, v5 + v3), s0 = fma2(v4, -4.0f, fma2(v3, 3.0f, v5));
+        const F2 s1 = v4 - v2, s2 = fma2(v2, -4.0f, fma2(v3, 3.0f, v1));
+        right = combine(q0, qB, qA, beta(t0, s0), fma2(s1, s1 * 0.25f, cB), fma2(s2, s2 * 0.25f, cA));
     }
 }
 
@@ -295,6 +357,104 @@ __device__ __forceinline__ void face_flux(const T (&p)[6], const T (&un)[6], con
 }
 
 // ---------------------------------------------------------------------------
+// FP32 Rusanov face flux with packed arithmetic: the same steps as face_flux
+// (frozen state, characteristic fields, WENO5-JS left/right, inverse
+// transform, first-order fallback, Rusanov flux). The characteristic fields
+// go through WENO in pairs, (w1, w5) and (w2, w_t1) (w_t2 alone in 3D, w2
+// alone in 1D), and the two face sides' conserved states and fluxes are
+// formed as pairs (left, right).
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ void face_flux_x2(const float (&p)[6], const float (&un)[6],
+                                             const float (&ut)[NT > 0 ? NT : 1][6], const float (&Tt)[6],
+                                             float gamma, float gm1, float (&F)[NT + 3]) {
+    constexpr int NF = NT + 3;
+    const float pbar = 0.5f * (p[2] + p[3]);
+    const float Tbar = 0.5f * (Tt[2] + Tt[3]);
+    const float rbar = __fdividef(pbar, Tbar);
+    const float cbar = sqrtf(gamma * Tbar);
+    const float z = rbar * cbar;
+    const float kap = __fdividef(gm1, gamma * rbar);
+    float wl[NF], wr[NF];
+    bool ok = true;
+    {
+        F2 a[6], b[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            a[k] = f2(fmaf(-z, un[k], p[k]), fmaf(z, un[k], p[k]));                 // (w1, w5)
+            b[k] = f2(fmaf(-kap, p[k], Tt[k]), NT >= 1 ? ut[0][k] : 0.0f);          // (w2, w_t1)
+        }
+        F2 L, R;
+        weno5_pair_x2(a[0], a[1], a[2], a[3], a[4], a[5], L, R, ok);
+        wl[0] = L.v.x; wl[NF - 1] = L.v.y; wr[0] = R.v.x; wr[NF - 1] = R.v.y;
+        if constexpr (NT >= 1) {
+            weno5_pair_x2(b[0], b[1], b[2], b[3], b[4], b[5], L, R, ok);
+            wl[1] = L.v.x; wl[2] = L.v.y; wr[1] = R.v.x; wr[2] = R.v.y;
+        } else {
+            weno5_pair<true>(b[0].v.x, b[1].v.x, b[2].v.x, b[3].v.x, b[4].v.x, b[5].v.x, wl[1], wr[1], ok);
+        }
+        if constexpr (NT == 2) weno5_pair<true>(ut[1][0], ut[1][1], ut[1][2], ut[1][3], ut[1][4], ut[1][5], wl[3],
+                                                wr[3], ok);
+    }
+    if (!ok) {          // a weight product out of range: every field again with three divisions
+        float w[6];
+        bool ok2 = true;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = p[k] - z * un[k];
+        weno5_pair<false>(w[0], w[1], w[2], w[3], w[4], w[5], wl[0], wr[0], ok2);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = Tt[k] - kap * p[k];
+        weno5_pair<false>(w[0], w[1], w[2], w[3], w[4], w[5], wl[1], wr[1], ok2);
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+            weno5_pair<false>(ut[j][0], ut[j][1], ut[j][2], ut[j][3], ut[j][4], ut[j][5], wl[2 + j], wr[2 + j], ok2);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = p[k] + z * un[k];
+        weno5_pair<false>(w[0], w[1], w[2], w[3], w[4], w[5], wl[NF - 1], wr[NF - 1], ok2);
+    }
+    // inverse transform of both sides, as (left, right) pairs
+    const float i2z = __fdividef(0.5f, z);
+    F2 P = f2(0.5f * (wl[0] + wl[NF - 1]), 0.5f * (wr[0] + wr[NF - 1]));
+    F2 UN = f2((wl[NF - 1] - wl[0]) * i2z, (wr[NF - 1] - wr[0]) * i2z);
+    F2 TT = fma2(P, kap, f2(wl[1], wr[1]));
+    F2 UT[NT > 0 ? NT : 1];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) UT[j] = f2(wl[2 + j], wr[2 + j]);
+    const bool bad = !(P.v.x > 0.f) || !(TT.v.x > 0.f) || !(P.v.y > 0.f) || !(TT.v.y > 0.f);
+    if (bad) {
+        P = f2(p[2], p[3]);
+        UN = f2(un[2], un[3]);
+        TT = f2(Tt[2], Tt[3]);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) UT[j] = f2(ut[j][2], ut[j][3]);
+    }
+    // conserved states and Euler fluxes of both sides
+    const F2 RHO = f2(__fdividef(P.v.x, TT.v.x), __fdividef(P.v.y, TT.v.y));
+    const F2 GT = TT * gamma;
+    const F2 C = f2(sqrtf(GT.v.x), sqrtf(GT.v.y));
+    F2 usq = UN * UN;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) usq = fma2(UT[j], UT[j], usq);
+    const F2 E = fma2(RHO * 0.5f, usq, P * (1.0f / gm1));
+    const F2 MN = RHO * UN;
+    F2 U[NF], FF[NF];
+    U[0] = RHO;
+    U[1] = MN;
+    FF[0] = MN;
+    FF[1] = fma2(MN, UN, P);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        U[2 + j] = RHO * UT[j];
+        FF[2 + j] = MN * UT[j];
+    }
+    U[NF - 1] = E;
+    FF[NF - 1] = (E + P) * UN;
+    const float hS = 0.5f * fmaxf(C.v.y + fabsf(UN.v.y), C.v.x + fabsf(UN.v.x));
+#pragma unroll
+    for (int v = 0; v < NF; ++v) F[v] = 0.5f * (FF[v].v.y + FF[v].v.x) - hS * (U[v].v.y - U[v].v.x);
+}
+
+// ---------------------------------------------------------------------------
 // Shock-free face flux (Sec. 3.2, Eq. 8 read as the edge value from node
 // values): p, u_n, u_t, T at the face from pencil nodes 1..4 (cells i-1 ..
 // i+2) by (9 (phi_i + phi_{i+1}) - (phi_{i-1} + phi_{i+2})) / 16; if p or T is
@@ -356,7 +516,8 @@ __device__ __forceinline__ void hybrid_flux(const T (&p)[6], const T (&un)[6], c
         shock = shock || fabs(p[k + 1] - p[k - 1]) > theta * (p[k + 1] + T(2) * p[k] + p[k - 1]);
     }
     if (shock) {
-        face_flux<T, NT, AMR_FLUX_RUSANOV>(p, un, ut, Tt, gamma, gm1, F);
+        if constexpr (sizeof(T) == 4) face_flux_x2<NT>(p, un, ut, Tt, gamma, gm1, F);
+        else face_flux<T, NT, AMR_FLUX_RUSANOV>(p, un, ut, Tt, gamma, gm1, F);
         return;
     }
     T Fl[NF], Fm[NF], Fh[NF];
@@ -901,6 +1062,8 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 T Fp[NT + 3];
                 if constexpr (CEN) central_flux<T, NT>(pp, un, ut, Tt, gm1, Fp);
                 else if constexpr (FLUX == AMR_FLUX_HYBRID) hybrid_flux<T, NT>(pp, un, ut, Tt, gamma, gm1, T(g.theta_sw), Fp);
+                else if constexpr (sizeof(T) == 4 && FLUX == AMR_FLUX_RUSANOV)
+                    face_flux_x2<NT>(pp, un, ut, Tt, gamma, gm1, Fp);
                 else face_flux<T, NT, FLUX>(pp, un, ut, Tt, gamma, gm1, Fp);
                 // pencil order -> global variable order
                 T Fg[NV];

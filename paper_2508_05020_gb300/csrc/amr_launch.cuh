@@ -6,15 +6,28 @@
 
 namespace amr {
 
-// chunk depth (3D) and block size of the fused RHS kernel per precision
-template <typename T, int D, int N> struct RhsCfg {
-    // 3D FP32 with 16^3 patches: four-plane chunks (110 KB of staging and face
-    // buffer), two CTAs of at most 128 registers per SM (fewer face-pass
-    // iterations per plane than two-plane chunks at three CTAs per SM);
-    // otherwise two-plane chunks
+// chunk depth (3D), block size and resident CTAs per SM of the fused RHS
+// kernel: candidate V of a precision, dimension and patch size
+template <typename T, int D, int N, int V = 0> struct RhsCfg {
+    // 3D FP32 with 16^3 patches: four-plane chunks (113 KB of staging and face
+    // buffer), two CTAs of at most 128 registers per SM; otherwise two-plane
+    // chunks
     static constexpr int DZ = D == 3 ? (sizeof(T) == 4 && N == 16 ? 4 : 2) : 1;
     static constexpr int NTH = D == 1 ? 64 : 256;
     static constexpr int MINB = (D == 3 && sizeof(T) == 4) ? (N == 16 ? 2 : 3) : 1;
+};
+// the other candidates of FP32 3D 16^3 patches: two-plane chunks (72 KB) at
+// three CTAs of at most 80 registers per SM (more warps to hide the staging
+// loads), and eight-plane chunks (195 KB) of 512 threads at one CTA per SM
+// (fewer halo planes staged per interior plane)
+template <> struct RhsCfg<float, 3, 16, 1> {
+    static constexpr int DZ = 2, NTH = 256, MINB = 3;
+};
+template <> struct RhsCfg<float, 3, 16, 2> {
+    static constexpr int DZ = 8, NTH = 512, MINB = 1;
+};
+template <typename T, int D, int N, int FLUX> struct RhsShapes {
+    static constexpr int n = (sizeof(T) == 4 && D == 3 && N == 16 && FLUX == AMR_FLUX_RUSANOV) ? 3 : 1;
 };
 
 #define AMR_DISPATCH(g, CALL)                                   \
@@ -32,51 +45,91 @@ template <typename T, int D, int N> struct RhsCfg {
 
 inline double4 d4(const double* v) { return make_double4(v[0], v[1], v[2], v[3]); }
 
+template <typename T, int D, int N, int FLUX, int V>
+static void rhs_launch_v(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
+                         cudaStream_t s, int one_slot) {
+    using C = RhsCfg<T, D, N, V>;
+    k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, FLUX>
+        <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, FLUX>(), s>>>(g, Us, U0, Uout, faces, stage, one_slot);
+}
+
+template <typename T, int D, int N, int FLUX>
+static void rhs_launch_f(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
+                         cudaStream_t s, int one_slot) {
+    if constexpr (RhsShapes<T, D, N, FLUX>::n == 3) {
+        if (g.rhs_shape == 1) return rhs_launch_v<T, D, N, FLUX, 1>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+        if (g.rhs_shape == 2) return rhs_launch_v<T, D, N, FLUX, 2>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+    }
+    rhs_launch_v<T, D, N, FLUX, 0>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+}
+
 template <typename T, int D, int N>
 static cudaError_t rhs_launch(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
                               cudaStream_t s, int one_slot) {
-    using C = RhsCfg<T, D, N>;
     // one instantiation per flux: the Rusanov kernel carries no HLLC code
     if (g.flux == AMR_FLUX_CENTRAL)
-        k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_CENTRAL>
-            <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_CENTRAL>(), s>>>(g, Us, U0, Uout, faces, stage,
-                                                                                   one_slot);
+        rhs_launch_f<T, D, N, AMR_FLUX_CENTRAL>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
     else if (g.flux == AMR_FLUX_HYBRID)
-        k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HYBRID>
-            <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HYBRID>(), s>>>(g, Us, U0, Uout, faces, stage,
-                                                                                  one_slot);
+        rhs_launch_f<T, D, N, AMR_FLUX_HYBRID>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
     else if (g.flux == AMR_FLUX_HLLC)
-        k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>
-            <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HLLC>(), s>>>(g, Us, U0, Uout, faces, stage,
-                                                                                one_slot);
+        rhs_launch_f<T, D, N, AMR_FLUX_HLLC>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
     else
-        k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_RUSANOV>
-            <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_RUSANOV>(), s>>>(g, Us, U0, Uout, faces, stage,
-                                                                                   one_slot);
+        rhs_launch_f<T, D, N, AMR_FLUX_RUSANOV>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
     return cudaGetLastError();
+}
+
+template <typename T, int D, int N, int FLUX, int V>
+static cudaError_t rhs_prepare_v() {
+    using C = RhsCfg<T, D, N, V>;
+    return cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, FLUX>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rhs_smem_bytes<T, D, N, C::DZ, FLUX>());
+}
+
+template <typename T, int D, int N, int FLUX>
+static cudaError_t rhs_prepare_f() {
+    cudaError_t e = rhs_prepare_v<T, D, N, FLUX, 0>();
+    if constexpr (RhsShapes<T, D, N, FLUX>::n == 3) {
+        if (e == cudaSuccess) e = rhs_prepare_v<T, D, N, FLUX, 1>();
+        if (e == cudaSuccess) e = rhs_prepare_v<T, D, N, FLUX, 2>();
+    }
+    return e;
 }
 
 template <typename T, int D, int N>
 static cudaError_t rhs_prepare() {
-    using C = RhsCfg<T, D, N>;
-    cudaError_t e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_RUSANOV>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_RUSANOV>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HLLC>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HLLC>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_HYBRID>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_HYBRID>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, AMR_FLUX_CENTRAL>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)rhs_smem_bytes<T, D, N, C::DZ, AMR_FLUX_CENTRAL>());
+    cudaError_t e = rhs_prepare_f<T, D, N, AMR_FLUX_RUSANOV>();
+    if (e == cudaSuccess) e = rhs_prepare_f<T, D, N, AMR_FLUX_HLLC>();
+    if (e == cudaSuccess) e = rhs_prepare_f<T, D, N, AMR_FLUX_HYBRID>();
+    if (e == cudaSuccess) e = rhs_prepare_f<T, D, N, AMR_FLUX_CENTRAL>();
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_flag_plain<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)flag_smem_bytes<T, D, N>());
+}
+
+template <typename T, int D, int N>
+static int rhs_shapes_of(int flux) {
+    switch (flux) {
+    case AMR_FLUX_RUSANOV: return RhsShapes<T, D, N, AMR_FLUX_RUSANOV>::n;
+    case AMR_FLUX_HLLC: return RhsShapes<T, D, N, AMR_FLUX_HLLC>::n;
+    case AMR_FLUX_HYBRID: return RhsShapes<T, D, N, AMR_FLUX_HYBRID>::n;
+    default: return RhsShapes<T, D, N, AMR_FLUX_CENTRAL>::n;
+    }
+}
+
+template <typename T>
+int Kernels<T>::rhs_shapes(const Grid& g) {
+    switch (g.dim * 100 + g.N) {
+    case 108: return rhs_shapes_of<T, 1, 8>(g.flux);
+    case 116: return rhs_shapes_of<T, 1, 16>(g.flux);
+    case 132: return rhs_shapes_of<T, 1, 32>(g.flux);
+    case 208: return rhs_shapes_of<T, 2, 8>(g.flux);
+    case 216: return rhs_shapes_of<T, 2, 16>(g.flux);
+    case 232: return rhs_shapes_of<T, 2, 32>(g.flux);
+    case 308: return rhs_shapes_of<T, 3, 8>(g.flux);
+    case 316: return rhs_shapes_of<T, 3, 16>(g.flux);
+    default: return 1;
+    }
 }
 
 template <typename T>
