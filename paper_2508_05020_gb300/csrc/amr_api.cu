@@ -1066,7 +1066,11 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.N = patch_size;
     g.L = levels;
     g.nv = c->nv;
-    g.SX = (S + 7) / 8 * 8;
+    {
+        const int per32 = 32 / (c->precision == 64 ? 8 : 4);       // elements per 32-byte sector
+        g.XP = (per32 - G % per32) % per32;
+        g.SX = (g.XP + S + 7) / 8 * 8;
+    }
     g.SY = dim >= 2 ? S : 1;
     g.SZ = dim == 3 ? S : 1;
     g.slot_elems = (long long)g.SX * g.SY * g.SZ;

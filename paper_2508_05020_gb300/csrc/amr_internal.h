@@ -3,10 +3,14 @@
 // Device layout of the patch pool (the patch region of Sec. 4.2, which spans
 // interior and ghost points): one array per state,
 //     U[slot][var][z][y][x],  z in [0, SZ), y in [0, SY), x in [0, SX),
-// with SZ = N + 6 in 3D (else 1), SY = N + 6 in 2D/3D (else 1), and the x
-// pitch SX = N + 6 rounded up to 8 elements so every row starts on a 16-byte
-// boundary (32-byte for FP64). Local cell index l in [-3, N+3) maps to slot
-// index l + 3. A patch's data is contiguous (nv * SZ * SY * SX elements).
+// with SZ = N + 6 in 3D (else 1), SY = N + 6 in 2D/3D (else 1). A row holds
+// XP pad elements, then the N + 6 cells of the row (3 ghosts, N interior, 3
+// ghosts), then pad up to the x pitch SX, a multiple of 8 elements. XP puts
+// the first interior cell of every row on a 32-byte boundary (FP32: XP = 5,
+// FP64: XP = 1), so a row's N interior cells fill whole 32-byte sectors and
+// are read as aligned 16-byte vectors. Local cell index l in [-3, N+3) maps to
+// slot index l + 3 (the x element l + 3 + XP). A patch's data is contiguous
+// (nv * SZ * SY * SX elements).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -41,6 +45,7 @@ struct DevTime {
 struct Grid {
     int dim, N, L, nv;
     int SX, SY, SZ;
+    int XP;                     // pad elements before the first ghost of a row
     long long slot_elems;       // SZ * SY * SX
     long long patch_elems;      // nv * slot_elems
     int cap;                    // pool capacity (slots)

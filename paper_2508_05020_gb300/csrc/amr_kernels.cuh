@@ -27,9 +27,12 @@ template <> struct Num<float> {
     __device__ __forceinline__ static float sqr(float a) { return sqrtf(a); }
 };
 
-template <int N> struct PatchShape {
+template <typename T, int N> struct PatchShape {
     static constexpr int S = N + 2 * G;                  // cells per slot side
-    static constexpr int SX = (S + 7) / 8 * 8;           // padded x pitch
+    static constexpr int PER32 = 32 / (int)sizeof(T);    // elements per 32-byte sector
+    static constexpr int XP = (PER32 - G % PER32) % PER32;   // pad before the first ghost of a row
+    static constexpr int SX = (XP + S + 7) / 8 * 8;      // padded x pitch
+    static_assert((XP + G) % PER32 == 0, "interior rows start on a 32-byte boundary");
 };
 
 __device__ __forceinline__ int floordiv(int a, int b) {
@@ -39,8 +42,31 @@ __device__ __forceinline__ int floordiv(int a, int b) {
 
 __device__ __forceinline__ long long slot_index(const Grid& g, int slot, int v, int sz, int sy, int sx) {
     return (long long)slot * g.patch_elems + (long long)v * g.slot_elems +
-           ((long long)sz * g.SY + sy) * g.SX + sx;
+           ((long long)sz * g.SY + sy) * g.SX + sx + g.XP;
 }
+
+// 16-byte vector of VE consecutive elements (FP32: 4, FP64: 2) at an aligned address
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    static constexpr int VE = 4;
+    __device__ __forceinline__ static void load(const float* p, float (&o)[4]) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+    __device__ __forceinline__ static void store(float* p, const float (&o)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct Vec16<double> {
+    static constexpr int VE = 2;
+    __device__ __forceinline__ static void load(const double* p, double (&o)[2]) {
+        const double2 t = *reinterpret_cast<const double2*>(p);
+        o[0] = t.x; o[1] = t.y;
+    }
+    __device__ __forceinline__ static void store(double* p, const double (&o)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    }
+};
 
 // slot coordinate of local index l in an active (d < D) or inactive dimension
 template <int D>
@@ -938,11 +964,14 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
             // centre planes (3D) or the whole slot (1D/2D): full rows; a row
             // outside the interior along y comes whole from its y source (its
             // x ghosts are edge cells, which no face reads)
-            constexpr int NXV = (C::QX + VE - 1) / VE;
+            // aligned vectors of the padded row covering slot x in [0, QX):
+            // vector xv starts at slot x xv VE - XP (negative: the row pad)
+            constexpr int XP = PatchShape<T, N>::XP;
+            constexpr int XV0 = XP / VE, NXV = (XP + C::QX + VE - 1) / VE - XV0;
             for (int iv = threadIdx.x; iv < NXV * C::QY * C::QZ; iv += NTH) {
                 const int xv = iv % NXV, qy = (iv / NXV) % C::QY, qz = iv / (NXV * C::QY);
                 const int sz = D == 3 ? z0 + G + qz : 0;
-                const int x0 = xv * VE;
+                const int x0 = (xv + XV0) * VE - XP;
                 T Uv[NV][VE];
                 const int ly = qy - G;
                 if (D >= 2 && (ly < 0 || ly >= N)) {
@@ -974,15 +1003,17 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 }
 #pragma unroll
                 for (int e = 0; e < VE; ++e) {
-                    const int qx = xv * VE + e;
-                    if (qx < C::QX) stage(Uv, e, (qz * C::QY + qy) * C::QX + qx);
+                    const int qx = x0 + e;
+                    if (qx >= 0 && qx < C::QX) stage(Uv, e, (qz * C::QY + qy) * C::QX + qx);
                 }
             }
             if constexpr (D == 3) {
-                // halo planes: interior x in [G, G + N) from aligned vectors,
-                // from the z source when the plane lies outside the interior
-                constexpr int HX0 = (G / VE) * VE;
-                constexpr int NHV = (G + N - HX0 + VE - 1) / VE;
+                // halo planes: interior x in [G, G + N), which starts on a
+                // 32-byte boundary, as N / VE aligned vectors, from the z
+                // source when the plane lies outside the interior
+                constexpr int HX0 = G;
+                constexpr int NHV = N / VE;
+                static_assert(N % VE == 0, "interior rows are whole vectors");
                 int szm, dzm, szp, dzp;
                 across(2, 0, szm, dzm);
                 across(2, 1, szp, dzp);
@@ -1248,11 +1279,15 @@ __global__ void __launch_bounds__(256) k_reflux(Grid g, T* Uout, const T* __rest
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int one_slot) {
-    // thread <-> coarse cell; the 2^d children of every variable are read
-    // before anything is written
+    // thread <-> CP coarse cells adjacent in x (FP32: 2, FP64: 1), whose
+    // children of each (y, z) offset are VE consecutive fine cells of a row:
+    // one aligned 16-byte vector (interior rows start on a 32-byte boundary)
     constexpr int NV = D + 2;
+    constexpr int VE = 16 / (int)sizeof(T);
+    constexpr int CP = VE / 2;
     constexpr int H = N / 2;
-    constexpr int HC = D == 1 ? H : (D == 2 ? H * H : H * H * H);
+    constexpr int HC = (D == 1 ? H : (D == 2 ? H * H : H * H * H)) / CP;
+    constexpr int NYZ = 1 << (D - 1);                    // child (y, z) offsets
     constexpr int NCH = 1 << D;
     if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
     const int lo = g.level_off[level], hi = g.level_off[level + 1];
@@ -1269,45 +1304,53 @@ __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int o
             atomicOr(&g.time->err, ERR_MESH);
             continue;
         }
-        const int cx = ci % H, cy = D >= 2 ? (ci / H) % H : 0, cz = D == 3 ? ci / (H * H) : 0;
-        T f[NV][NCH];
+        constexpr int HX = H / CP;
+        const int cx = (ci % HX) * CP, cy = D >= 2 ? (ci / HX) % H : 0, cz = D == 3 ? ci / (HX * H) : 0;
+        const int ox = (g.coord[slot * 3 + 0] & 1) * H, oy = D >= 2 ? (g.coord[slot * 3 + 1] & 1) * H : 0,
+                  oz = D == 3 ? (g.coord[slot * 3 + 2] & 1) * H : 0;
+        T f[NV][NYZ][VE];                                  // [var][(az, ay)][fine x]
 #pragma unroll
         for (int v = 0; v < NV; ++v)
 #pragma unroll
-            for (int k = 0; k < NCH; ++k) {                // child order: z, then y, then x
-                const int ax = k & 1, ay = D >= 2 ? (k >> 1) & 1 : 0, az = D == 3 ? k >> 2 : 0;
-                f[v][k] = U[slot_index(g, slot, v, D == 3 ? 2 * cz + az + G : 0, D >= 2 ? 2 * cy + ay + G : 0,
-                                       2 * cx + ax + G)];
+            for (int k = 0; k < NYZ; ++k) {
+                const int ay = D >= 2 ? k & 1 : 0, az = D == 3 ? k >> 1 : 0;
+                Vec16<T>::load(U + slot_index(g, slot, v, D == 3 ? 2 * cz + az + G : 0, D >= 2 ? 2 * cy + ay + G : 0,
+                                              2 * cx + G),
+                               f[v][k]);
             }
-        const int ox = (g.coord[slot * 3 + 0] & 1) * H, oy = D >= 2 ? (g.coord[slot * 3 + 1] & 1) * H : 0,
-                  oz = D == 3 ? (g.coord[slot * 3 + 2] & 1) * H : 0;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            T mean;
-            if constexpr (sizeof(T) == 4) {
-                // FP32 fields: the sum carried as an unevaluated pair s + e
-                // (Knuth's TwoSum adds each child without error into s and
-                // collects the rounding errors in e), rounded once; equal to
-                // the FP64 sum rounded to FP32 up to near-ties, at FP32 cost
-                float sum = f[v][0], err = 0.0f;
+        for (int v = 0; v < NV; ++v)
 #pragma unroll
-                for (int k = 1; k < NCH; ++k) {
-                    const float a = f[v][k];
-                    const float t = __fadd_rn(sum, a);
-                    const float bv = __fsub_rn(t, sum);
-                    const float e = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bv)), __fsub_rn(a, bv));
-                    sum = t;
-                    err = __fadd_rn(err, e);
+            for (int q = 0; q < CP; ++q) {
+                // the coarse cell's children in lexicographic z, y, x order
+                T ch[NCH];
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) ch[k] = f[v][k >> 1][2 * q + (k & 1)];
+                T mean;
+                if constexpr (sizeof(T) == 4) {
+                    // FP32 fields: the sum carried as an unevaluated pair s + e
+                    // (Knuth's TwoSum adds each child without error into s and
+                    // collects the rounding errors in e), rounded once; equal to
+                    // the FP64 sum rounded to FP32 up to near-ties, at FP32 cost
+                    float sum = ch[0], err = 0.0f;
+#pragma unroll
+                    for (int k = 1; k < NCH; ++k) {
+                        const float a = ch[k];
+                        const float t = __fadd_rn(sum, a);
+                        const float bv = __fsub_rn(t, sum);
+                        const float e = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bv)), __fsub_rn(a, bv));
+                        sum = t;
+                        err = __fadd_rn(err, e);
+                    }
+                    mean = __fmul_rn(__fadd_rn(sum, err), (float)scale);
+                } else {
+                    double acc = (double)ch[0];
+#pragma unroll
+                    for (int k = 1; k < NCH; ++k) acc = acc + (double)ch[k];
+                    mean = T(acc * scale);
                 }
-                mean = __fmul_rn(__fadd_rn(sum, err), (float)scale);
-            } else {
-                double acc = (double)f[v][0];
-#pragma unroll
-                for (int k = 1; k < NCH; ++k) acc = acc + (double)f[v][k];
-                mean = T(acc * scale);
+                U[slot_index(g, par, v, D == 3 ? oz + cz + G : 0, D >= 2 ? oy + cy + G : 0, ox + cx + q + G)] = mean;
             }
-            U[slot_index(g, par, v, D == 3 ? oz + cz + G : 0, D >= 2 ? oy + cy + G : 0, ox + cx + G)] = mean;
-        }
     }
 }
 
@@ -1320,9 +1363,12 @@ template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
     // the running maximum is kept in the storage precision (exact: the
     // maximum of FP32 values converts to the maximum of their FP64 images)
-    // and turned into FP64 once per CTA
+    // and turned into FP64 once per CTA. A work item is VE consecutive
+    // interior cells of a row, read as one aligned 16-byte vector per
+    // variable (interior rows start on a 32-byte boundary)
     constexpr int NV = D + 2;
-    constexpr int NC = D == 1 ? N : (D == 2 ? N * N : N * N * N);
+    constexpr int VE = Vec16<T>::VE;
+    constexpr int NC = (D == 1 ? N : (D == 2 ? N * N : N * N * N)) / VE;
     if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
     const int npatch = one_slot >= 0 ? 1 : g.counts[1];
     const long long total = (long long)npatch * NC;
@@ -1330,27 +1376,36 @@ __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
     const T gm1 = T(g.gamma) - T(1);
     T lmax = T(0);
     bool bad = false;
-#pragma unroll 4
+#pragma unroll 2
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
          it += (long long)gridDim.x * blockDim.x) {
         const int pi = (int)(it / NC);
         const int ci = (int)(it - (long long)pi * NC);
         const int slot = one_slot >= 0 ? one_slot : g.leaf_list[pi];
         const int lev = g.level[slot];
-        const int x = ci % N, y = D >= 2 ? (ci / N) % N : 0, z = D == 3 ? ci / (N * N) : 0;
-        T Uc[NV];
+        const int x = (ci % (N / VE)) * VE, y = D >= 2 ? (ci / (N / VE)) % N : 0, z = D == 3 ? ci / ((N / VE) * N) : 0;
+        T Uv[NV][VE];
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-            Uc[v] = U[slot_index(g, slot, v, D == 3 ? z + G : 0, D >= 2 ? y + G : 0, x + G)];
-        T rho, u[D], p, Tt;
-        primitives<T, D>(Uc, gm1, rho, u, p, Tt);
-        if (!(rho > T(0)) || !(p > T(0))) bad = true;
-        const T c = Num<T>::sqr(Num<T>::div(gamma * p, rho));
-        T lam = Num<T>::div(fabs(u[0]) + c, T(g.dx[lev][0]));
+            Vec16<T>::load(U + slot_index(g, slot, v, D == 3 ? z + G : 0, D >= 2 ? y + G : 0, x + G), Uv[v]);
+        T idx[D];
 #pragma unroll
-        for (int d = 1; d < D; ++d) lam = lam + Num<T>::div(fabs(u[d]) + c, T(g.dx[lev][d]));
-        if (!((double)lam <= 1.0e300)) bad = true;       // FP32: not finite; FP64: out of range
-        else lmax = lmax > lam ? lmax : lam;
+        for (int d = 0; d < D; ++d) idx[d] = T(g.dx[lev][d]);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) {
+            T Uc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Uc[v] = Uv[v][e];
+            T rho, u[D], p, Tt;
+            primitives<T, D>(Uc, gm1, rho, u, p, Tt);
+            if (!(rho > T(0)) || !(p > T(0))) bad = true;
+            const T c = Num<T>::sqr(Num<T>::div(gamma * p, rho));
+            T lam = Num<T>::div(fabs(u[0]) + c, idx[0]);
+#pragma unroll
+            for (int d = 1; d < D; ++d) lam = lam + Num<T>::div(fabs(u[d]) + c, idx[d]);
+            if (!((double)lam <= 1.0e300)) bad = true;       // FP32: not finite; FP64: out of range
+            else lmax = lmax > lam ? lmax : lam;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1379,9 +1434,16 @@ __global__ void __launch_bounds__(256) k_cfl(Grid g, const T* U, int one_slot) {
 // precision from 16-byte vector loads of the slot rows, and a patch's flag is
 // the OR over its items.
 // ---------------------------------------------------------------------------
-template <int D, int N> struct FlagStage {
+template <typename T, int D, int N> struct FlagStage {
     static constexpr int S = N + 2 * G;
-    static constexpr int SXP = PatchShape<N>::SX;            // padded x pitch of the slot
+    static constexpr int XP = PatchShape<T, N>::XP;          // pad before the first ghost of a row
+    // staged rows: the aligned 16-byte vectors of the slot row that cover
+    // slot x in [0, S), from vector XV0 on; staged x = slot x + XO
+    static constexpr int VE = 16 / (int)sizeof(T);
+    static constexpr int XV0 = XP / VE;
+    static constexpr int NXV = (XP + S + VE - 1) / VE - XV0;
+    static constexpr int SXP = NXV * VE;                     // x pitch of the staged rows
+    static constexpr int XO = XP - XV0 * VE;
     static constexpr int B = N + 4;                         // band cells per dimension
     static constexpr int NSLAB = D == 3 ? 4 : 1;
     static constexpr int DZB = D == 3 ? B / 4 : 1;           // band planes per slab
@@ -1392,15 +1454,15 @@ template <int D, int N> struct FlagStage {
 };
 
 template <typename T, int D, int N>
-constexpr size_t flag_smem_bytes() { return 2 * sizeof(T) * FlagStage<D, N>::NS; }
+constexpr size_t flag_smem_bytes() { return 2 * sizeof(T) * FlagStage<T, D, N>::NS; }
 
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* anyflag) {
-    using F = FlagStage<D, N>;
+    using F = FlagStage<T, D, N>;
     constexpr int NV = D + 2;
     constexpr int B = F::B;
     constexpr int NB = D == 1 ? B : (D == 2 ? B * B : B * B * F::DZB);     // band cells per item
-    constexpr int VE = 16 / sizeof(T), NXV = F::SXP / VE;
+    constexpr int VE = F::VE, NXV = F::NXV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* srho = reinterpret_cast<T*>(smem_raw);
     T* sp = srho + F::NS;
@@ -1418,7 +1480,7 @@ __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* any
             T Uv[NV][VE];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const T* src = U + slot_index(g, slot, v, sz0 + z, y, xv * VE);
+                const T* src = U + slot_index(g, slot, v, sz0 + z, y, xv * VE - F::XO);   // aligned
                 if constexpr (sizeof(T) == 4) {
                     const float4 q = *reinterpret_cast<const float4*>(src);
                     Uv[v][0] = q.x; Uv[v][1] = q.y; Uv[v][2] = q.z; Uv[v][3] = q.w;
@@ -1452,7 +1514,7 @@ __global__ void __launch_bounds__(256) k_flag_plain(Grid g, const T* U, int* any
                 indom = indom && Gd >= 0 && Gd < g.ext[lev][d] * N;
             }
             if (!indom) continue;
-            const int i0 = ((D == 3 ? l[2] + G - sz0 : 0) * F::SY + sc<D>(1, l[1])) * F::SXP + sc<D>(0, l[0]);
+            const int i0 = ((D == 3 ? l[2] + G - sz0 : 0) * F::SY + sc<D>(1, l[1])) * F::SXP + sc<D>(0, l[0]) + F::XO;
             const T r0 = srho[i0], p0 = sp[i0];
             bool f = false;
 #pragma unroll

@@ -367,16 +367,20 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
             // primitives of the slab and its halo: local z in [zb0 - 2, zb0 + DZ + 2),
             // loaded as 16-byte vectors along x (slot rows are 16-byte aligned)
             {
+                // aligned vectors of the padded row covering slot x in [0, S):
+                // vector xv starts at slot x xv VE - XP (negative: the row pad)
                 constexpr int VE = 16 / sizeof(T);
-                constexpr int NXV = (P::S + VE - 1) / VE;
+                constexpr int XP = PatchShape<T, N>::XP;
+                constexpr int XV0 = XP / VE, NXV = (XP + P::S + VE - 1) / VE - XV0;
                 constexpr int NVEC = NXV * P::PY * P::PZ;
                 for (int iv = ptid; iv < NVEC; iv += P::NPROD) {
                     const int xv = iv % NXV, py = (iv / NXV) % P::PY, pz = iv / (NXV * P::PY);
                     const int sz = D == 3 ? zb0 - 2 + pz + G : 0;
+                    const int x0 = (xv + XV0) * VE - XP;
                     T Uv[D + 2][VE];
 #pragma unroll
                     for (int v = 0; v < D + 2; ++v) {
-                        const T* src = U + slot_index(g, slot, v, sz, py, xv * VE);
+                        const T* src = U + slot_index(g, slot, v, sz, py, x0);
                         if constexpr (sizeof(T) == 4) {
                             const float4 q = *reinterpret_cast<const float4*>(src);
                             Uv[v][0] = q.x; Uv[v][1] = q.y; Uv[v][2] = q.z; Uv[v][3] = q.w;
@@ -387,8 +391,8 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
                     }
 #pragma unroll
                     for (int e = 0; e < VE; ++e) {
-                        const int px = xv * VE + e;
-                        if (px >= P::S) break;
+                        const int px = x0 + e;
+                        if (px < 0 || px >= P::S) continue;
                         T Uc[D + 2];
 #pragma unroll
                         for (int v = 0; v < D + 2; ++v) Uc[v] = Uv[v][e];
