@@ -42,19 +42,20 @@ FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 WEIGHTS_DIR = os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights')
 
 # DRAM bytes of one stage-1 k_rhs launch (ncu, dram__bytes_read.sum +
-# dram__bytes_write.sum) on the default workload right after its initial
-# hierarchy (1408 leaf patches), valid while the sources of the kernel (the
-# regions below: EOS, WENO5, face fluxes, the kernel and its launch) hash as
-# recorded. Leaves are independent work items, so a launch over another
-# hierarchy of the same workload moves this figure per leaf times its leaves.
-RHS_TRAFFIC = {'bytes': 320362496 + 152754688, 'leaves': 1408, 'workload': 'blast3d', 'base': 128, 'levels': 3,
+# dram__bytes_write.sum) on the default workload at t_end / 2 (4656 leaf
+# patches, the state a checkpoint of the default run holds at the start of its
+# headline window), valid while the sources of the kernel (the regions below:
+# EOS, WENO5, face fluxes, the kernel and its launch) hash as recorded. Leaves
+# are independent work items, so a launch over another hierarchy of the same
+# workload moves this figure per leaf times its leaves.
+RHS_TRAFFIC = {'bytes': 1121615360 + 381913344, 'leaves': 4656, 'workload': 'blast3d', 'base': 128, 'levels': 3,
                'regions': [('paper_2508_05020_gb300/csrc/amr_kernels.cuh', 'template <typename T> struct Num;',
                             '// Metadata of one patch staged'),
                            ('paper_2508_05020_gb300/csrc/amr_kernels.cuh', '// K4: fused right-hand side',
                             '// K5: coarse-fine flux correction'),
                            ('paper_2508_05020_gb300/csrc/amr_launch.cuh', 'template <typename T, int D, int N, int V = 0> struct RhsCfg',
                             'template <typename T>\ncudaError_t Kernels<T>::prepare')],
-               'hash': '3a9f979e10e4a37b'}
+               'hash': 'e1b1a18fc97e51d7'}
 
 
 def rhs_source_hash():
@@ -610,8 +611,8 @@ def main():
         roof = {'bound': 'alu', 'kernel': 'k_rhs (fused %s + SSP-RK3 stage)' % scheme,
                 'achieved': achieved, 'peak': fp32_peak, 'unit': 'TFLOP/s', 'frac': achieved / fp32_peak,
                 'traffic': rhs_traffic(args.workload, args.base, args.levels, leaf_patches(w, ppl)),
-                'traffic_unit': 'DRAM bytes per launch (stage 1; ncu capture at 1408 leaf patches scaled to '
-                                'this launch\'s %d)' % leaf_patches(w, ppl),
+                'traffic_unit': 'DRAM bytes per launch (stage 1; ncu capture at %d leaf patches scaled to '
+                                'this launch\'s %d)' % (RHS_TRAFFIC['leaves'], leaf_patches(w, ppl)),
                 'avg_launch_ms': rhs_ms, 'flop_per_launch': flops_rhs,
                 'peak_basis': 'FP32 ALU: 152 SMs x 128 lanes x 2 FLOP x %.0f MHz (of the measured maximum SM clock)'
                               % sm_max}
