@@ -1034,6 +1034,17 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
             }
         }
         __syncthreads();
+        // stages 2-3 read U0 in the update: its interior rows of this chunk
+        // into L2 now (last written a step ago, so not in L2), while the
+        // face passes run
+        if (stage > 0) {
+            constexpr int ROWS = NV * C::CZ * C::CY;
+            for (int r = threadIdx.x; r < ROWS; r += NTH) {
+                const int v = r / (C::CZ * C::CY), rz = (r / C::CY) % C::CZ, ry = r % C::CY;
+                const T* a = U0 + slot_index(g, slot, v, D == 3 ? z0 + G + rz : 0, D >= 2 ? ry + G : 0, G);
+                asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
+            }
+        }
         T R[CPT][NV];
         // two phases: the x and y faces of the chunk in one pass (an even
         // share of faces per thread), then the z faces; each phase ends with
