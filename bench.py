@@ -676,8 +676,17 @@ def main():
 
 
 def level0_rho(amr):
-    _, x = amr.get_level(0)
-    return x[:, 0]
+    """Density of level 0 (the conservative average of the whole hierarchy)
+    as one array over the level's cells, (z, y, x) order."""
+    import numpy as np
+    coords, x = amr.get_level(0)
+    d, N = amr.dim, amr.N
+    ext = [int(coords[:, k].max()) + 1 if k < d else 1 for k in range(3)]
+    out = np.zeros(tuple(ext[k] * (N if k < d else 1) for k in (2, 1, 0)))
+    for c, patch in zip(coords, x[:, 0]):
+        sl = tuple(slice(int(c[k]) * N, int(c[k]) * N + N) if k < d else slice(None) for k in (2, 1, 0))
+        out[sl] = patch.reshape(out[sl].shape)
+    return out
 
 
 def l1_rel(a, b):
@@ -750,7 +759,18 @@ def compare(AMR, w, args, fe, K_r, weights_name, whole, mid_state, value):
         ref.regrid()
     rho64 = level0_rho(ref)
     ref.close()
-    l1 = {}
+    # every cell refined to the finest level (thresholds below zero flag every
+    # cell), FP64, the same dt sequence: the finest level is the uniform grid
+    # at the finest spacing, the discrete solution every AMR mesh approximates
+    # (uniform-fine equivalence, bit for bit in the oracle's pins), and its
+    # level 0 is that solution averaged over each level-0 cell
+    uni = AMR(dict(wr, theta_rho=-1.0, theta_p=-1.0), precision=64, flagger='plain', autotune=False)
+    for dt in dts:
+        uni.step(dt=dt, sync=False)
+    rho_uni = level0_rho(uni)
+    r_fine = 2 ** (w['levels'] - 1)
+    uni.close()
+    l1 = {'fp64_plain_every_1': {'l1_rho_vs_uniform_fine': l1_rel(rho64, rho_uni)}}
     for label, flagger, wname, K in VARIANTS:
         wts = load_weights(wname, w['dim']) if flagger == 'mlp' else None
         a = AMR(wr, precision=32, flagger=flagger, mlp_weights=wts, mlp_keep_margin=args.keep_margin)
@@ -761,7 +781,8 @@ def compare(AMR, w, args, fe, K_r, weights_name, whole, mid_state, value):
                 a.regrid()
             if (i + 1) % args.sample_every == 0:
                 unmet.append(a.plain_requests())
-        l1[label] = {'l1_rho': l1_rel(level0_rho(a), rho64),
+        r0 = level0_rho(a)
+        l1[label] = {'l1_rho': l1_rel(r0, rho64), 'l1_rho_vs_uniform_fine': l1_rel(r0, rho_uni),
                      'unmet_plain_requests_per_step': float(np.mean(unmet)) if unmet else None}
         a.close()
         if label == head_label:
@@ -770,10 +791,12 @@ def compare(AMR, w, args, fe, K_r, weights_name, whole, mid_state, value):
         l1['fp32_headline'] = None
     out['l1_rho_at_t_end_reduced'] = l1
     out['l1_note'] = ('relative L1 of rho on level 0 (the conservative average of the whole hierarchy) at t_end = %g '
-                      'after %d steps, against the batched FP64 plain run (regrid every step) of the same problem at '
-                      '32^%d base cells, every run with that run\'s dt sequence; FP32 plain every step isolates the '
-                      'FP32 storage and arithmetic (same meshes), the other rows add their mesh choices'
-                      % (w['t_end'], len(dts), w['dim']))
+                      'after %d steps of the same problem at 32^%d base cells, every run with the dt sequence of the '
+                      'batched FP64 plain run (regrid every step): l1_rho against that run (FP32 plain every step '
+                      'isolates the FP32 storage and arithmetic, the other rows add their mesh choices), '
+                      'l1_rho_vs_uniform_fine against the FP64 uniform grid at the finest spacing (%d^%d cells, every '
+                      'cell refined) averaged to level 0: the discretisation error a mesh choice leaves'
+                      % (w['t_end'], len(dts), w['dim'], 32 * r_fine, w['dim']))
     return out
 
 

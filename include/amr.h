@@ -124,13 +124,18 @@ typedef struct {
                              gives the central schemes for shock-free flows and WENO for flows with
                              shocks, the per-face switch is this library's extension) */
     double mlp_keep_margin;  /* H >= 0, learned flagger only: a patch requests refinement if a band
-                                cell's logit is > 0 and blocks the coarsening of its parent if one
-                                is > -H (hysteresis between the two decisions; 0: the same test) */
+                                cell's logit is > -R (R = mlp_refine_margin, default 0) and blocks the
+                                coarsening of its parent if one is > -H (hysteresis between the two
+                                decisions; H = R: the same test) */
     double theta_switch;  /* AMR_FLUX_HYBRID only: a face i+1/2 takes the WENO5 + Rusanov flux if, at
                              any pencil node k = i-1 .. i+2 and for phi = rho (= p / T) or p,
                              |phi_{k+1} - phi_{k-1}| > theta_switch (phi_{k+1} + 2 phi_k + phi_{k-1})
                              (the relative jump of the refinement sensor along the face normal);
                              else the central value. Default 0.05 */
+    double mlp_refine_margin;  /* R in [0, H], learned flagger only: a patch requests refinement if a
+                                  band cell's logit is > -R (0: the network's own decision, logit > 0;
+                                  a larger R refines more, trading precision for recall against the
+                                  plain sensor); H is mlp_keep_margin */
 } amr_options_t;
 
 #define AMR_FLUX_RUSANOV 0

@@ -180,11 +180,12 @@ def cell_stencils(orc, key):
     return R, Us, P, np.stack([cx, cy, cz], axis=1)
 
 
-def make_flagger(params, gamma, keep_margin=0.0):
+def make_flagger(params, gamma, keep_margin=0.0, refine_margin=0.0):
     """A per-patch flagger for Oracle.flag_override: refine if any in-domain
-    band cell [-1, N]^d has a logit > 0; with keep_margin H > 0 it returns
-    (refine, keep), keep (which blocks the coarsening of the parent) if any
-    such cell has a logit > -H (a hysteresis between refining and coarsening)."""
+    band cell [-1, N]^d has a logit > -R (R = refine_margin, 0 by default);
+    with keep_margin H > R it returns (refine, keep), keep (which blocks the
+    coarsening of the parent) if any such cell has a logit > -H (a hysteresis
+    between refining and coarsening)."""
     def flag(orc, key):
         R, Us, P, cells = cell_stencils(orc, key)
         X = features(R, Us, P, gamma)
@@ -197,9 +198,10 @@ def make_flagger(params, gamma, keep_margin=0.0):
                 continue
             g = c[d] * orc.N + cells[:, d]
             ok &= (g >= 0) & (g < ext[d] * orc.N)
-        if keep_margin > 0.0:
-            return bool(np.any((z > 0.0) & ok)), bool(np.any((z > -keep_margin) & ok))
-        return bool(np.any((z > 0.0) & ok))
+        refine = bool(np.any((z > -refine_margin) & ok))
+        if keep_margin > refine_margin:
+            return refine, bool(np.any((z > -keep_margin) & ok))
+        return refine
     return flag
 
 

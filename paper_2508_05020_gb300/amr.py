@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ('dev_alloc', ALLOC_FN), ('dev_free', FREE_FN), ('user', C.c_void_p),
                 ('stream', C.c_void_p), ('mlp_weights', C.c_void_p), ('mlp_n_weights', C.c_long),
                 ('autotune', C.c_int), ('flux', C.c_int),
-                ('mlp_keep_margin', C.c_double), ('theta_switch', C.c_double)]
+                ('mlp_keep_margin', C.c_double), ('theta_switch', C.c_double), ('mlp_refine_margin', C.c_double)]
 
 FLUX = {'rusanov': 0, 'hllc': 1, 'central': 2, 'hybrid': 3}
 
@@ -145,7 +145,7 @@ class _TorchMemory:
 
 def make_options(precision=64, cfl=0.5, t_end=0.0, flagger='plain', theta_rho=0.05, theta_p=0.05,
                  max_patches=0, seed=0, amp=0.01, mode='batched', use_graph=True, torch_memory=True,
-                 autotune=False, flux='rusanov', mlp_keep_margin=0.0, theta_switch=0.05):
+                 autotune=False, flux='rusanov', mlp_keep_margin=0.0, theta_switch=0.05, mlp_refine_margin=0.0):
     """Options struct plus the objects that must outlive it."""
     lib = load()
     o = Options()
@@ -165,6 +165,7 @@ def make_options(precision=64, cfl=0.5, t_end=0.0, flagger='plain', theta_rho=0.
     o.flux = FLUX[flux]
     o.mlp_keep_margin = mlp_keep_margin
     o.theta_switch = theta_switch
+    o.mlp_refine_margin = mlp_refine_margin
     keep = []
     if torch_memory:
         import torch
@@ -181,7 +182,8 @@ class AMR:
     """One hierarchy on the current CUDA device (see include/amr.h)."""
 
     def __init__(self, w, precision=64, flagger='plain', mode='batched', use_graph=True,
-                 max_patches=0, torch_memory=True, mlp_weights=None, autotune=False, mlp_keep_margin=0.0):
+                 max_patches=0, torch_memory=True, mlp_weights=None, autotune=False, mlp_keep_margin=0.0,
+                 mlp_refine_margin=0.0):
         self.lib = load()
         self.w = dict(w)
         self.dim = w['dim']
@@ -198,7 +200,7 @@ class AMR:
         self.opt, self._keep = make_options(precision, w['cfl'], w['t_end'], flagger, w['theta_rho'],
                                             w['theta_p'], max_patches, w.get('seed', 0), w.get('amp', 0.01),
                                             mode, use_graph, torch_memory, autotune, w.get('flux', 'rusanov'),
-                                            mlp_keep_margin, w.get('theta_switch', 0.05))
+                                            mlp_keep_margin, w.get('theta_switch', 0.05), mlp_refine_margin)
         if mlp_weights is not None:
             self._w_host = np.ascontiguousarray(mlp_weights, dtype=np.float32)
             self.opt.mlp_weights = _ptr(self._w_host)

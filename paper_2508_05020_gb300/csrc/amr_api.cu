@@ -47,7 +47,9 @@ struct amr_ctx {
     bool own_stream = false;
     // hierarchy
     Mesh mesh;
-    std::unordered_map<uint64_t, int> slot_of;
+    std::unordered_map<uint64_t, int> slot_of;   // key -> slot (when the mesh has no dense index)
+    std::vector<int> slot_at;                      // position -> slot, -1 if none (dense index)
+    int slot_hi = 0;                               // one past the highest slot handed out
     std::vector<uint64_t> key_of;        // slot -> packed key (valid if used)
     std::vector<char> used;
     std::set<int> free_slots;
@@ -184,8 +186,23 @@ struct MetaLayout {
 };
 
 int slot_lookup(const amr_ctx* c, const Key& k) {
+    if (c->mesh.dense()) {
+        const long long p = c->mesh.pos(k);
+        return p < 0 ? -1 : c->slot_at[(size_t)p];
+    }
     auto it = c->slot_of.find(pack(k));
     return it == c->slot_of.end() ? -1 : it->second;
+}
+
+void slot_map_clear(amr_ctx* c) {
+    c->slot_of.clear();
+    if (c->mesh.dense()) c->slot_at.assign((size_t)c->mesh.positions(), -1);
+    else c->slot_at.clear();
+}
+
+void slot_map_set(amr_ctx* c, const Key& k, int s) {
+    if (c->mesh.dense()) c->slot_at[(size_t)c->mesh.pos(k)] = s;
+    else c->slot_of[pack(k)] = s;
 }
 
 // Every metadata table and work list of the host mirror (meta_h and the host
@@ -196,9 +213,8 @@ void fill_tables(amr_ctx* c, const std::vector<Key>& created) {
     const Mesh& m = c->mesh;
     c->canon = m.canonical();
     c->canon_slot.resize(c->canon.size());
-    std::fill(h + ml.nbr, h + ml.nbr + (size_t)NBR * c->cap, -2);
-    std::fill(h + ml.child, h + ml.child + 8 * (size_t)c->cap, -1);
-    std::fill(h + ml.reflux_fine, h + ml.reflux_fine + 24 * (size_t)c->cap, -1);
+    // only the entries of the slots in use are written (every per-slot entry
+    // of each of them, below); the kernels read no other slot's entries
     for (int l = 0; l <= MAXL; ++l) c->level_off_h[l] = 0;
     c->leaf_slots.clear();
     c->reflux_slots.clear();
@@ -215,10 +231,21 @@ void fill_tables(amr_ctx* c, const std::vector<Key>& created) {
         h[ml.parent + s] = k.l > 0 ? slot_lookup(c, Mesh::parent(k)) : -1;
         const bool has_ch = m.has_children(k);
         int pf = has_ch ? 1 : 0;
-        if (has_ch) {
-            const auto ch = m.children(k);
-            for (size_t j = 0; j < ch.size(); ++j) h[ml.child + 8 * s + j] = slot_lookup(c, ch[j]);
+        {
+            int* chs = h + ml.child + 8 * (size_t)s;
+            for (int j = 0; j < 8; ++j) chs[j] = -1;
+            if (has_ch) {                                  // (z, y, x)-lexicographic, x fastest
+                const int nz = c->dim == 3 ? 2 : 1, ny = c->dim >= 2 ? 2 : 1;
+                int j = 0;
+                for (int sz = 0; sz < nz; ++sz)
+                    for (int sy = 0; sy < ny; ++sy)
+                        for (int sx = 0; sx < 2; ++sx)
+                            chs[j++] = slot_lookup(c, Key{k.l + 1, 2 * k.x + sx, c->dim >= 2 ? 2 * k.y + sy : 0,
+                                                          c->dim == 3 ? 2 * k.z + sz : 0});
+            }
         }
+        int* nb = h + ml.nbr + (size_t)NBR * s;
+        for (int e = 0; e < NBR; ++e) nb[e] = -2;                // offsets in unused dimensions
         const int rz = c->dim == 3 ? 1 : 0, ry = c->dim >= 2 ? 1 : 0;
         for (int oz = -rz; oz <= rz; ++oz)
             for (int oy = -ry; oy <= ry; ++oy)
@@ -227,7 +254,7 @@ void fill_tables(amr_ctx* c, const std::vector<Key>& created) {
                     int v;
                     if (!m.wrap(q)) v = -2;
                     else v = slot_lookup(c, q);
-                    h[ml.nbr + (size_t)NBR * s + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = v;
+                    nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = v;
                 }
         // coarse-fine faces: a leaf whose neighbour has children keeps its face
         // flux and takes the fine mean; a fine patch without a same-level
@@ -296,8 +323,23 @@ void fill_tables(amr_ctx* c, const std::vector<Key>& created) {
 int rebuild_tables(amr_ctx* c, const std::vector<Key>& created) {
     fill_tables(c, created);
     const MetaLayout ml(c->cap);
-    const size_t bytes = ml.total * sizeof(int);
-    CK(cudaMemcpyAsync(c->meta_d, c->meta_h, bytes, cudaMemcpyHostToDevice, c->stream), "upload tables");
+    // the written parts only: per-slot tables up to the highest slot handed
+    // out, the lists up to their lengths
+    const size_t hi = (size_t)c->slot_hi, n_all = c->canon.size();
+    const size_t n_new = (size_t)c->meta_h[ml.counts + 3];
+    const size_t parts[][2] = {{ml.level, hi}, {ml.coord, 3 * hi}, {ml.nbr, NBR * hi}, {ml.parent, hi},
+                               {ml.child, 8 * hi}, {ml.pflag, hi}, {ml.all_list, n_all},
+                               {ml.level_off, MAXL + 1}, {ml.leaf_list, (size_t)c->n_leaf}, {ml.counts, 4},
+                               {ml.reflux_list, (size_t)c->n_reflux}, {ml.reflux_fine, 24 * (size_t)c->n_reflux},
+                               {ml.new_list, n_new}};
+    size_t bytes = 0;
+    for (const auto& pt : parts) {
+        if (!pt[1]) continue;
+        CK(cudaMemcpyAsync(c->meta_d + pt[0], c->meta_h + pt[0], pt[1] * sizeof(int), cudaMemcpyHostToDevice,
+                           c->stream),
+           "upload tables");
+        bytes += pt[1] * sizeof(int);
+    }
     c->h2d += (long long)bytes;
     // the pinned mirror is rewritten by the next rebuild: wait for the copy
     CK(cudaStreamSynchronize(c->stream), "upload tables");
@@ -307,20 +349,22 @@ int rebuild_tables(amr_ctx* c, const std::vector<Key>& created) {
 // give slots to new keys (lowest free first, canonical order), free deleted ones
 void assign_slots(amr_ctx* c, const std::vector<Key>& created, const std::vector<Key>& deleted) {
     for (const auto& k : deleted) {
-        auto it = c->slot_of.find(pack(k));
-        if (it == c->slot_of.end()) continue;
-        c->used[it->second] = 0;
-        c->free_slots.insert(it->second);
-        c->slot_of.erase(it);
+        const int s = slot_lookup(c, k);
+        if (s < 0) continue;
+        c->used[s] = 0;
+        c->free_slots.insert(s);
+        if (c->mesh.dense()) c->slot_at[(size_t)c->mesh.pos(k)] = -1;
+        else c->slot_of.erase(pack(k));
     }
     std::vector<Key> cr = created;
     std::sort(cr.begin(), cr.end(), canon_less);
     for (const auto& k : cr) {
         const int s = *c->free_slots.begin();
         c->free_slots.erase(c->free_slots.begin());
-        c->slot_of[pack(k)] = s;
+        slot_map_set(c, k, s);
         c->key_of[s] = pack(k);
         c->used[s] = 1;
+        c->slot_hi = std::max(c->slot_hi, s + 1);
     }
 }
 
@@ -642,7 +686,7 @@ int regrid_finish(amr_ctx* c, bool resample_ic, bool* void_step, bool* changed) 
     r = set_rejected(c, -1);
     if (r) return r;
     Range tables("regrid: tables and new patches");
-    c->mesh.patches.swap(m2.patches);
+    c->mesh.swap_patches(m2);
     assign_slots(c, created, deleted);
     const auto t2 = std::chrono::steady_clock::now();
     r = rebuild_tables(c, created);
@@ -735,7 +779,7 @@ int get_level_impl(amr_ctx* c, int level, int* n_out, int* coords, double* data)
 template <typename T>
 int set_state_impl(amr_ctx* c, int n, const int* levels, const int* coords, const double* data, double t) {
     Mesh m2(c->dim, c->mesh.base, c->mesh.periodic, c->L - 1);
-    m2.patches.clear();
+    m2.clear();
     std::vector<Key> keys;
     for (int i = 0; i < n; ++i) {
         Key k{levels[i], coords[i * c->dim], c->dim >= 2 ? coords[i * c->dim + 1] : 0,
@@ -745,14 +789,15 @@ int set_state_impl(amr_ctx* c, int n, const int* levels, const int* coords, cons
             const int x = coords[i * c->dim + d];
             if (x < 0 || x >= m2.extent(k.l, d)) return fail(c, AMR_ERR_MESH, "patch outside the domain");
         }
-        if (!m2.patches.insert(pack(k)).second) return fail(c, AMR_ERR_MESH, "duplicate patch");
+        if (!m2.insert(k)) return fail(c, AMR_ERR_MESH, "duplicate patch");
         keys.push_back(k);
     }
     const std::string why = m2.check();
     if (!why.empty()) return fail(c, AMR_ERR_MESH, why);
     if ((int)keys.size() > c->cap) return fail(c, AMR_ERR_POOL, "patch pool capacity exceeded");
-    c->mesh.patches.swap(m2.patches);
-    c->slot_of.clear();
+    c->mesh.swap_patches(m2);
+    slot_map_clear(c);
+    c->slot_hi = 0;
     c->free_slots.clear();
     for (int s = 0; s < c->cap; ++s) {
         c->free_slots.insert(s);
@@ -1002,6 +1047,8 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     if (c->opt.theta_switch != c->opt.theta_switch) return bad("theta_switch is NaN");
     if (!(c->opt.mlp_keep_margin >= 0.0) || !(c->opt.mlp_keep_margin < 1.0e30))
         return bad("mlp_keep_margin must be in [0, 1e30)");
+    if (!(c->opt.mlp_refine_margin >= 0.0) || !(c->opt.mlp_refine_margin <= c->opt.mlp_keep_margin))
+        return bad("mlp_refine_margin must be in [0, mlp_keep_margin]");
     int bp[3] = {1, 1, 1};
     bool periodic[3] = {false, false, false};
     for (int d = 0; d < dim; ++d) {
@@ -1098,6 +1145,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     g.theta_sw = c->opt.theta_switch;
     g.rhs_shape = 0;
     g.mlp_keep = (float)c->opt.mlp_keep_margin;
+    g.mlp_refine = (float)c->opt.mlp_refine_margin;
     g.tc_wait = TC_WAIT_CYCLES;
     g.tc_test = 0;
     g.seed = c->opt.seed;
@@ -1216,6 +1264,8 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     c->used.assign(c->cap, 0);
     c->key_of.assign(c->cap, 0);
     for (int s = 0; s < c->cap; ++s) c->free_slots.insert(s);
+    slot_map_clear(c);
+    c->slot_hi = 0;
     std::vector<Key> base = c->mesh.canonical();
     assign_slots(c, base, {});
     int r = rebuild_tables(c, base);
@@ -1646,7 +1696,7 @@ int amr_mesh_tables(int dim, const int base_patches[3], const int periodic[3], i
     t.L = max_level + 1;
     t.cap = n;
     t.mesh = Mesh(dim, bp, per, max_level);
-    t.mesh.patches.clear();
+    t.mesh.clear();
     for (int i = 0; i < n; ++i) {
         const int* r = keys + 4 * (size_t)i;
         const Key k{r[0], r[1], r[2], r[3]};
@@ -1654,14 +1704,16 @@ int amr_mesh_tables(int dim, const int base_patches[3], const int periodic[3], i
         const int cc[3] = {k.x, k.y, k.z};
         for (int d = 0; d < 3; ++d)
             if (cc[d] < 0 || cc[d] >= t.mesh.extent(k.l, d)) return AMR_ERR_ARG;
-        if (!t.mesh.patches.insert(pack(k)).second) return AMR_ERR_MESH;
+        if (!t.mesh.insert(k)) return AMR_ERR_MESH;
     }
     if (!t.mesh.check().empty()) return AMR_ERR_MESH;
     const MetaLayout ml(n);
     *n_ints = (long long)ml.total;
     if (!tables) return AMR_OK;
     const std::vector<Key> all = t.mesh.canonical();
-    for (int i = 0; i < n; ++i) t.slot_of[pack(all[i])] = i;    // slot = canonical index
+    slot_map_clear(&t);
+    for (int i = 0; i < n; ++i) slot_map_set(&t, all[i], i);    // slot = canonical index
+    t.slot_hi = n;
     std::vector<int> h(ml.total, 0);
     t.meta_h = h.data();
     fill_tables(&t, {});

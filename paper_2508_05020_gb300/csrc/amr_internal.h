@@ -62,6 +62,7 @@ struct Grid {
     double theta_sw;            // AMR_FLUX_HYBRID: threshold of the face's shock sensor
     int rhs_shape;              // tile-shape candidate of the fused RHS (AMR_TUNE_RHS_SHAPE)
     float mlp_keep;             // learned flagger: a logit above -mlp_keep sets the keep bit
+    float mlp_refine;           // learned flagger: a logit above -mlp_refine sets the refine bit
     long long tc_wait;          // learned flagger: limit of a role's pipeline wait (SM cycles)
     int tc_test;                // learned flagger, tests of the timeout path only: nonzero makes
                                 //   the MMA thread withhold the epilogue's accumulator signal, so

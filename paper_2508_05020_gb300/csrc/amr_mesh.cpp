@@ -13,10 +13,17 @@ Mesh::Mesh(int dim_, const int base_[3], const bool periodic_[3], int max_level_
         base[d] = d < dim ? base_[d] : 1;
         periodic[d] = d < dim ? periodic_[d] : false;
     }
+    long long o = 0;
+    for (int l = 0; l <= max_level; ++l) {
+        lvl_off[l] = o;
+        o += (long long)extent(l, 0) * extent(l, 1) * extent(l, 2);
+    }
+    for (int l = max_level + 1; l < 9; ++l) lvl_off[l] = o;
+    if (o <= kDenseMax) present.assign((size_t)o, 0);
     // R1: the level-0 Cartesian layout is the permanent scaffold
     for (int z = 0; z < base[2]; ++z)
         for (int y = 0; y < base[1]; ++y)
-            for (int x = 0; x < base[0]; ++x) patches.insert(pack(Key{0, x, y, z}));
+            for (int x = 0; x < base[0]; ++x) insert(Key{0, x, y, z});
 }
 
 bool Mesh::wrap(Key& k) const {
@@ -63,6 +70,18 @@ std::vector<Key> Mesh::children(const Key& k) const {
 std::vector<Key> Mesh::canonical() const {
     std::vector<Key> out;
     out.reserve(patches.size());
+    if (dense() && (long long)patches.size() * 16 >= positions()) {
+        // the position order is the canonical order
+        for (int l = 0; l <= max_level; ++l) {
+            const int ex = extent(l, 0), ey = extent(l, 1), ez = extent(l, 2);
+            long long p = lvl_off[l];
+            for (int z = 0; z < ez; ++z)
+                for (int y = 0; y < ey; ++y)
+                    for (int x = 0; x < ex; ++x, ++p)
+                        if (present[(size_t)p]) out.push_back(Key{l, x, y, z});
+        }
+        return out;
+    }
     for (uint64_t v : patches) out.push_back(unpack(v));
     std::sort(out.begin(), out.end(), canon_less);
     return out;
@@ -119,7 +138,7 @@ void Mesh::refine_patch(const Key& k, std::vector<Key>& created) {
         if (!exists(q)) refine_patch(parent(q), created);
     }
     for (const auto& c : children(k)) {
-        if (patches.insert(pack(c)).second) created.push_back(c);
+        if (insert(c)) created.push_back(c);
     }
 }
 
@@ -166,7 +185,7 @@ std::vector<Key> Mesh::coarsen(const std::vector<Key>& candidates, const std::un
         if (accept.empty()) break;
         for (const auto& k : accept)
             for (const auto& c : children(k)) {
-                patches.erase(pack(c));
+                erase(c);
                 deleted.push_back(c);
             }
         pending.swap(rest);
@@ -212,11 +231,11 @@ extern "C" int amr_mesh_close(int dim, const int base_patches[3], const int peri
         per[d] = periodic[d] != 0;
     }
     amr::Mesh m(dim, base, per, max_level);
-    m.patches.clear();
+    m.clear();
     for (int i = 0; i < n; ++i) {
         Key k;
         if (!key_of_row(m, keys + 4 * (size_t)i, k)) return AMR_ERR_ARG;
-        if (!m.patches.insert(amr::pack(k)).second) return AMR_ERR_MESH;
+        if (!m.insert(k)) return AMR_ERR_MESH;
     }
     if (!m.check().empty()) return AMR_ERR_MESH;
     std::vector<Key> req(n_refine), cand(n_candidates);

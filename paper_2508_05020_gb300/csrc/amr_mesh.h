@@ -3,6 +3,7 @@
 // refinement) and the coarsening rule of Sec. 4.3.
 #pragma once
 #include <cstdint>
+#include <algorithm>
 #include <string>
 #include <unordered_set>
 #include <vector>
@@ -43,17 +44,63 @@ public:
     int dim = 1, max_level = 0;
     int base[3] = {1, 1, 1};
     bool periodic[3] = {false, false, false};
+    // the patch set; read freely, change only through insert / erase / clear /
+    // swap_patches, which keep the position index below in step
     std::unordered_set<uint64_t> patches;
+    // Dense position index of every patch position a level can hold: level
+    // by level, then lexicographic (z, y, x), i.e. the canonical order. Used
+    // (present non-empty) when all positions fit in kDenseMax; a membership
+    // test is then one array read.
+    static constexpr long long kDenseMax = 1ll << 26;
+    long long lvl_off[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    std::vector<uint8_t> present;
 
     int extent(int level, int d) const { return d < dim ? base[d] << level : 1; }
-    bool exists(const Key& k) const { return patches.count(pack(k)) != 0; }
+    // position of k in the dense index, -1 outside the levels or the domain
+    long long pos(const Key& k) const {
+        if (k.l < 0 || k.l > max_level) return -1;
+        const int ex = extent(k.l, 0), ey = extent(k.l, 1), ez = extent(k.l, 2);
+        if (k.x < 0 || k.x >= ex || k.y < 0 || k.y >= ey || k.z < 0 || k.z >= ez) return -1;
+        return lvl_off[k.l] + ((long long)k.z * ey + k.y) * ex + k.x;
+    }
+    long long positions() const { return lvl_off[max_level + 1]; }
+    bool dense() const { return !present.empty(); }
+    bool exists(const Key& k) const {
+        if (dense()) {
+            const long long p = pos(k);
+            return p >= 0 && present[(size_t)p];
+        }
+        return patches.count(pack(k)) != 0;
+    }
+    // false if k is present already (or, with the dense index, outside it)
+    bool insert(const Key& k) {
+        const long long p = dense() ? pos(k) : 0;
+        if (p < 0 || !patches.insert(pack(k)).second) return false;
+        if (dense()) present[(size_t)p] = 1;
+        return true;
+    }
+    bool erase(const Key& k) {
+        if (!patches.erase(pack(k))) return false;
+        if (dense()) present[(size_t)pos(k)] = 0;
+        return true;
+    }
+    void clear() {
+        patches.clear();
+        std::fill(present.begin(), present.end(), 0);
+    }
+    void swap_patches(Mesh& o) {
+        patches.swap(o.patches);
+        present.swap(o.present);
+    }
     // wrap coordinates across periodic dimensions; false if outside the domain
     bool wrap(Key& k) const;
     // in-domain Moore-neighbour positions (wrapped), excluding the patch itself
     std::vector<Key> moore(const Key& k) const;
     std::vector<Key> children(const Key& k) const;   // (z, y, x)-lexicographic, x fastest
     static Key parent(const Key& k) { return Key{k.l - 1, k.x >> 1, k.y >> 1, k.z >> 1}; }
-    bool has_children(const Key& k) const { return exists(children(k)[0]); }
+    bool has_children(const Key& k) const {     // the first child (all or none exist)
+        return exists(Key{k.l + 1, 2 * k.x, dim >= 2 ? 2 * k.y : 0, dim == 3 ? 2 * k.z : 0});
+    }
     bool is_leaf(const Key& k) const { return !has_children(k); }
     std::vector<Key> canonical() const;
 

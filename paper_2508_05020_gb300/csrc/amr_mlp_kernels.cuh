@@ -559,8 +559,8 @@ __global__ void __launch_bounds__(MlpBand<D, N>::NTH, 1)
                 const int Gd = g.coord[slot * 3 + dd] * N + lc[dd];
                 indom = indom && Gd >= 0 && Gd < g.ext[lev][dd] * N;
             }
-            // bit 0: refine (logit > 0); bit 1: keep, blocks coarsening (logit > -H)
-            const bool m = indom && z > 0.f;
+            // bit 0: refine (logit > -R); bit 1: keep, blocks coarsening (logit > -H)
+            const bool m = indom && z > -g.mlp_refine;
             const bool k = indom && z > -g.mlp_keep;
             const int bits = (__any_sync(0xffffffffu, m) ? 1 : 0) | (__any_sync(0xffffffffu, k) ? 2 : 0);
             if (bits && lane == 0) atomicOr(&anyflag[slot], bits);

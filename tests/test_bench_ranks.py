@@ -101,3 +101,24 @@ def test_run_planning_and_traffic_scaling():
         b = bench.RHS_TRAFFIC['bytes']
         assert bench.rhs_traffic('blast3d', 0, 0, bench.RHS_TRAFFIC['leaves']) == b
         assert bench.rhs_traffic('blast3d', 0, 0, 2 * bench.RHS_TRAFFIC['leaves']) == 2 * b
+
+
+def test_level0_assembly():
+    # level 0's patches placed by their coordinates into one (z, y, x) array
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Fake:
+        dim, N = 3, 2
+
+        def get_level(self, l):
+            coords = np.array([[x, y, z] for z in range(2) for y in range(3) for x in range(2)])
+            data = np.zeros((len(coords), 5, 2, 2, 2))
+            for i, (x, y, z) in enumerate(coords):
+                data[i, 0] = 100 * z + 10 * y + x
+            return coords, data
+    a = bench.level0_rho(Fake())
+    assert a.shape == (4, 6, 4)
+    assert a[3, 5, 3] == 100 * 1 + 10 * 2 + 1 and a[0, 0, 0] == 0 and a[2, 1, 1] == 100
+    assert bench.l1_rel(a + 1.0, a + 1.0) == 0.0

@@ -104,3 +104,22 @@ def test_plain_requests_single_level_and_plain_context():
     r, _ = p.requests()
     assert p.plain_requests() == len(r)
     p.close()
+
+
+def test_refine_margin_refines_at_least_as_much():
+    """The learned flags' refine margin R (refine where a band logit is above
+    -R): the learned cells found per band cell (true and false positives
+    against the plain sensor) and the patches after a regrid do not shrink as
+    R grows, and R = H refines every leaf whose keep bit is set."""
+    from paper_2508_05020_gb300.amr import AMR
+    w = workload('blast3d', base_cells=(32, 32, 32))
+    out = []
+    for R in (0.0, 2.0, 12.0):
+        a = AMR(w, precision=32, flagger='mlp', mlp_weights=_weights(3), mlp_keep_margin=12.0, mlp_refine_margin=R)
+        c = a.flag_stats()
+        n = int(sum(a.diag()[2]))
+        out.append((int(c[0] + c[1]), n))
+        a.close()
+    assert out[0][0] <= out[1][0] <= out[2][0]
+    assert out[0][1] <= out[1][1] <= out[2][1]
+    assert out[2][0] > out[0][0]

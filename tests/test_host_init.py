@@ -22,7 +22,8 @@ def init(amr, w, levels=None, ratio=2, patch=None, ic=None, gamma=None, **opt):
     lib = amr.load()
     o, keep = amr.make_options(torch_memory=False, cfl=w['cfl'], t_end=w['t_end'],
                                **{k: v for k, v in opt.items() if k in ('precision', 'flagger', 'max_patches', 'mode',
-                                                                       'flux', 'mlp_keep_margin', 'theta_switch')})
+                                                                       'flux', 'mlp_keep_margin', 'theta_switch',
+                                                                       'mlp_refine_margin')})
     for k in ('raw_flagger', 'raw_mode', 'raw_precision', 'raw_flux', 'raw_cfl'):
         if k in opt:
             setattr(o, k[4:], opt[k])
@@ -82,7 +83,9 @@ def test_invalid_arguments_are_refused_before_any_device_call(amr):
 def test_options_out_of_range_are_refused(amr):
     w = workload('sod')
     for kw, word in ((dict(raw_flux=4), 'flux'), (dict(mlp_keep_margin=-1.0), 'margin'),
-                     (dict(theta_switch=float('nan')), 'theta_switch')):
+                     (dict(theta_switch=float('nan')), 'theta_switch'),
+                     (dict(mlp_keep_margin=2.0, mlp_refine_margin=3.0), 'mlp_refine_margin'),
+                     (dict(mlp_refine_margin=-1.0), 'mlp_refine_margin')):
         rc, msg = init(amr, w, **kw)
         assert rc == -1 and word in msg, (kw, rc, msg)
 

@@ -117,6 +117,40 @@ def test_keep_margin_hysteresis():
     assert not out[1e9][1]
 
 
+def test_refine_margin_widens_refinement():
+    # refinement requests grow with the refine margin R (a leaf refines when
+    # a band logit is above -R): nested sets, R = 0 the default flagger,
+    # strictly more leaves refined at a wider margin, every leaf below the
+    # finest level once R exceeds every logit's distance below 0; and a
+    # network whose every logit is exactly -3 (zero weights, output bias -3)
+    # refines nothing at R = 2.9 and every such leaf at R = 3.1
+    from oracle.amr import Oracle
+    from synth import workload
+    w = workload('riemann2d', base_cells=(48, 48, 1), patch=8, levels=2)
+    r = Oracle(w)
+    r.step()
+    r.regrid()
+    below = {k for k in r.mesh.canonical() if r.mesh.is_leaf(k) and k[0] < r.L - 1}
+    assert below, 'no leaf below the finest level: the case does not test refinement'
+    p = mlp_init(5, mlp.k_in(2))
+    p['b3'][:] = -3.0
+    q = mlp.unflatten(mlp.flatten(p), mlp.k_in(2))
+
+    def refined(flagger):
+        r.flag_override = flagger
+        rr, _, _ = r.requests()
+        return set(rr)
+    out = {R: refined(mlp.make_flagger(q, 1.4, keep_margin=1e9, refine_margin=R)) for R in (0.0, 2.0, 3.0, 1e9)}
+    assert out[0.0] == refined(mlp.make_flagger(q, 1.4))
+    assert out[0.0] <= out[2.0] <= out[3.0] <= out[1e9]
+    assert out[3.0] > out[0.0]
+    assert len(out[1e9]) == len(below)
+    zero = {k: np.zeros_like(v) for k, v in q.items()}
+    zero['b3'][:] = -3.0
+    assert not refined(mlp.make_flagger(zero, 1.4, keep_margin=6.0, refine_margin=2.9))
+    assert len(refined(mlp.make_flagger(zero, 1.4, keep_margin=6.0, refine_margin=3.1))) == len(below)
+
+
 def test_adam_steps_from_the_definition():
     # with a constant gradient the bias-corrected moments are g and g^2 at
     # every step, so each update is -lr g / (|g| + eps); a zero gradient
