@@ -968,6 +968,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
             // vector xv starts at slot x xv VE - XP (negative: the row pad)
             constexpr int XP = PatchShape<T, N>::XP;
             constexpr int XV0 = XP / VE, NXV = (XP + C::QX + VE - 1) / VE - XV0;
+#pragma unroll 2
             for (int iv = threadIdx.x; iv < NXV * C::QY * C::QZ; iv += NTH) {
                 const int xv = iv % NXV, qy = (iv / NXV) % C::QY, qz = iv / (NXV * C::QY);
                 const int sz = D == 3 ? z0 + G + qz : 0;
@@ -1017,6 +1018,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 int szm, dzm, szp, dzp;
                 across(2, 0, szm, dzm);
                 across(2, 1, szp, dzp);
+#pragma unroll 2
                 for (int iv = threadIdx.x; iv < NHV * N * 2 * G; iv += NTH) {
                     const int xv = iv % NHV, hy = (iv / NHV) % N, zh = iv / (NHV * N);
                     const int sz = z0 + (zh < G ? zh : zh + DZ);
