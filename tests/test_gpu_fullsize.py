@@ -2,7 +2,8 @@
 16^3 patches), the double Mach reflection (512 x 128 base, 4 levels) and the
 four-quadrant problem (256^2 base, 3 levels), in the launch configuration
 bench.py times (batched step in a CUDA graph, autotuned launch parameters,
-amr_advance; FP32 fields with the learned flags and keep margin 12). The
+amr_advance; FP32 fields with the learned flags and keep margin 12, the
+blast also with the bench's lookahead network regridding every 4 steps). The
 oracle cannot run these sizes, so it checks sampled outputs it computes one
 by one (per-patch flags and requests from the GPU's own state) and
 properties that hold at any size (conservation, mesh validity, FP32 against
@@ -33,11 +34,6 @@ def cuda():
 
 
 FULL = ['blast3d', 'dmr', 'riemann2d']
-
-
-def weights(dim):
-    return np.load(os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights',
-                                'indicator_d%d.npy' % dim)).astype(np.float32)
 
 
 def bf16(x):
@@ -140,18 +136,23 @@ def max_logit_bf16(r, q, key):
     return float(np.max(z[ok]))
 
 
-@pytest.mark.parametrize('name', FULL)
-def test_fullsize_learned_requests_match_oracle_on_sampled_patches(name):
-    # the bench's configuration: FP32, learned flags, keep margin, autotuned,
-    # after timed-style steps; refine bits of sampled leaves below the finest
-    # level and candidate status of sampled parents, except where a logit lies
-    # within the BF16 margin of its threshold
+@pytest.mark.parametrize('name,wname,K', [('blast3d', 'indicator_d{d}_diag_k4.npy', 4),
+                                           ('blast3d', 'indicator_d{d}.npy', 1),
+                                           ('dmr', 'indicator_d{d}.npy', 1),
+                                           ('riemann2d', 'indicator_d{d}.npy', 1)])
+def test_fullsize_learned_requests_match_oracle_on_sampled_patches(name, wname, K):
+    # FP32, learned flags, keep margin, autotuned, after timed-style steps of
+    # amr_advance (the first case is the bench's configuration: the lookahead
+    # network regridding every 4 steps); refine bits of sampled leaves below
+    # the finest level and candidate status of sampled parents, except where
+    # a logit lies within the BF16 margin of its threshold
     from oracle import mlp
     from paper_2508_05020_gb300.amr import AMR
     w = workload(name)
-    wf = weights(w['dim'])
+    wf = np.load(os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights',
+                              wname.format(d=w['dim']))).astype(np.float32)
     g = AMR(w, precision=32, flagger='mlp', mlp_weights=wf, autotune=True, mlp_keep_margin=KEEP)
-    g.advance(3)
+    g.advance(3 if K == 1 else 2 * K + 1, regrid=K)
     r = oracle_from_gpu(w, g)
     q = mlp.unflatten(wf.astype(np.float64), mlp.k_in(w['dim']))
     rg, cg = g.requests()
