@@ -145,9 +145,15 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
 // face together; the right stencil is the left one mirrored, so two candidate
 // values and two smoothness terms are shared between them. Same formulas as
 // weno5. FAST: the normalised weights are unchanged when every alpha_k is
-// multiplied by e0^2 e1^2 e2^2, which leaves a single division, valid while
-// the products stay far inside the FP32 range (ok is cleared otherwise, and
-// the caller evaluates the face again without FAST); else three divisions.
+// multiplied by e0^2 e1^2 e2^2, which leaves a single division, exact up to
+// rounding while no product overflows: checked on the division's operands, a
+// finite numerator and a denominator below 2^126, the range of the fast
+// division (the denominator is at least 0.0625 eps^4, far above 2^-126). ok
+// is cleared otherwise, and the caller evaluates the face again without FAST;
+// else three divisions.
+__device__ __forceinline__ bool weights_in_range(float num, float den) {
+    return fabsf(num) < 1.0e37f && den < 1.0e37f;
+}
 template <bool FAST>
 __device__ __forceinline__ void weno5_pair(float v0, float v1, float v2, float v3, float v4, float v5, float& left,
                                            float& right, bool& ok) {
@@ -160,9 +166,10 @@ __device__ __forceinline__ void weno5_pair(float v0, float v1, float v2, float v
         const float e0 = 1.0e-6f + b0, e1 = 1.0e-6f + b1, e2 = 1.0e-6f + b2;
         const float s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
         if constexpr (FAST) {
-            ok = ok && fmaxf(s0, fmaxf(s1, s2)) < 1.0e12f;
             const float m0 = 0.0625f * (s1 * s2), m1 = 0.625f * (s0 * s2), m2 = 0.3125f * (s0 * s1);
-            return __fdividef(m0 * q0 + m1 * q1 + m2 * q2, m0 + m1 + m2);
+            const float num = m0 * q0 + m1 * q1 + m2 * q2, den = m0 + m1 + m2;
+            ok = ok && weights_in_range(num, den);
+            return __fdividef(num, den);
         } else {
             const float a0 = __fdividef(0.0625f, s0), a1 = __fdividef(0.625f, s1), a2 = __fdividef(0.3125f, s2);
             return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
@@ -198,6 +205,39 @@ __device__ __forceinline__ F2 operator*(F2 a, float s) { return {__fmul2_rn(a.v,
 __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
 __device__ __forceinline__ F2 fma2(F2 a, float s, F2 c) { return {__ffma2_rn(a.v, make_float2(s, s), c.v)}; }
 __device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+// approximate reciprocal (PTX rcp.approx, about 1 ulp; operands here are
+// normal numbers) of both lanes
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ F2 rcp2(F2 a) { return f2(rcp_approx(a.v.x), rcp_approx(a.v.y)); }
+
+// the weights of weno5_pair<true> on both lanes, from candidates q and
+// smoothness indicators b given as 4 beta_k (with eps scaled alike: the
+// normalised weights are unchanged) and without the common factor 1/16 of the
+// linear weights (1, 10, 5) / 16; LIN: q1 and q2 come multiplied by their
+// linear weights 10 and 5. ok is cleared when either lane's division is out
+// of range.
+template <bool LIN>
+__device__ __forceinline__ F2 weno5_combine_x2(F2 q0, F2 q1, F2 q2, F2 b0, F2 b1, F2 b2, bool& ok) {
+    const F2 eps = f2s(4.0e-6f);
+    const F2 e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+    const F2 s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
+    const F2 p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
+    F2 num, den;
+    if constexpr (LIN) {
+        num = fma2(p01, q2, fma2(p02, q1, p12 * q0));
+        den = fma2(p01, 5.0f, fma2(p02, 10.0f, p12));
+    } else {
+        const F2 m1 = p02 * 10.0f, m2 = p01 * 5.0f;
+        num = fma2(m2, q2, fma2(m1, q1, p12 * q0));
+        den = p12 + m1 + m2;
+    }
+    ok = ok && weights_in_range(num.v.x, den.v.x) && weights_in_range(num.v.y, den.v.y);
+    return num * rcp2(den);
+}
 
 // weno5_pair<FAST> on two characteristic fields at once (lane x and lane y):
 // the same candidates, smoothness indicators and single-division weights,
@@ -205,34 +245,45 @@ __device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, ma
 // either lane would leave the FP32 range
 __device__ __forceinline__ void weno5_pair_x2(F2 v0, F2 v1, F2 v2, F2 v3, F2 v4, F2 v5, F2& left, F2& right,
                                               bool& ok) {
-    const float c1312 = 13.0f / 12.0f;
+    const float c133 = 13.0f / 3.0f;                                      // 4 beta = 13/3 t^2 + s^2
     const F2 qA = fma2(v3, 0.375f, fma2(v2, 0.75f, v1 * -0.125f));     // left q1 = right q2
     const F2 qB = fma2(v4, -0.125f, fma2(v3, 0.75f, v2 * 0.375f));     // left q2 = right q1
     const F2 tA = fma2(v2, -2.0f, v1 + v3), tB = fma2(v3, -2.0f, v2 + v4);
-    const F2 cA = tA * (tA * c1312), cB = tB * (tB * c1312);
-    auto combine = [&ok](F2 q0, F2 q1, F2 q2, F2 b0, F2 b1, F2 b2) {
-        const F2 eps = f2s(1.0e-6f);
-        const F2 e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-        const F2 s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
-        ok = ok && fmaxf(s0.v.x, fmaxf(s1.v.x, s2.v.x)) < 1.0e12f && fmaxf(s0.v.y, fmaxf(s1.v.y, s2.v.y)) < 1.0e12f;
-        const F2 m0 = (s1 * s2) * 0.0625f, m1 = (s0 * s2) * 0.625f, m2 = (s0 * s1) * 0.3125f;
-        const F2 num = fma2(m2, q2, fma2(m1, q1, m0 * q0));
-        const F2 den = m0 + m1 + m2;
-        return f2(__fdividef(num.v.x, den.v.x), __fdividef(num.v.y, den.v.y));
-    };
-    auto beta = [c1312](F2 t, F2 s) { return fma2(t, t * c1312, s * (s * 0.25f)); };
+    const F2 cA = tA * (tA * c133), cB = tB * (tB * c133);
+    auto beta4 = [c133](F2 t, F2 s) { return fma2(t, t * c133, s * s); };
     {   // left: a = v0, b = v1, c = v2, d = v3, e = v4
         const F2 q0 = fma2(v2, 1.875f, fma2(v1, -1.25f, v0 * 0.375f));
         const F2 t0 = fma2(v1, -2.0f, v0 + v2), s0 = fma2(v1, -4.0f, fma2(v2, 3.0f, v0));
         const F2 s1 = v1 - v3, s2 = fma2(v3, -4.0f, fma2(v2, 3.0f, v4));
-        left = combine(q0, qA, qB, beta(t0, s0), fma2(s1, s1 * 0.25f, cA), fma2(s2, s2 * 0.25f, cB));
+        left = weno5_combine_x2<false>(q0, qA, qB, beta4(t0, s0), fma2(s1, s1, cA), fma2(s2, s2, cB), ok);
     }
     {   // right: a = v5, b = v4, c = v3, d = v2, e = v1
         const F2 q0 = fma2(v3, 1.875f, fma2(v4, -1.25f, v5 * 0.375f));
         const F2 t0 = fma2(v4, -2.0f, v5 + v3), s0 = fma2(v4, -4.0f, fma2(v3, 3.0f, v5));
         const F2 s1 = v4 - v2, s2 = fma2(v2, -4.0f, fma2(v3, 3.0f, v1));
-        right = combine(q0, qB, qA, beta(t0, s0), fma2(s1, s1 * 0.25f, cB), fma2(s2, s2 * 0.25f, cA));
+        right = weno5_combine_x2<false>(q0, qB, qA, beta4(t0, s0), fma2(s1, s1, cB), fma2(s2, s2, cA), ok);
     }
+}
+
+// weno5 (single-division weights) of two stencils a..e at once, one per lane:
+// used for the left (nodes 0..4) and right (nodes 5..1) values of one field
+__device__ __forceinline__ F2 weno5_x2(F2 a, F2 b, F2 c, F2 d, F2 e, bool& ok) {
+    const float c133 = 13.0f / 3.0f;
+    const F2 q0 = fma2(c, 1.875f, fma2(b, -1.25f, a * 0.375f));
+    const F2 q1 = fma2(d, 3.75f, fma2(c, 7.5f, b * -1.25f));          // 10 q1
+    const F2 q2 = fma2(e, -0.625f, fma2(d, 3.75f, c * 1.875f));       // 5 q2
+    const F2 t0 = fma2(b, -2.0f, a + c), s0 = fma2(b, -4.0f, fma2(c, 3.0f, a));
+    const F2 t1 = fma2(c, -2.0f, b + d), s1 = b - d;
+    const F2 t2 = fma2(d, -2.0f, c + e), s2 = fma2(d, -4.0f, fma2(c, 3.0f, e));
+    auto beta4 = [c133](F2 t, F2 s) { return fma2(t, t * c133, s * s); };
+    return weno5_combine_x2<true>(q0, q1, q2, beta4(t0, s0), beta4(t1, s1), beta4(t2, s2), ok);
+}
+// left and right WENO values of one field with nodes v[0..5], as one packed call
+__device__ __forceinline__ void weno5_lr_x2(float v0, float v1, float v2, float v3, float v4, float v5, float& left,
+                                            float& right, bool& ok) {
+    const F2 r = weno5_x2(f2(v0, v5), f2(v1, v4), f2(v2, v3), f2(v3, v2), f2(v4, v1), ok);
+    left = r.v.x;
+    right = r.v.y;
 }
 
 // left and right values of one characteristic field; FP32 see weno5_pair
@@ -417,10 +468,9 @@ __device__ __forceinline__ void face_flux_x2(const float (&p)[6], const float (&
             weno5_pair_x2(b[0], b[1], b[2], b[3], b[4], b[5], L, R, ok);
             wl[1] = L.v.x; wl[2] = L.v.y; wr[1] = R.v.x; wr[2] = R.v.y;
         } else {
-            weno5_pair<true>(b[0].v.x, b[1].v.x, b[2].v.x, b[3].v.x, b[4].v.x, b[5].v.x, wl[1], wr[1], ok);
+            weno5_lr_x2(b[0].v.x, b[1].v.x, b[2].v.x, b[3].v.x, b[4].v.x, b[5].v.x, wl[1], wr[1], ok);
         }
-        if constexpr (NT == 2) weno5_pair<true>(ut[1][0], ut[1][1], ut[1][2], ut[1][3], ut[1][4], ut[1][5], wl[3],
-                                                wr[3], ok);
+        if constexpr (NT == 2) weno5_lr_x2(ut[1][0], ut[1][1], ut[1][2], ut[1][3], ut[1][4], ut[1][5], wl[3], wr[3], ok);
     }
     if (!ok) {          // a weight product out of range: every field again with three divisions
         float w[6];
@@ -1056,52 +1106,69 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
         constexpr int NPH = D == 3 ? 2 : 1;
 #pragma unroll 1
         for (int ph = 0; ph < NPH; ++ph) {
-            const int dlo = ph == 0 ? 0 : 2, dhi = ph == 0 ? (D < 2 ? D : 2) : 3;
             const int nfp = ph == 0 ? (D >= 2 ? C::F0 + C::F1 : C::F0) : C::F2;
             for (int fp = threadIdx.x; fp < nfp; fp += NTH) {
+                // the face's dimension (uniform across a warp except at the one
+                // x/y boundary of the buffer when F0 is not a multiple of 32).
+                // Node loads and face stores are compiled per dimension, so
+                // their shared-memory offsets are constants; the flux code
+                // between them exists once
                 const int d = ph == 1 ? 2 : (D >= 2 && fp >= C::F0 ? 1 : 0);
-                const int fbase = d == 1 ? C::F0 : 0;     // the dimension's faces in the buffer
-                const int f = fp - fbase;
-                const int ex = d == 0, ey = d == 1;
-                const int FX = d == 0 ? C::FX0 : (d == 1 ? C::FX1 : C::FX2);
-                const int FY = d == 0 ? C::FY0 : (d == 1 ? C::FY1 : C::FY2);
-                // f -> (fi, fj, fk) by multiply-high division, exact for f * FX < 2^32
-                const unsigned mFX = d == 0 ? C::MX0 : (d == 1 ? C::MX1 : C::MX2);
-                const unsigned mFY = D == 1 ? 0u : (d == 0 ? C::MY0 : (d == 1 ? C::MY1 : C::MY2));   // 1D: FY = FZ = 1
-                const int step = d == 0 ? 1 : C::QX;      // x and y pencils stay in one centre plane
-                // tangential velocity components in increasing dimension order
-                const int t1 = d == 0 ? 1 : 0;
-                const int t2 = d == 2 ? 1 : 2;
-                const int q1 = (int)__umulhi((unsigned)f, mFX);
-                const int fk = D == 1 ? 0 : (int)__umulhi((unsigned)q1, mFY);
-                const int fi = f - q1 * FX;
-                const int fj = q1 - fk * FY;
-                // smem index of pencil node 0 (cell index - 3 along d; G = 3).
-                // Central: face index a along d is the face i - 1/2 of cell
-                // i = a - 1, and only nodes 1..4 (cells i - 2 .. i + 1) are read
-                int base = 0;
-                if (d < 2) {
-                    const int bx = fi + G - (ex ? G + EXT / 2 : 0);
-                    const int by = (D >= 2 ? fj + G : 0) - (ey ? G + EXT / 2 : 0);
-                    base = ((D == 3 ? fk : 0) * C::QY + by) * C::QX + bx;
-                }
                 T pp[6], un[6], ut[NT > 0 ? NT : 1][6], Tt[6];
-#pragma unroll
-                for (int k = CEN ? 1 : 0; k < (CEN ? 5 : 6); ++k) {
-                    int id;
-                    if (D < 3 || d < 2) {
-                        id = base + k * step;
-                    } else {                                 // z pencil: halo plane or centre plane
-                        const int zz = fk + k - EXT / 2;     // staged z index 0 .. DZ + 5
-                        id = (zz >= G && zz < G + DZ)
-                                 ? ((zz - G) * C::QY + fj + G) * C::QX + fi + G
-                                 : C::QC + ((zz < G ? zz : zz - DZ) * N + fj) * N + fi;
+                int fi, fj, fk;
+                auto load = [&](auto dc) {
+                    constexpr int DD = decltype(dc)::value;
+                    constexpr int fbase = DD == 1 ? C::F0 : 0;   // the dimension's faces in the buffer
+                    constexpr int FX = DD == 0 ? C::FX0 : (DD == 1 ? C::FX1 : C::FX2);
+                    constexpr int FY = DD == 0 ? C::FY0 : (DD == 1 ? C::FY1 : C::FY2);
+                    // f -> (fi, fj, fk) by multiply-high division, exact for f * FX < 2^32
+                    constexpr unsigned mFX = DD == 0 ? C::MX0 : (DD == 1 ? C::MX1 : C::MX2);
+                    constexpr unsigned mFY = DD == 0 ? C::MY0 : (DD == 1 ? C::MY1 : C::MY2);
+                    constexpr int step = DD == 0 ? 1 : C::QX;     // x and y pencils stay in one centre plane
+                    // tangential velocity components in increasing dimension order
+                    [[maybe_unused]] constexpr int t1 = DD == 0 ? 1 : 0;
+                    [[maybe_unused]] constexpr int t2 = DD == 2 ? 1 : 2;
+                    const int f = fp - fbase;
+                    const int q1 = (int)__umulhi((unsigned)f, mFX);
+                    fk = D == 1 ? 0 : (int)__umulhi((unsigned)q1, mFY);   // 1D: FY = FZ = 1
+                    fi = f - q1 * FX;
+                    fj = q1 - fk * FY;
+                    // smem index of pencil node 0 (cell index - 3 along d; G = 3).
+                    // Central: face index a along d is the face i - 1/2 of cell
+                    // i = a - 1, and only nodes 1..4 (cells i - 2 .. i + 1) are read
+                    int base = 0;
+                    if constexpr (DD < 2) {
+                        const int bx = fi + G - (DD == 0 ? G + EXT / 2 : 0);
+                        const int by = (D >= 2 ? fj + G : 0) - (DD == 1 ? G + EXT / 2 : 0);
+                        base = ((D == 3 ? fk : 0) * C::QY + by) * C::QX + bx;
                     }
-                    pp[k] = q[id];
-                    un[k] = q[(1 + d) * C::QN + id];
-                    Tt[k] = q[(D + 1) * C::QN + id];
-                    if (NT >= 1) ut[0][k] = q[(1 + t1) * C::QN + id];
-                    if (NT >= 2) ut[NT > 1 ? 1 : 0][k] = q[(1 + t2) * C::QN + id];
+#pragma unroll
+                    for (int k = CEN ? 1 : 0; k < (CEN ? 5 : 6); ++k) {
+                        int id;
+                        if constexpr (DD < 2) {
+                            id = base + k * step;
+                        } else {                                 // z pencil: halo plane or centre plane
+                            const int zz = fk + k - EXT / 2;     // staged z index 0 .. DZ + 5
+                            id = (zz >= G && zz < G + DZ)
+                                     ? ((zz - G) * C::QY + fj + G) * C::QX + fi + G
+                                     : C::QC + ((zz < G ? zz : zz - DZ) * N + fj) * N + fi;
+                        }
+                        pp[k] = q[id];
+                        un[k] = q[(1 + DD) * C::QN + id];
+                        Tt[k] = q[(D + 1) * C::QN + id];
+                        if constexpr (NT >= 1) ut[0][k] = q[(1 + t1) * C::QN + id];
+                        if constexpr (NT >= 2) ut[NT > 1 ? 1 : 0][k] = q[(1 + t2) * C::QN + id];
+                    }
+                };
+                if constexpr (D == 3) {
+                    if (d == 2) load(std::integral_constant<int, 2>{});
+                    else if (d == 1) load(std::integral_constant<int, 1>{});
+                    else load(std::integral_constant<int, 0>{});
+                } else if constexpr (D == 2) {
+                    if (d == 1) load(std::integral_constant<int, 1>{});
+                    else load(std::integral_constant<int, 0>{});
+                } else {
+                    load(std::integral_constant<int, 0>{});
                 }
                 T Fp[NT + 3];
                 if constexpr (CEN) central_flux<T, NT>(pp, un, ut, Tt, gm1, Fp);
@@ -1109,83 +1176,105 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 else if constexpr (sizeof(T) == 4 && FLUX == AMR_FLUX_RUSANOV)
                     face_flux_x2<NT>(pp, un, ut, Tt, gamma, gm1, Fp);
                 else face_flux<T, NT, FLUX>(pp, un, ut, Tt, gamma, gm1, Fp);
-                // pencil order -> global variable order
-                T Fg[NV];
-                Fg[0] = Fp[0];
+                auto store = [&](auto dc) {
+                    constexpr int DD = decltype(dc)::value;
+                    constexpr int t1 = DD == 0 ? 1 : 0;
+                    // pencil order -> global variable order
+                    T Fg[NV];
+                    Fg[0] = Fp[0];
 #pragma unroll
-                for (int e = 0; e < D; ++e)
-                    Fg[1 + e] = e == d ? Fp[1] : (e == t1 ? Fp[NT >= 1 ? 2 : 1] : Fp[NT >= 2 ? 3 : 1]);
-                Fg[NV - 1] = Fp[NT + 2];
+                    for (int e = 0; e < D; ++e)
+                        Fg[1 + e] = e == DD ? Fp[1] : (e == t1 ? Fp[NT >= 1 ? 2 : 1] : Fp[NT >= 2 ? 3 : 1]);
+                    Fg[NV - 1] = Fp[NT + 2];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) Fs[v * C::FMAX + fp] = Fg[v];
-                // patch-boundary faces needed by the coarse-fine flux correction
-                // (central: the conservative face values, saved by the divergence)
-                const int fd = d == 0 ? fi : (d == 1 ? fj : fk + z0);
-                const int side = fd == 0 ? 0 : (fd == N ? 1 : -1);
-                if (!CEN && side >= 0 && ((pf >> (8 + 2 * d + side)) & 1)) {
-                    int tidx;
-                    if (D == 1) tidx = 0;
-                    else if (D == 2) tidx = d == 0 ? fj : fi;
-                    else tidx = d == 0 ? (fk + z0) * N + fj : (d == 1 ? (fk + z0) * N + fi : fj * N + fi);
-                    T* dst = faces + ((long long)slot * 2 * D + 2 * d + side) * NV * C::TRANS + tidx;
+                    for (int v = 0; v < NV; ++v) Fs[v * C::FMAX + fp] = Fg[v];
+                    // patch-boundary faces needed by the coarse-fine flux correction
+                    // (central: the conservative face values, saved by the divergence)
+                    const int fd = DD == 0 ? fi : (DD == 1 ? fj : fk + z0);
+                    const int side = fd == 0 ? 0 : (fd == N ? 1 : -1);
+                    if (!CEN && side >= 0 && ((pf >> (8 + 2 * DD + side)) & 1)) {
+                        int tidx;
+                        if constexpr (D == 1) tidx = 0;
+                        else if constexpr (D == 2) tidx = DD == 0 ? fj : fi;
+                        else tidx = DD == 0 ? (fk + z0) * N + fj : (DD == 1 ? (fk + z0) * N + fi : fj * N + fi);
+                        T* dst = faces + ((long long)slot * 2 * D + 2 * DD + side) * NV * C::TRANS + tidx;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) dst[v * C::TRANS] = Fg[v];
+                        for (int v = 0; v < NV; ++v) dst[v * C::TRANS] = Fg[v];
+                    }
+                };
+                if constexpr (D == 3) {
+                    if (d == 2) store(std::integral_constant<int, 2>{});
+                    else if (d == 1) store(std::integral_constant<int, 1>{});
+                    else store(std::integral_constant<int, 0>{});
+                } else if constexpr (D == 2) {
+                    if (d == 1) store(std::integral_constant<int, 1>{});
+                    else store(std::integral_constant<int, 0>{});
+                } else {
+                    store(std::integral_constant<int, 0>{});
                 }
             }
             __syncthreads();
-#pragma unroll 1
-            for (int d = dlo; d < dhi; ++d) {
-            const int FX = d == 0 ? C::FX0 : (d == 1 ? C::FX1 : C::FX2);
-            const int FY = d == 0 ? C::FY0 : (d == 1 ? C::FY1 : C::FY2);
-            const T* Fd = Fs + (d == 1 ? C::F0 : 0);
-            const T dxd = T(g.dx[lev][d]);
-            const T idx = T(1) / dxd;                        // FP32: multiply by the reciprocal
-            const int fstep = d == 0 ? 1 : (d == 1 ? FX : FX * FY);
+            // divergence of the phase's dimensions, each compiled for its own
+            // dimension (constant face strides)
+            auto divergence = [&](auto dc) {
+                constexpr int d = decltype(dc)::value;
+                constexpr int FX = d == 0 ? C::FX0 : (d == 1 ? C::FX1 : C::FX2);
+                constexpr int FY = d == 0 ? C::FY0 : (d == 1 ? C::FY1 : C::FY2);
+                const T* Fd = Fs + (d == 1 ? C::F0 : 0);
+                const T dxd = T(g.dx[lev][d]);
+                const T idx = T(1) / dxd;                        // FP32: multiply by the reciprocal
+                constexpr int fstep = d == 0 ? 1 : (d == 1 ? FX : FX * FY);
 #pragma unroll
-            for (int n = 0; n < CPT; ++n) {
-                const int cidx = threadIdx.x + n * NTH;
-                if (cidx < C::CELLS) {
-                    const int ci = cidx % C::CX;
-                    const int cj = (cidx / C::CX) % C::CY;
-                    const int ck = cidx / (C::CX * C::CY);
-                    const int flo = (ck * FY + cj) * FX + ci + (CEN ? fstep : 0);
-                    const int fhi = flo + fstep;
-                    if constexpr (CEN) {
-                        // Eq. 9 as the difference of G = (26 F_f - F_{f-1} - F_{f+1}) / 24
-                        const int cd = d == 0 ? ci : (d == 1 ? cj : ck + z0);
-                        const int side = cd == 0 ? 0 : (cd == N - 1 ? 1 : -1);
-                        const bool save = side >= 0 && ((pf >> (8 + 2 * d + side)) & 1);
-                        T* dst = nullptr;
-                        if (save) {
-                            int tidx;
-                            if (D == 1) tidx = 0;
-                            else if (D == 2) tidx = d == 0 ? cj : ci;
-                            else tidx = d == 0 ? (ck + z0) * N + cj : (d == 1 ? (ck + z0) * N + ci : cj * N + ci);
-                            dst = faces + ((long long)slot * 2 * D + 2 * d + side) * NV * C::TRANS + tidx;
-                        }
+                for (int n = 0; n < CPT; ++n) {
+                    const int cidx = threadIdx.x + n * NTH;
+                    if (cidx < C::CELLS) {
+                        const int ci = cidx % C::CX;
+                        const int cj = (cidx / C::CX) % C::CY;
+                        const int ck = cidx / (C::CX * C::CY);
+                        const int flo = (ck * FY + cj) * FX + ci + (CEN ? fstep : 0);
+                        const int fhi = flo + fstep;
+                        if constexpr (CEN) {
+                            // Eq. 9 as the difference of G = (26 F_f - F_{f-1} - F_{f+1}) / 24
+                            const int cd = d == 0 ? ci : (d == 1 ? cj : ck + z0);
+                            const int side = cd == 0 ? 0 : (cd == N - 1 ? 1 : -1);
+                            const bool save = side >= 0 && ((pf >> (8 + 2 * d + side)) & 1);
+                            T* dst = nullptr;
+                            if (save) {
+                                int tidx;
+                                if (D == 1) tidx = 0;
+                                else if (D == 2) tidx = d == 0 ? cj : ci;
+                                else tidx = d == 0 ? (ck + z0) * N + cj : (d == 1 ? (ck + z0) * N + ci : cj * N + ci);
+                                dst = faces + ((long long)slot * 2 * D + 2 * d + side) * NV * C::TRANS + tidx;
+                            }
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            const T* Fv = Fd + v * C::FMAX;
-                            const T flo_m = Fv[flo - fstep], flo_c = Fv[flo], fhi_c = Fv[fhi], fhi_p = Fv[fhi + fstep];
-                            T glo = T(26) * flo_c - flo_m - fhi_c;
-                            T ghi = T(26) * fhi_c - flo_c - fhi_p;
-                            if constexpr (sizeof(T) == 4) { glo = glo * T(1.0 / 24.0); ghi = ghi * T(1.0 / 24.0); }
-                            else { glo = glo / T(24); ghi = ghi / T(24); }
-                            if (save) dst[v * C::TRANS] = side ? ghi : glo;
-                            const T df = ghi - glo;
-                            const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
-                            R[n][v] = d == 0 ? -dv : R[n][v] - dv;
-                        }
-                    } else {
+                            for (int v = 0; v < NV; ++v) {
+                                const T* Fv = Fd + v * C::FMAX;
+                                const T flo_m = Fv[flo - fstep], flo_c = Fv[flo], fhi_c = Fv[fhi], fhi_p = Fv[fhi + fstep];
+                                T glo = T(26) * flo_c - flo_m - fhi_c;
+                                T ghi = T(26) * fhi_c - flo_c - fhi_p;
+                                if constexpr (sizeof(T) == 4) { glo = glo * T(1.0 / 24.0); ghi = ghi * T(1.0 / 24.0); }
+                                else { glo = glo / T(24); ghi = ghi / T(24); }
+                                if (save) dst[v * C::TRANS] = side ? ghi : glo;
+                                const T df = ghi - glo;
+                                const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
+                                R[n][v] = d == 0 ? -dv : R[n][v] - dv;
+                            }
+                        } else {
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            const T df = Fd[v * C::FMAX + fhi] - Fd[v * C::FMAX + flo];
-                            const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
-                            R[n][v] = d == 0 ? -dv : R[n][v] - dv;
+                            for (int v = 0; v < NV; ++v) {
+                                const T df = Fd[v * C::FMAX + fhi] - Fd[v * C::FMAX + flo];
+                                const T dv = sizeof(T) == 4 ? df * idx : df / dxd;
+                                R[n][v] = d == 0 ? -dv : R[n][v] - dv;
+                            }
                         }
                     }
                 }
-            }
+            };
+            if (ph == 0) {
+                divergence(std::integral_constant<int, 0>{});
+                if constexpr (D >= 2) divergence(std::integral_constant<int, 1>{});
+            } else if constexpr (D == 3) {
+                divergence(std::integral_constant<int, 2>{});
             }
             __syncthreads();
         }
