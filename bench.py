@@ -41,21 +41,22 @@ PEAKS_FILE = os.path.join(ROOT, 'MEASURED_PEAKS.json')
 FLOPS_FILE = os.path.join(ROOT, 'oracle', 'flop_counts.json')
 WEIGHTS_DIR = os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights')
 
-# DRAM bytes of one stage-1 k_rhs launch (ncu, dram__bytes_read.sum +
-# dram__bytes_write.sum) on the default workload at t_end / 2 (4656 leaf
+# DRAM bytes of one stage-1 k_rhs launch per RHS tile shape (ncu,
+# dram__bytes_read.sum + dram__bytes_write.sum; None: not captured) on the
+# default workload at t_end / 2 (4656 leaf
 # patches, the state a checkpoint of the default run holds at the start of its
 # headline window), valid while the sources of the kernel (the regions below:
 # EOS, WENO5, face fluxes, the kernel and its launch) hash as recorded. Leaves
 # are independent work items, so a launch over another hierarchy of the same
 # workload moves this figure per leaf times its leaves.
-RHS_TRAFFIC = {'bytes': 1125297920 + 382622720, 'leaves': 4656, 'workload': 'blast3d', 'base': 128, 'levels': 3,
+RHS_TRAFFIC = {'bytes': {0: 1124540672 + 381762048, 2: 958110464 + 379358464}, 'leaves': 4656, 'workload': 'blast3d', 'base': 128, 'levels': 3,
                'regions': [('paper_2508_05020_gb300/csrc/amr_kernels.cuh', 'template <typename T> struct Num;',
                             '// Metadata of one patch staged'),
                            ('paper_2508_05020_gb300/csrc/amr_kernels.cuh', '// K4: fused right-hand side',
                             '// K5: coarse-fine flux correction'),
                            ('paper_2508_05020_gb300/csrc/amr_launch.cuh', 'template <typename T, int D, int N, int V = 0> struct RhsCfg',
                             'template <typename T>\ncudaError_t Kernels<T>::prepare')],
-               'hash': '46a850e2ba224fe2'}
+               'hash': '24eef3427ac14dac'}
 
 
 def rhs_source_hash():
@@ -69,9 +70,10 @@ def rhs_source_hash():
     return h.hexdigest()[:16]
 
 
-def rhs_traffic(workload_name, base, levels, leaves=None):
-    """DRAM bytes of one stage-1 RHS launch over `leaves` leaf patches (the
-    captured launch's own count if None), or None when no capture applies."""
+def rhs_traffic(workload_name, base, levels, leaves=None, shape=0):
+    """DRAM bytes of one stage-1 RHS launch of tile shape `shape` over `leaves`
+    leaf patches (the captured launch's own count if None), or None when no
+    capture applies."""
     if workload_name != RHS_TRAFFIC['workload'] or base not in (0, RHS_TRAFFIC['base']) or \
             levels not in (0, RHS_TRAFFIC['levels']):
         return None
@@ -80,9 +82,12 @@ def rhs_traffic(workload_name, base, levels, leaves=None):
             return None
     except ValueError:
         return None
+    b = RHS_TRAFFIC['bytes'].get(shape)
+    if b is None:
+        return None
     if leaves is None:
-        return RHS_TRAFFIC['bytes']
-    return int(round(RHS_TRAFFIC['bytes'] * leaves / RHS_TRAFFIC['leaves']))
+        return b
+    return int(round(b * leaves / RHS_TRAFFIC['leaves']))
 
 
 def load_json(path, default):
@@ -487,6 +492,9 @@ def main():
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-autotune', action='store_true', help='default launch parameters instead of tuned ones')
+    ap.add_argument('--set-tuning', default='',
+                    help='launch parameters to pin after any tuning, as name=value[,name=value] with the names of '
+                         'amr.TUNE_NAMES (e.g. rhs_tile_shape=2,rhs_ctas_per_sm=1, to profile one tile shape)')
     ap.add_argument('--no-compare', action='store_true',
                     help='skip the regrid-interval variants, the FP64 paths and the L1(rho) comparison')
     args = ap.parse_args()
@@ -518,6 +526,9 @@ def main():
     weights = load_weights(weights_name, w['dim']) if args.flagger == 'mlp' else None
     K_r = args.regrid_every or (4 if weights_name and '_k4' in weights_name else 1)
     amr = make_amr(AMR, w, args, args.flagger, weights, precision=args.precision)
+    pinned = {k: int(v) for k, v in (kv.split('=') for kv in args.set_tuning.split(',') if kv)}
+    if pinned:
+        amr.set_tuning(pinned)
     tuned, tuned_ms = amr.tuning()
     fe = fine_equivalent_cells(w)
     N = w['patch']
@@ -547,6 +558,13 @@ def main():
             run.advance_to(args.window * w['t_end'])
         if args.checkpoint:
             amr.checkpoint(args.checkpoint)
+    # the tuner again on the hierarchy of the headline window (untimed; it
+    # leaves the state, time and dt as they are): the mesh has grown since t = 0
+    if not args.no_autotune:
+        amr.autotune()
+    if pinned:
+        amr.set_tuning(pinned)
+    tuned_half = amr.tuning()[0]
     mid_state = host_state(amr) if (rank == 0 and (not args.no_e2e or not args.no_compare)) else None
     t_h = run.t
     amr.set_timing(True)
@@ -610,9 +628,11 @@ def main():
                   else 'WENO5 + Rusanov')
         roof = {'bound': 'alu', 'kernel': 'k_rhs (fused %s + SSP-RK3 stage)' % scheme,
                 'achieved': achieved, 'peak': fp32_peak, 'unit': 'TFLOP/s', 'frac': achieved / fp32_peak,
-                'traffic': rhs_traffic(args.workload, args.base, args.levels, leaf_patches(w, ppl)),
-                'traffic_unit': 'DRAM bytes per launch (stage 1; ncu capture at %d leaf patches scaled to '
-                                'this launch\'s %d)' % (RHS_TRAFFIC['leaves'], leaf_patches(w, ppl)),
+                'traffic': rhs_traffic(args.workload, args.base, args.levels, leaf_patches(w, ppl),
+                                       tuned_half['rhs_tile_shape']),
+                'traffic_unit': 'DRAM bytes per launch (stage 1, RHS tile shape %d; ncu capture at %d leaf patches '
+                                'scaled to this launch\'s %d)' % (tuned_half['rhs_tile_shape'], RHS_TRAFFIC['leaves'],
+                                                                  leaf_patches(w, ppl)),
                 'avg_launch_ms': rhs_ms, 'flop_per_launch': flops_rhs,
                 'peak_basis': 'FP32 ALU: 152 SMs x 128 lanes x 2 FLOP x %.0f MHz (of the measured maximum SM clock)'
                               % sm_max}
@@ -634,7 +654,9 @@ def main():
                        'fine_equivalent_cells': fe, 'patches_per_level': [int(x) for x in ppl],
                        'l2': 'inputs larger than L2 (state arrays of several GB)',
                        'parallelism': 'replicas (dp%d, no data-path collective)' % world,
-                       'launch_parameters': tuned, 'autotuned': not args.no_autotune,
+                       'launch_parameters': tuned_half, 'launch_parameters_t0': tuned,
+                       'autotuned': ('at t = 0 and again at the start of the timed window' if not args.no_autotune
+                                     else False),
                        'mlp_keep_margin': args.keep_margin if args.flagger == 'mlp' else None,
                        'regrid_every': K_r,
                        'cells_per_step': cell_counts(w, ppl)},

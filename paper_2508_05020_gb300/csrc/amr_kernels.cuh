@@ -1008,9 +1008,13 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 src = nb >= 0 ? nb : slot;
                 shift = nb >= 0 ? (side ? -N : N) : 0;
             };
-            int sxm, dxm, sxp, dxp;
+            int sxm, dxm, sxp, dxp, sym = slot, dym = 0, syp = slot, dyp = 0;
             across(0, 0, sxm, dxm);
             across(0, 1, sxp, dxp);
+            if constexpr (D >= 2) {
+                across(1, 0, sym, dym);
+                across(1, 1, syp, dyp);
+            }
             // centre planes (3D) or the whole slot (1D/2D): full rows; a row
             // outside the interior along y comes whole from its y source (its
             // x ghosts are edge cells, which no face reads)
@@ -1026,9 +1030,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 T Uv[NV][VE];
                 const int ly = qy - G;
                 if (D >= 2 && (ly < 0 || ly >= N)) {
-                    int src, sh;
-                    across(1, ly >= N, src, sh);
-                    loadv(Uv, src, sz, qy + sh, x0);
+                    loadv(Uv, ly < 0 ? sym : syp, sz, qy + (ly < 0 ? dym : dyp), x0);
                 } else {
                     loadv(Uv, slot, sz, qy, x0);
                     if (x0 < G) {                            // x ghosts below the interior
@@ -1276,7 +1278,13 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
             } else if constexpr (D == 3) {
                 divergence(std::integral_constant<int, 2>{});
             }
-            __syncthreads();
+            // the next phase's faces overwrite the face buffer; after the last
+            // phase no barrier is needed: the update touches no shared memory,
+            // the next item's staging writes only the primitives (which no
+            // divergence reads), and its face pass starts after the barrier
+            // that ends that staging, which every thread reaches only after
+            // its divergence here
+            if (ph + 1 < NPH) __syncthreads();
         }
         // 3. stage update of the chunk's cells
 #pragma unroll

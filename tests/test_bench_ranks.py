@@ -80,8 +80,10 @@ def test_roofline_accounting():
     assert bench.rhs_flops_per_launch(Fake(), workload('blast3d', flux='hllc'), flops) is None
     # the recorded DRAM bytes apply to the default workload, and only while the
     # kernel's sources hash as they did at capture (else null)
-    assert bench.rhs_traffic('blast3d', 0, 0) in (bench.RHS_TRAFFIC['bytes'], None)
+    assert bench.rhs_traffic('blast3d', 0, 0) in (bench.RHS_TRAFFIC['bytes'][0], None)
     assert (bench.rhs_traffic('blast3d', 0, 0) is None) == (bench.rhs_source_hash() != bench.RHS_TRAFFIC['hash'])
+    # per tile shape: a shape without a capture has none
+    assert bench.rhs_traffic('blast3d', 0, 0, shape=1) is None
     assert bench.rhs_traffic('blast3d', 64, 0) is None
     assert bench.rhs_traffic('dmr', 0, 0) is None
 
@@ -97,10 +99,10 @@ def test_run_planning_and_traffic_scaling():
     assert bench.plan_chunk(2.5e-5, 1e-5, 25) == 1
     assert bench.plan_chunk(1.0, 0.0, 25) == 1
     # the captured launch's DRAM bytes, scaled per leaf patch to another launch
-    if bench.rhs_traffic('blast3d', 0, 0) is not None:
-        b = bench.RHS_TRAFFIC['bytes']
-        assert bench.rhs_traffic('blast3d', 0, 0, bench.RHS_TRAFFIC['leaves']) == b
-        assert bench.rhs_traffic('blast3d', 0, 0, 2 * bench.RHS_TRAFFIC['leaves']) == 2 * b
+    for shape, b in bench.RHS_TRAFFIC['bytes'].items():
+        if bench.rhs_traffic('blast3d', 0, 0, shape=shape) is not None:
+            assert bench.rhs_traffic('blast3d', 0, 0, bench.RHS_TRAFFIC['leaves'], shape) == b
+            assert bench.rhs_traffic('blast3d', 0, 0, 2 * bench.RHS_TRAFFIC['leaves'], shape) == 2 * b
 
 
 def test_level0_assembly():
