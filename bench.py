@@ -672,11 +672,13 @@ def main():
             'wall_s': wall}
     if learned:
         line['learned_indicator'] = learned
+    # the end-to-end leg first, on a GPU in the state the headline window saw
+    # (after the long comparison legs it measured half the rate)
+    if rank == 0 and not args.no_e2e and mid_state is not None:
+        line['e2e'] = e2e_measure(AMR, w, args, fe, weights, K_r, mid_state, local)
     if rank == 0 and not args.no_compare and has_end:
         line['compare'] = compare(AMR, w, args, fe, K_r, weights_name, whole, mid_state, value)
         line['l1_rho_at_t_end'] = line['compare']['l1_rho_at_t_end_reduced'].get('fp32_headline')
-    if rank == 0 and not args.no_e2e and mid_state is not None:
-        line['e2e'] = e2e_measure(AMR, w, args, fe, weights, K_r, mid_state)
     if rank == 0 and not args.no_cpu_baseline:
         v1, lv1, dt1, desc1 = oracle_sample(1)
         res, cores = oracle_all_cores(32)
@@ -822,7 +824,7 @@ def compare(AMR, w, args, fe, K_r, weights_name, whole, mid_state, value):
     return out
 
 
-def e2e_measure(AMR, w, args, fe, weights, K_r, mid_state):
+def e2e_measure(AMR, w, args, fe, weights, K_r, mid_state, gpu_index=0):
     """The same metric through the public API with host buffers, on the
     headline window's state: the hierarchy is uploaded from pinned host
     memory (amr_set_state), every step calls amr_advance(1) (a regrid every
@@ -839,11 +841,15 @@ def e2e_measure(AMR, w, args, fe, weights, K_r, mid_state):
         amr.advance(1, regrid=K_r)
         amr.diag()
     h0, d0, _ = amr.counters()
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
     t0 = time.perf_counter()
     amr.set_state(lv, co, da, t=t_mid)
+    t1 = time.perf_counter()
     for _ in range(args.steps):
         amr.advance(1, regrid=K_r)
         amr.diag()
+    t2 = time.perf_counter()
     off = 0
     for l in range(w['levels']):
         c, _ = amr.get_level(l, data=False)
@@ -851,11 +857,14 @@ def e2e_measure(AMR, w, args, fe, weights, K_r, mid_state):
         n = int(np.prod(shape))
         amr.get_level(l, out=res[off:off + n].reshape(shape) if off + n <= res.size else None)
         off += n
-    el = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    clk = clocks.stop()
+    el = t3 - t0
     h1, d1, _ = amr.counters()
     amr.close()
     return {'value': fe * args.steps / el, 'unit': UNIT,
             'h2d_bytes_per_step': int((h1 - h0) / args.steps), 'd2h_bytes_per_step': int((d1 - d0) / args.steps),
+            'parts_s': {'set_state': t1 - t0, 'steps': t2 - t1, 'readback': t3 - t2}, 'clocks': clk,
             'note': 'state of the headline window (t = %.4g) uploaded and final state read back inside the timed '
                     'region (amortised over the steps); per step amr_advance(1) + amr_get_diag' % t_mid}
 

@@ -206,7 +206,11 @@ int amr_regrid(amr_ctx* ctx);
 /* Patches of one level: *n_patches receives their number; coords (may be
  * NULL) receives n x dim integer patch coordinates; data (may be NULL)
  * receives n x (dim+2) x N^d interior values as double, variables
- * (rho, rho u_0.., rho e), cells in (z, y, x) order. */
+ * (rho, rho u_0.., rho e), cells in (z, y, x) order. A data buffer in
+ * page-locked host memory (cudaHostAlloc, cudaHostRegister, PyTorch's pinned
+ * memory) is written by the device directly, in one kernel; any other buffer
+ * through the library's device staging buffer. Either way the buffer must
+ * hold the whole level. */
 int amr_get_level(amr_ctx* ctx, int level, int* n_patches, int* coords, double* data);
 
 /* Diagnostics: time, sum over leaf cells of U times the cell volume (FP64,
@@ -217,7 +221,9 @@ int amr_get_diag(amr_ctx* ctx, double* t, double cons_sums[5], int patches_per_l
 /* Replace the hierarchy and state: n patches given by level (n ints), coords
  * (n x dim ints) and interiors (n x (dim+2) x N^d doubles, layout of
  * amr_get_level), and the time t. The set must contain every level-0 patch,
- * complete sibling groups, and satisfy R2; otherwise AMR_ERR_MESH. */
+ * complete sibling groups, and satisfy R2; otherwise AMR_ERR_MESH. Interiors
+ * in page-locked host memory are read by the device in place; others are
+ * copied through the staging buffer (as in amr_get_level). */
 int amr_set_state(amr_ctx* ctx, int n, const int* levels, const int* coords,
                   const double* data, double t);
 

@@ -739,6 +739,19 @@ int advance_impl(amr_ctx* c, int n, int K) {
     return AMR_OK;
 }
 
+// device address of a caller's host buffer that the GPU can access directly
+// (page-locked host memory, e.g. from cudaHostAlloc or PyTorch's pinned
+// memory), else nullptr: such buffers are read or written by the pack and
+// unpack kernels in one launch, other buffers go through the staging buffer
+void* mapped_host(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();                                // not a CUDA-known pointer: clear the error
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 template <typename T>
 int get_level_impl(amr_ctx* c, int level, int* n_out, int* coords, double* data) {
     std::vector<int> slots;
@@ -758,6 +771,17 @@ int get_level_impl(amr_ctx* c, int level, int* n_out, int* coords, double* data)
         long long ncell = 1;
         for (int d = 0; d < c->dim; ++d) ncell *= c->N;
         const size_t per = (size_t)c->nv * ncell;
+        if (double* dev = static_cast<double*>(mapped_host(data))) {   // straight into the caller's buffer
+            const int n = (int)slots.size();
+            CK(cudaMemcpyAsync(c->slots_d, slots.data(), n * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+               "get level");
+            CK(Kernels<T>::unpack_interiors(c->grid, St<T>(c, 0), c->slots_d, n, dev, c->stream), "unpack");
+            CK(cudaStreamSynchronize(c->stream), "get level");
+            c->h2d += n * sizeof(int);
+            c->d2h += (long long)(n * per * sizeof(double));
+            ++c->kernels;
+            return AMR_OK;
+        }
         const size_t chunk = std::max<size_t>(1, c->dense_cap / per);
         for (size_t b = 0; b < slots.size(); b += chunk) {
             const int n = (int)std::min(chunk, slots.size() - b);
@@ -815,7 +839,15 @@ int set_state_impl(amr_ctx* c, int n, const int* levels, const int* coords, cons
     const size_t chunk = std::max<size_t>(1, c->dense_cap / per);
     std::vector<int> slots(n);
     for (int i = 0; i < n; ++i) slots[i] = slot_lookup(c, keys[i]);
-    for (int b = 0; b < n; b += (int)chunk) {
+    const double* dev = static_cast<const double*>(mapped_host(data));   // read in place if possible
+    if (dev) {
+        CK(cudaMemcpyAsync(c->slots_d, slots.data(), n * sizeof(int), cudaMemcpyHostToDevice, c->stream), "set");
+        CK(Kernels<T>::pack_interiors(c->grid, St<T>(c, 0), c->slots_d, n, dev, c->stream), "pack");
+        CK(cudaStreamSynchronize(c->stream), "set");
+        c->h2d += (long long)(n * sizeof(int) + n * per * sizeof(double));
+        ++c->kernels;
+    }
+    for (int b = 0; dev == nullptr && b < n; b += (int)chunk) {
         const int m = (int)std::min<size_t>(chunk, n - b);
         CK(cudaMemcpyAsync(c->slots_d, slots.data() + b, m * sizeof(int), cudaMemcpyHostToDevice, c->stream), "set");
         CK(cudaMemcpyAsync(c->dense_d, data + (size_t)b * per, m * per * sizeof(double), cudaMemcpyHostToDevice,
