@@ -426,7 +426,7 @@ int enqueue_step(amr_ctx* c, bool with_cfl, bool skip_fill0, long long* nk) {
         CK(mark(c->ev[s][1]), "event");
         CK(Kernels<T>::rhs_stage(g, src, St<T>(c, 0), dst, reinterpret_cast<T*>(c->faces), s,
                                  grid_size(c, c->tune[AMR_TUNE_RHS_GRID]),
-                                 c->stream, -1),
+                                 c->stream, -1, 1),
            "rhs stage");
         CK(mark(c->ev[s][2]), "event");
         CK(Kernels<T>::reflux(g, dst, reinterpret_cast<T*>(c->faces), s, grid_size(c, c->tune[AMR_TUNE_REFLUX_GRID]),
@@ -434,7 +434,7 @@ int enqueue_step(amr_ctx* c, bool with_cfl, bool skip_fill0, long long* nk) {
            "reflux");
         CK(mark(c->ev[s][3]), "event");
         k += 2;
-        for (int l = c->L - 1; l >= 1; --l) {
+        for (int l = c->L - 2; l >= 1; --l) {             // level L - 1: fused into the RHS
             CK(Kernels<T>::restrict_level(g, dst, l, grid_size(c, c->tune[AMR_TUNE_RESTRICT_GRID]), c->stream, -1),
                "restrict");
             ++k;
@@ -971,9 +971,9 @@ int autotune_impl(amr_ctx* c) {
                 err = timed([&]() {
                     nk += 2;
                     const cudaError_t e =
-                        Kernels<T>::rhs_stage(g, A, St<T>(c, 0), B, faces, 0, grid_size(c, gr), c->stream, -1);
+                        Kernels<T>::rhs_stage(g, A, St<T>(c, 0), B, faces, 0, grid_size(c, gr), c->stream, -1, 1);
                     if (e != cudaSuccess) return e;
-                    return Kernels<T>::rhs_stage(g, B, A, A, faces, 2, grid_size(c, gr), c->stream, -1);
+                    return Kernels<T>::rhs_stage(g, B, A, A, faces, 2, grid_size(c, gr), c->stream, -1, 1);
                 }, t);
                 if (t < bestv) {
                     bestv = t;
@@ -994,10 +994,10 @@ int autotune_impl(amr_ctx* c) {
             return Kernels<T>::reflux(g, B, faces, 0, grid_size(c, gr), c->stream, -1);
         });
     }
-    if (err == cudaSuccess) {                            // restriction of every level of A
-        const int cands[] = {2, 4, 8, 16, 32};
+    if (err == cudaSuccess) {                            // restriction of the levels a step restricts
+        const int cands[] = {2, 4, 8, 16, 32};           // (the finest is fused into the RHS)
         err = tune_one(AMR_TUNE_RESTRICT_GRID, cands, 5, [&](int gr) {
-            for (int l = c->L - 1; l >= 1; --l) {
+            for (int l = c->L - 2; l >= 1; --l) {
                 ++nk;
                 const cudaError_t e = Kernels<T>::restrict_level(g, A, l, grid_size(c, gr), c->stream, -1);
                 if (e != cudaSuccess) return e;

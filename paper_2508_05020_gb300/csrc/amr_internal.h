@@ -111,9 +111,11 @@ struct Kernels {
                                   cudaStream_t s, int one_slot, int chunk = 512, bool stage_only = false);
     // compiled tile-shape candidates of the fused RHS for this grid and flux
     static int rhs_shapes(const Grid& g);
-    // RHS + SSP-RK3 stage of every patch (or one patch if one_slot >= 0)
+    // RHS + SSP-RK3 stage of every patch (or one patch if one_slot >= 0);
+    // fuse_restrict: patches of the finest level L - 1 also restrict their
+    // output into their parents (the restriction of level L - 1 is then done)
     static cudaError_t rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces,
-                                 int stage, int grid, cudaStream_t s, int one_slot);
+                                 int stage, int grid, cudaStream_t s, int one_slot, int fuse_restrict = 0);
     static cudaError_t reflux(const Grid& g, T* Uout, const T* faces, int stage, int grid,
                               cudaStream_t s, int one_slot);
     // covered cells of level-1 patches from the children of level `level`

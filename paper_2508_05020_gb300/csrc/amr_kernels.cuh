@@ -899,6 +899,38 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
     }
 }
 
+// Restriction mean of the 2^d children of a covered coarse cell, given in
+// lexicographic z, y, x order: (sum) * 2^-d, summed in FP64 (FP32 fields: an
+// error-free FP32 pair sum, rounded once). Shared by the restriction kernel
+// and the fused restriction of the RHS, so both give the same bits.
+template <typename T, int D>
+__device__ __forceinline__ T restrict_mean(const T (&ch)[1 << D]) {
+    constexpr int NCH = 1 << D;
+    constexpr double scale = D == 1 ? 0.5 : (D == 2 ? 0.25 : 0.125);
+    if constexpr (sizeof(T) == 4) {
+        // FP32 fields: the sum carried as an unevaluated pair s + e (Knuth's
+        // TwoSum adds each child without error into s and collects the
+        // rounding errors in e), rounded once; equal to the FP64 sum rounded
+        // to FP32 up to near-ties, at FP32 cost
+        float sum = ch[0], err = 0.0f;
+#pragma unroll
+        for (int k = 1; k < NCH; ++k) {
+            const float a = ch[k];
+            const float t = __fadd_rn(sum, a);
+            const float bv = __fsub_rn(t, sum);
+            const float e = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bv)), __fsub_rn(a, bv));
+            sum = t;
+            err = __fadd_rn(err, e);
+        }
+        return __fmul_rn(__fadd_rn(sum, err), (float)scale);
+    } else {
+        double acc = (double)ch[0];
+#pragma unroll
+        for (int k = 1; k < NCH; ++k) acc = acc + (double)ch[k];
+        return T(acc * scale);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K4: fused right-hand side and SSP-RK3 stage of a chunk of one leaf patch.
 // The chunk (DZ planes in 3D, the whole patch in 1D/2D) plus its ghost halo
@@ -906,6 +938,11 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
 // dimension at a time go to a shared buffer; each thread accumulates the
 // divergence of its own cells in registers, then writes
 // U_out = a U0 + b (U_s + dt R)  (a = 0, b = 1 in stage 1).
+// fuse_restrict: a chunk of a patch of the finest level L - 1 (>= 1) also
+// restricts its updated cells into the parent (restrict_mean, as the
+// restriction kernel does): the finest level is never the coarse side of a
+// reflux, so its stage output is final here, and its parent, whose cells are
+// all covered, is neither read by this launch nor refluxed.
 // ---------------------------------------------------------------------------
 // EXT: extra faces per dimension beyond the N + 1 of a patch row (2 for the
 // central scheme, whose divergence reads the faces at i -+ 3/2)
@@ -944,7 +981,7 @@ constexpr size_t rhs_smem_bytes() {
 template <typename T, int D, int N, int DZ, int NTH, int MINB, int FLUX>
 __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__ Us, const T* U0,
                                              T* Uout, T* __restrict__ faces,
-                                             int stage, int one_slot) {
+                                             int stage, int one_slot, int fuse_restrict) {
     constexpr bool CEN = FLUX == AMR_FLUX_CENTRAL;
     constexpr int EXT = CEN ? 2 : 0;                   // central: faces i - 3/2 .. N + 1/2 along d
     using C = Chunk<D, N, DZ, EXT>;
@@ -971,6 +1008,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
         const int slot = one_slot >= 0 ? one_slot : g.leaf_list[pi];
         const int lev = g.level[slot];
         const int pf = g.pflag[slot];
+        const bool fuse = fuse_restrict && lev == g.L - 1 && lev >= 1;
         // 1. stage the chunk and its halo as primitives, loading 16-byte vectors
         //    along x (slot rows are 16-byte aligned)
         {
@@ -1278,13 +1316,14 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
             } else if constexpr (D == 3) {
                 divergence(std::integral_constant<int, 2>{});
             }
-            // the next phase's faces overwrite the face buffer; after the last
-            // phase no barrier is needed: the update touches no shared memory,
-            // the next item's staging writes only the primitives (which no
-            // divergence reads), and its face pass starts after the barrier
-            // that ends that staging, which every thread reaches only after
-            // its divergence here
-            if (ph + 1 < NPH) __syncthreads();
+            // the next phase's faces overwrite the face buffer, and so does a
+            // fused restriction's copy of the update; otherwise no barrier is
+            // needed after the last phase: the update touches no shared
+            // memory, the next item's staging writes only the primitives
+            // (which no divergence reads), and its face pass starts after the
+            // barrier that ends that staging, which every thread reaches only
+            // after its divergence here
+            if (ph + 1 < NPH || fuse) __syncthreads();
         }
         // 3. stage update of the chunk's cells
 #pragma unroll
@@ -1303,6 +1342,35 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                     if (stage == 0) o = us + dt * R[n][v];
                     else o = ra * U0[id] + rb * (us + dt * R[n][v]);
                     Uout[id] = o;
+                    if (fuse) Fs[v * C::CELLS + cidx] = o;   // the chunk's output, [v][z][y][x]
+                }
+            }
+        }
+        // 4. fused restriction of the chunk's cells into the parent
+        if (fuse) {
+            constexpr int H = N / 2;
+            constexpr int HZ = D == 3 ? DZ / 2 : 1, HY = D >= 2 ? H : 1;
+            constexpr int NCC = HZ * HY * H;                // coarse cells of the chunk
+            static_assert(D < 3 || DZ % 2 == 0, "chunks hold whole coarse planes");
+            __syncthreads();
+            const int par = g.parent[slot];
+            if (par < 0) {
+                if (threadIdx.x == 0) atomicOr(&g.time->err, ERR_MESH);
+            } else {
+                const int ox = (g.coord[slot * 3 + 0] & 1) * H;
+                const int oy = D >= 2 ? (g.coord[slot * 3 + 1] & 1) * H : 0;
+                const int oz = D == 3 ? (g.coord[slot * 3 + 2] & 1) * H + z0 / 2 : 0;
+                for (int c = threadIdx.x; c < NV * NCC; c += NTH) {
+                    const int v = c / NCC, r = c - v * NCC;
+                    const int cx = r % H, cy = (r / H) % HY, cz = r / (H * HY);
+                    T ch[1 << D];                           // children in lexicographic z, y, x order
+#pragma unroll
+                    for (int k = 0; k < (1 << D); ++k) {
+                        const int ax = k & 1, ay = D >= 2 ? (k >> 1) & 1 : 0, az = D == 3 ? k >> 2 : 0;
+                        ch[k] = Fs[v * C::CELLS + ((2 * cz + az) * C::CY + 2 * cy + ay) * C::CX + 2 * cx + ax];
+                    }
+                    Uout[slot_index(g, par, v, D == 3 ? oz + cz + G : 0, D >= 2 ? oy + cy + G : 0, ox + cx + G)] =
+                        restrict_mean<T, D>(ch);
                 }
             }
         }
@@ -1403,7 +1471,6 @@ __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int o
     const int lo = g.level_off[level], hi = g.level_off[level + 1];
     const int npatch = one_slot >= 0 ? 1 : hi - lo;
     const long long total = (long long)npatch * HC;
-    const double scale = D == 1 ? 0.5 : (D == 2 ? 0.25 : 0.125);
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
          it += (long long)gridDim.x * blockDim.x) {
         const int pi = (int)(it / HC);
@@ -1436,29 +1503,7 @@ __global__ void __launch_bounds__(256) k_restrict(Grid g, T* U, int level, int o
                 T ch[NCH];
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) ch[k] = f[v][k >> 1][2 * q + (k & 1)];
-                T mean;
-                if constexpr (sizeof(T) == 4) {
-                    // FP32 fields: the sum carried as an unevaluated pair s + e
-                    // (Knuth's TwoSum adds each child without error into s and
-                    // collects the rounding errors in e), rounded once; equal to
-                    // the FP64 sum rounded to FP32 up to near-ties, at FP32 cost
-                    float sum = ch[0], err = 0.0f;
-#pragma unroll
-                    for (int k = 1; k < NCH; ++k) {
-                        const float a = ch[k];
-                        const float t = __fadd_rn(sum, a);
-                        const float bv = __fsub_rn(t, sum);
-                        const float e = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bv)), __fsub_rn(a, bv));
-                        sum = t;
-                        err = __fadd_rn(err, e);
-                    }
-                    mean = __fmul_rn(__fadd_rn(sum, err), (float)scale);
-                } else {
-                    double acc = (double)ch[0];
-#pragma unroll
-                    for (int k = 1; k < NCH; ++k) acc = acc + (double)ch[k];
-                    mean = T(acc * scale);
-                }
+                const T mean = restrict_mean<T, D>(ch);
                 U[slot_index(g, par, v, D == 3 ? oz + cz + G : 0, D >= 2 ? oy + cy + G : 0, ox + cx + q + G)] = mean;
             }
     }

@@ -47,34 +47,34 @@ inline double4 d4(const double* v) { return make_double4(v[0], v[1], v[2], v[3])
 
 template <typename T, int D, int N, int FLUX, int V>
 static void rhs_launch_v(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
-                         cudaStream_t s, int one_slot) {
+                         cudaStream_t s, int one_slot, int fuse) {
     using C = RhsCfg<T, D, N, V>;
     k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, FLUX>
-        <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, FLUX>(), s>>>(g, Us, U0, Uout, faces, stage, one_slot);
+        <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, FLUX>(), s>>>(g, Us, U0, Uout, faces, stage, one_slot, fuse);
 }
 
 template <typename T, int D, int N, int FLUX>
 static void rhs_launch_f(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
-                         cudaStream_t s, int one_slot) {
+                         cudaStream_t s, int one_slot, int fuse) {
     if constexpr (RhsShapes<T, D, N, FLUX>::n == 3) {
-        if (g.rhs_shape == 1) return rhs_launch_v<T, D, N, FLUX, 1>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
-        if (g.rhs_shape == 2) return rhs_launch_v<T, D, N, FLUX, 2>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+        if (g.rhs_shape == 1) return rhs_launch_v<T, D, N, FLUX, 1>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
+        if (g.rhs_shape == 2) return rhs_launch_v<T, D, N, FLUX, 2>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
     }
-    rhs_launch_v<T, D, N, FLUX, 0>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+    rhs_launch_v<T, D, N, FLUX, 0>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
 }
 
 template <typename T, int D, int N>
 static cudaError_t rhs_launch(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
-                              cudaStream_t s, int one_slot) {
+                              cudaStream_t s, int one_slot, int fuse) {
     // one instantiation per flux: the Rusanov kernel carries no HLLC code
     if (g.flux == AMR_FLUX_CENTRAL)
-        rhs_launch_f<T, D, N, AMR_FLUX_CENTRAL>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+        rhs_launch_f<T, D, N, AMR_FLUX_CENTRAL>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
     else if (g.flux == AMR_FLUX_HYBRID)
-        rhs_launch_f<T, D, N, AMR_FLUX_HYBRID>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+        rhs_launch_f<T, D, N, AMR_FLUX_HYBRID>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
     else if (g.flux == AMR_FLUX_HLLC)
-        rhs_launch_f<T, D, N, AMR_FLUX_HLLC>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+        rhs_launch_f<T, D, N, AMR_FLUX_HLLC>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
     else
-        rhs_launch_f<T, D, N, AMR_FLUX_RUSANOV>(g, Us, U0, Uout, faces, stage, grid, s, one_slot);
+        rhs_launch_f<T, D, N, AMR_FLUX_RUSANOV>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
     return cudaGetLastError();
 }
 
@@ -150,8 +150,8 @@ cudaError_t Kernels<T>::ghost_fill(const Grid& g, T* U, int level, double tfrac,
 
 template <typename T>
 cudaError_t Kernels<T>::rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
-                                  cudaStream_t s, int one_slot) {
-    AMR_DISPATCH(g, return (rhs_launch<T, D, N>(g, Us, U0, Uout, faces, stage, grid, s, one_slot)));
+                                  cudaStream_t s, int one_slot, int fuse_restrict) {
+    AMR_DISPATCH(g, return (rhs_launch<T, D, N>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse_restrict)));
     return cudaSuccess;
 }
 
