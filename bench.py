@@ -90,6 +90,21 @@ def rhs_traffic(workload_name, base, levels, leaves=None, shape=0):
     return int(round(b * leaves / RHS_TRAFFIC['leaves']))
 
 
+def parse_tuning(text):
+    """`name=value[,name=value]` (launch parameter names of amr.TUNE_NAMES,
+    integer values) as a dict; ValueError on a malformed item."""
+    out = {}
+    for item in text.split(','):
+        item = item.strip()
+        if not item:
+            continue
+        name, sep, value = item.partition('=')
+        if not sep or not name.strip():
+            raise ValueError('launch parameter %r is not name=value' % item)
+        out[name.strip()] = int(value)
+    return out
+
+
 def load_json(path, default):
     try:
         with open(path) as f:
@@ -526,7 +541,7 @@ def main():
     weights = load_weights(weights_name, w['dim']) if args.flagger == 'mlp' else None
     K_r = args.regrid_every or (4 if weights_name and '_k4' in weights_name else 1)
     amr = make_amr(AMR, w, args, args.flagger, weights, precision=args.precision)
-    pinned = {k: int(v) for k, v in (kv.split('=') for kv in args.set_tuning.split(',') if kv)}
+    pinned = parse_tuning(args.set_tuning)
     if pinned:
         amr.set_tuning(pinned)
     tuned, tuned_ms = amr.tuning()

@@ -6,6 +6,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -31,3 +33,17 @@ def test_reference_arm_line():
     e2e = line['e2e']
     assert e2e['value'] == line['value'] and e2e['unit'] == line['unit']
     assert e2e['h2d_bytes_per_step'] == 0 and e2e['d2h_bytes_per_step'] == 0
+
+
+def test_set_tuning_parsing():
+    """--set-tuning pins launch parameters by name (amr.TUNE_NAMES)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2508_05020_gb300.amr import TUNE_NAMES
+    got = bench.parse_tuning('rhs_tile_shape=2, rhs_ctas_per_sm=1,')
+    assert got == {'rhs_tile_shape': 2, 'rhs_ctas_per_sm': 1}
+    assert set(got) <= set(TUNE_NAMES)
+    assert bench.parse_tuning('') == {}
+    for bad in ('rhs_tile_shape', '=2', 'rhs_tile_shape=two'):
+        with pytest.raises(ValueError):
+            bench.parse_tuning(bad)
