@@ -334,8 +334,9 @@ int amr_harvest(amr_ctx* ctx, long* n, double* samples, uint8_t* labels);
  * through its captured CUDA graph (the events are event-record nodes of it),
  * or launch by launch when the context was created without graphs.
  * amr_get_timing synchronises and returns AMR_TIMING_SLOTS milliseconds.
- * Of the last step (CUDA events): ms[0] ghost fill, [1] fused RHS + stage,
- * [2] reflux, [3] restriction, [4] CFL reduction (0 if the step had a given
+ * Of the last step (CUDA events): ms[0] ghost fill, [1] fused RHS + stage
+ * (with the finest level's restriction), [2] reflux, [3] restriction of the
+ * coarser levels, [4] CFL reduction (0 if the step had a given
  * dt). Of the last regrid: [5] the flag kernel (plain or learned; CUDA
  * events), [6] host closure (wall), [7] table upload + new-patch fill (wall),
  * [8] the ghost fill that precedes flagging (CUDA events), [9] the whole

@@ -1674,7 +1674,8 @@ int amr_get_timing(amr_ctx* c, double ms[AMR_TIMING_SLOTS], int launches[AMR_TIM
     ms[9] = c->regrid_ms[0];
     if (launches) {
         const int rt = c->regrid_timed ? 1 : 0;
-        const int l[AMR_TIMING_SLOTS] = {3 * c->L, 3, 3, 3 * (c->L - 1), c->cfl_timed ? 2 : 0, rt, 0, 0,
+        // restriction: levels L-2..1 per stage (level L-1 is restricted inside the RHS launch)
+        const int l[AMR_TIMING_SLOTS] = {3 * c->L, 3, 3, 3 * std::max(c->L - 2, 0), c->cfl_timed ? 2 : 0, rt, 0, 0,
                                          rt * c->regrid_fill_launches, 0};
         for (int i = 0; i < AMR_TIMING_SLOTS; ++i) launches[i] = l[i];
     }

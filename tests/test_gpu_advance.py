@@ -89,3 +89,34 @@ def test_regrid_interval_equals_step_calls(name, base, precision, flagger, K):
         b.advance(1, regrid=-1)
     for o in (a, b, c):
         o.close()
+
+
+@pytest.mark.parametrize('levels', [2, 3])
+def test_step_timing_slots(levels):
+    """amr_set_timing / amr_get_timing on the batched step: every class timed,
+    the launch counts of the step's classes as issued (the finest level's
+    restriction runs inside the RHS launch, so the restriction slot has the
+    coarser levels only), and timing leaves the results unchanged."""
+    from paper_2508_05020_gb300.amr import AMR
+    w = workload('blast3d', base_cells=(32, 32, 32), levels=levels)
+    a = AMR(w, precision=32)
+    b = AMR(w, precision=32)
+    a.set_timing(True)
+    for _ in range(2):
+        assert a.step() == b.step()
+        a.regrid()
+        b.regrid()
+    a.advance(1, regrid=False)
+    b.advance(1, regrid=False)
+    ms, n = a.timing()
+    slots = dict(zip(AMR.TIMING_SLOTS, range(len(AMR.TIMING_SLOTS))))
+    assert ms[slots['rhs']] > 0 and ms[slots['ghost']] > 0 and ms[slots['cfl']] > 0
+    assert n[slots['rhs']] == 3 and n[slots['reflux']] == 3
+    assert n[slots['restrict']] == 3 * (levels - 2)
+    assert ms[slots['restrict']] >= 0 and (levels == 2 or ms[slots['restrict']] > 0)
+    for l in range(a.L):
+        ca, xa = a.get_level(l)
+        cb, xb = b.get_level(l)
+        assert np.array_equal(ca, cb) and np.array_equal(xa, xb)
+    a.close()
+    b.close()
