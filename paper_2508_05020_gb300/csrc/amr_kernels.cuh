@@ -665,12 +665,19 @@ __device__ __forceinline__ void load_meta_warp(const Grid& g, int slot, PatchMet
 // neighbour when it exists, as a stage leaves that face ghost of Q unfilled;
 // otherwise (new patches in a regrid, which may create that neighbour in the
 // same launch) from Q's ghost cells, filled before the mesh changed.
-template <typename T, int D, int N, bool NBR_READS>
-__device__ void prolong_cell(const Grid& g, const T* U, const PatchMeta& m, const int* l, T* out) {
-    constexpr int NV = D + 2;
+// The coarse cell C of fine local cell l: returns Q, the patch that holds C
+// (from the parent's neighbour table; -1 if there is none), and sets C's
+// local coordinates Lc in Q and the child index s of l (bit d: the upper half
+// along d)
+template <int D, int N>
+__device__ __forceinline__ int prolong_locate(const PatchMeta& m, const int* l, int* Lc, int* s) {
     const int* c = m.c;
-    const int par = m.par;
-    int Lc[3] = {0, 0, 0}, s[3] = {0, 0, 0}, oc[3] = {0, 0, 0};
+    int oc[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        Lc[d] = 0;
+        s[d] = 0;
+    }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         const int Gd = c[d] * N + l[d];
@@ -680,15 +687,15 @@ __device__ void prolong_cell(const Grid& g, const T* U, const PatchMeta& m, cons
         oc[d] = floordiv(Gc, N) - PC;
         Lc[d] = Gc - (PC + oc[d]) * N;
     }
-    const int Q = par >= 0 ? m.pnbr[(oc[2] + 1) * 9 + (oc[1] + 1) * 3 + (oc[0] + 1)] : -1;
-    if (Q < 0) {
-        atomicOr(&g.time->err, ERR_MESH);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) out[v] = T(0);
-        return;
-    }
+    return m.par >= 0 ? m.pnbr[(oc[2] + 1) * 9 + (oc[1] + 1) * 3 + (oc[0] + 1)] : -1;
+}
+
+// U_C and the minmod slopes of coarse cell Lc of Q (NBR_READS: see below)
+template <typename T, int D, int N, bool NBR_READS>
+__device__ __forceinline__ void prolong_slopes(const Grid& g, const T* U, int Q, const int* Lc, T (&UC)[D + 2],
+                                               T (&slope)[D][D + 2]) {
+    constexpr int NV = D + 2;
     const int bx = sc<D>(0, Lc[0]), by = sc<D>(1, Lc[1]), bz = sc<D>(2, Lc[2]);
-    T UC[NV], slope[D][NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) UC[v] = U[slot_index(g, Q, v, bz, by, bx)];
 #pragma unroll
@@ -715,31 +722,57 @@ __device__ void prolong_cell(const Grid& g, const T* U, const PatchMeta& m, cons
             slope[d][v] = (a * b <= T(0)) ? T(0) : pick;
         }
     }
+}
+
+// value of child ch of C: U_C + sum_d (+-1/4) s_d, dims in order
+template <typename T, int D>
+__device__ __forceinline__ void prolong_child(const T (&UC)[D + 2], const T (&slope)[D][D + 2], int ch,
+                                              T (&v)[D + 2]) {
+#pragma unroll
+    for (int k = 0; k < D + 2; ++k) v[k] = UC[k];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const bool up = (ch >> d) & 1;
+#pragma unroll
+        for (int k = 0; k < D + 2; ++k) v[k] = up ? v[k] + T(0.25) * slope[d][k] : v[k] - T(0.25) * slope[d][k];
+    }
+}
+
+// every child of C has rho > 0 and p > 0
+template <typename T, int D>
+__device__ __forceinline__ bool prolong_positive(const Grid& g, const T (&UC)[D + 2], const T (&slope)[D][D + 2]) {
     const T gm1 = T(g.gamma) - T(1);
     bool ok = true;
-    T chosen[NV];
 #pragma unroll
     for (int ch = 0; ch < (1 << D); ++ch) {
-        T v[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = UC[k];
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const bool up = (ch >> d) & 1;
-#pragma unroll
-            for (int k = 0; k < NV; ++k) v[k] = up ? v[k] + T(0.25) * slope[d][k] : v[k] - T(0.25) * slope[d][k];
-        }
+        T v[D + 2];
+        prolong_child<T, D>(UC, slope, ch, v);
         T rho, u[D], p, Tt;
         primitives<T, D>(v, gm1, rho, u, p, Tt);
         ok = ok && (rho > T(0)) && (p > T(0));
-        bool mine = true;
-#pragma unroll
-        for (int d = 0; d < D; ++d) mine = mine && (((ch >> d) & 1) == s[d]);
-        if (mine) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) chosen[k] = v[k];
-        }
     }
+    return ok;
+}
+
+template <typename T, int D, int N, bool NBR_READS>
+__device__ void prolong_cell(const Grid& g, const T* U, const PatchMeta& m, const int* l, T* out) {
+    constexpr int NV = D + 2;
+    int Lc[3], s[3];
+    const int Q = prolong_locate<D, N>(m, l, Lc, s);
+    if (Q < 0) {
+        atomicOr(&g.time->err, ERR_MESH);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out[v] = T(0);
+        return;
+    }
+    T UC[NV], slope[D][NV];
+    prolong_slopes<T, D, N, NBR_READS>(g, U, Q, Lc, UC, slope);
+    const bool ok = prolong_positive<T, D>(g, UC, slope);
+    int mine = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) mine |= s[d] << d;
+    T chosen[NV];
+    prolong_child<T, D>(UC, slope, mine, chosen);
 #pragma unroll
     for (int k = 0; k < NV; ++k) out[k] = ok ? chosen[k] : UC[k];
 }
@@ -852,10 +885,10 @@ __device__ void ghost_value(const Grid& g, const T* U, const PatchMeta& m, int* 
 // taken by one warp, which stages the patch's metadata in its own
 // shared-memory copy; warps never wait for one another.
 // ---------------------------------------------------------------------------
-template <typename T, int D, int N>
+template <typename T, int D, int N, bool STAGE>
 __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
-                                               double4 pre, double4 post, int chunk, int n_cells,
-                                               int stage_only) {
+                                               double4 pre, double4 post, int chunk, int n_cells) {
+    constexpr bool stage_only = STAGE;                  // compiled apart: the full fill keeps its registers
     constexpr int NV = D + 2;
     __shared__ PatchMeta metas[256 / 32];
     if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
@@ -882,8 +915,71 @@ __global__ void __launch_bounds__(256) k_ghost(Grid g, T* U, int level, double t
         const int g1 = min(g0 + chunk, run * span + span);
         const int slot = one_slot >= 0 ? one_slot : g.all_list[lo + pi];
         if (stage_only) {
-            const int d = run >> 1;
-            if (g.nbr[slot * NBR + 13 + ((run & 1) ? 1 : -1) * (d == 0 ? 1 : (d == 1 ? 3 : 9))] >= 0) continue;
+            const int d = run >> 1, side = run & 1;
+            const int across = g.nbr[slot * NBR + 13 + (side ? 1 : -1) * (d == 0 ? 1 : (d == 1 ? 3 : 9))];
+            if (across >= 0) continue;
+            if constexpr (STAGE) if (across == -1) {
+                // in the domain without a same-level patch: every cell of the box
+                // is prolonged; per coarse cell C of the box (2 layers along d,
+                // H^(d-1) across) one slope evaluation and positivity test, then
+                // the 4 or 8 children of C in the box are written, each with the
+                // value the per-cell path gives it
+                constexpr int H = N / 2;
+                constexpr int HT = D == 1 ? 1 : (D == 2 ? H : H * H);
+                constexpr int NCB = 2 * HT;
+                const int per = (NCB + nchunk - 1) / nchunk;
+                const int q0 = (rest - run * nchunk) * per, q1 = min(q0 + per, NCB);
+                load_meta_warp(g, slot, m);
+                for (int qc = q0 + lane; qc < q1; qc += 32) {
+                    const int layer = qc / HT, tq = qc - layer * HT;
+                    // a fine cell of the box among C's children (local coordinates)
+                    int l[3] = {0, 0, 0};
+                    const int t1 = tq % H, t2 = tq / H;
+                    int ti = 0;
+#pragma unroll
+                    for (int e = 0; e < D; ++e) {
+                        if (e == d) l[e] = side ? (layer ? N + 2 : N) : (layer ? -3 : -1);
+                        else l[e] = 2 * (ti++ == 0 ? t1 : t2);
+                    }
+                    int Lc[3], sr[3];
+                    const int Q = prolong_locate<D, N>(m, l, Lc, sr);
+                    T UC[NV], slope[D][NV];
+                    bool ok = false;
+                    if (Q < 0) {
+                        atomicOr(&g.time->err, ERR_MESH);
+                    } else {
+                        prolong_slopes<T, D, N, true>(g, U, Q, Lc, UC, slope);
+                        ok = prolong_positive<T, D>(g, UC, slope);
+                    }
+#pragma unroll
+                    for (int ch = 0; ch < (1 << D); ++ch) {
+                        int lc[3] = {0, 0, 0};
+                        bool in = true;
+#pragma unroll
+                        for (int e = 0; e < D; ++e) {
+                            lc[e] = l[e] - sr[e] + ((ch >> e) & 1);
+                            in = in && (e == d ? (side ? lc[e] >= N && lc[e] < N + G : lc[e] >= -G && lc[e] < 0)
+                                               : lc[e] >= 0 && lc[e] < N);
+                        }
+                        if (!in) continue;
+                        T val[NV];
+                        if (Q < 0) {
+#pragma unroll
+                            for (int v = 0; v < NV; ++v) val[v] = T(0);
+                        } else if (ok) {
+                            prolong_child<T, D>(UC, slope, ch, val);
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < NV; ++v) val[v] = UC[v];
+                        }
+#pragma unroll
+                        for (int v = 0; v < NV; ++v)
+                            U[slot_index(g, slot, v, sc<D>(2, lc[2]), sc<D>(1, lc[1]), sc<D>(0, lc[0]))] = val[v];
+                    }
+                }
+                __syncwarp();                            // the copy is read until here
+                continue;
+            }
         }
         load_meta_warp(g, slot, m);
         for (int gi = g0 + lane; gi < g1; gi += 32) {

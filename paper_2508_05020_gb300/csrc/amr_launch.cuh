@@ -143,8 +143,13 @@ cudaError_t Kernels<T>::ghost_fill(const Grid& g, T* U, int level, double tfrac,
                                    int one_slot, int chunk, bool stage_only) {
     if (chunk < 32) return cudaErrorInvalidValue;
     const int n_cells = stage_only ? g.n_ghost_face : g.n_ghost;
-    AMR_DISPATCH(g, (k_ghost<T, D, N><<<grid, 256, 0, s>>>(g, U, level, tfrac, one_slot, d4(g.dmr_pre),
-                                                            d4(g.dmr_post), chunk, n_cells, stage_only ? 1 : 0)));
+    if (stage_only) {
+        AMR_DISPATCH(g, (k_ghost<T, D, N, true><<<grid, 256, 0, s>>>(g, U, level, tfrac, one_slot, d4(g.dmr_pre),
+                                                                      d4(g.dmr_post), chunk, n_cells)));
+    } else {
+        AMR_DISPATCH(g, (k_ghost<T, D, N, false><<<grid, 256, 0, s>>>(g, U, level, tfrac, one_slot, d4(g.dmr_pre),
+                                                                       d4(g.dmr_post), chunk, n_cells)));
+    }
     return cudaGetLastError();
 }
 
