@@ -158,7 +158,9 @@ typedef struct {
                                    threads per CTA, resident CTAs per SM) candidate, 0 where only one is
                                    compiled (FP32 3D 16^3 patches, Rusanov flux: 0 = four planes, 256
                                    threads, 2 CTAs; 1 = two planes, 256 threads, 3 CTAs; 2 = eight planes,
-                                   512 threads, 1 CTA) */
+                                   512 threads, 1 CTA; 3 and 4 = shapes 0 and 2 with the halo planes
+                                   copied by TMA (tensor copies on an mbarrier) while the threads stage
+                                   the centre planes) */
 #define AMR_TUNE_N 8
 
 void amr_default_options(amr_options_t* opt);

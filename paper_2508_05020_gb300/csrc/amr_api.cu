@@ -1,6 +1,7 @@
 // C ABI of libamr (include/amr.h): context, patch pool, metadata tables,
 // step sequence (batched persistent kernels in a CUDA graph, or one launch per
 // patch per operation) and regrid.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -61,6 +62,10 @@ struct amr_ctx {
     // device memory
     std::vector<void*> allocs;
     void* U[3] = {nullptr, nullptr, nullptr};   // U0, Ua, Ub
+    // tensor maps of the three state arrays (FP32 3D 16^3 patches) for the RHS
+    // tile shapes that copy halo planes with TMA; tma_ok: encoded
+    CUtensorMap tmap[3] = {};
+    bool tma_ok = false;
     void* faces = nullptr;
     int* meta_d = nullptr;                     // all int tables, one block
     int* meta_h = nullptr;                     // pinned mirror
@@ -384,6 +389,45 @@ void drop_graphs(amr_ctx* c) {
 template <typename T>
 T* St(amr_ctx* c, int i) { return reinterpret_cast<T*>(c->U[i]); }
 
+// tensor map of the state array U for the RHS's halo copies (nullptr if none)
+const void* tmap_of(const amr_ctx* c, const void* U) {
+    if (!c->tma_ok) return nullptr;
+    for (int i = 0; i < 3; ++i)
+        if (c->U[i] == U) return &c->tmap[i];
+    return nullptr;
+}
+// the RHS tile shapes 3 and 4 (FP32 3D 16^3 patches) copy halo planes with TMA
+bool shape_needs_tma(const amr_ctx* c, int shape) { return c->precision == 32 && shape >= 3; }
+
+// Tensor maps of the three FP32 state arrays, viewed as 4D tensors
+// (x: SX, y: SY, z: SZ, slot x variable), boxes of N x N x G cells: the halo
+// planes of a chunk of one variable. cuTensorMapEncodeTiled is taken from the
+// driver through the runtime's entry-point query (no link to libcuda).
+bool encode_tmaps(amr_ctx* c) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        !fn || q != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const Grid& g = c->grid;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.SX, (cuuint64_t)g.SY, (cuuint64_t)g.SZ, (cuuint64_t)c->cap * c->nv};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.SX * 4, (cuuint64_t)g.SX * g.SY * 4, (cuuint64_t)g.slot_elems * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)g.N, (cuuint32_t)g.N, (cuuint32_t)G, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int i = 0; i < 3; ++i)
+        if (reinterpret_cast<Encode>(fn)(&c->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->U[i], dims, strides, box,
+                                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    return true;
+}
+
 template <typename T>
 int fill_all_levels(amr_ctx* c, T* U, double tfrac) {
     for (int l = 0; l < c->L; ++l) {
@@ -426,7 +470,7 @@ int enqueue_step(amr_ctx* c, bool with_cfl, bool skip_fill0, long long* nk) {
         CK(mark(c->ev[s][1]), "event");
         CK(Kernels<T>::rhs_stage(g, src, St<T>(c, 0), dst, reinterpret_cast<T*>(c->faces), s,
                                  grid_size(c, c->tune[AMR_TUNE_RHS_GRID]),
-                                 c->stream, -1, 1),
+                                 c->stream, -1, 1, tmap_of(c, src)),
            "rhs stage");
         CK(mark(c->ev[s][2]), "event");
         CK(Kernels<T>::reflux(g, dst, reinterpret_cast<T*>(c->faces), s, grid_size(c, c->tune[AMR_TUNE_REFLUX_GRID]),
@@ -471,7 +515,7 @@ int per_patch_step(amr_ctx* c, bool with_cfl) {
             }
         for (size_t i = 0; i < c->canon_slot.size(); ++i) {
             CK(Kernels<T>::rhs_stage(g, src, St<T>(c, 0), dst, reinterpret_cast<T*>(c->faces), s, 8, c->stream,
-                                     c->canon_slot[i]),
+                                     c->canon_slot[i], 0, tmap_of(c, src)),
                "rhs stage");
             ++c->kernels;
         }
@@ -965,15 +1009,18 @@ int autotune_impl(amr_ctx* c) {
         float bestv = 1e30f;
         int best_shape = 0, best_grid = c->tune[AMR_TUNE_RHS_GRID];
         for (int sh = 0; sh < shapes && err == cudaSuccess; ++sh) {
+            if (shape_needs_tma(c, sh) && !c->tma_ok) continue;
             c->grid.rhs_shape = sh;
             for (int gr = 1; gr <= 4 && err == cudaSuccess; ++gr) {
                 float t = 0.f;
                 err = timed([&]() {
                     nk += 2;
                     const cudaError_t e =
-                        Kernels<T>::rhs_stage(g, A, St<T>(c, 0), B, faces, 0, grid_size(c, gr), c->stream, -1, 1);
+                        Kernels<T>::rhs_stage(g, A, St<T>(c, 0), B, faces, 0, grid_size(c, gr), c->stream, -1, 1,
+                                              tmap_of(c, A));
                     if (e != cudaSuccess) return e;
-                    return Kernels<T>::rhs_stage(g, B, A, A, faces, 2, grid_size(c, gr), c->stream, -1, 1);
+                    return Kernels<T>::rhs_stage(g, B, A, A, faces, 2, grid_size(c, gr), c->stream, -1, 1,
+                                                 tmap_of(c, B));
                 }, t);
                 if (t < bestv) {
                     bestv = t;
@@ -1204,6 +1251,7 @@ int amr_init(amr_ctx** out, const amr_domain_t* dom, double gamma, const int bas
     c->time_d = (DevTime*)dalloc(c, sizeof(DevTime));
     for (int i = 0; i < 3; ++i)
         if (!c->U[i]) return fail(c, AMR_ERR_CUDA, "device allocation failed");
+    if (c->precision == 32 && dim == 3 && patch_size == 16) c->tma_ok = encode_tmaps(c);
     if (!c->faces || !c->meta_d || !c->anyflag || !c->req_d || !c->cons_partial || !c->cons_d || !c->dense_d ||
         !c->slots_d || !c->time_d)
         return fail(c, AMR_ERR_CUDA, "device allocation failed");
@@ -1607,7 +1655,8 @@ int amr_set_tuning(amr_ctx* c, const int params[AMR_TUNE_N]) {
         if (i == AMR_TUNE_GHOST_CHUNK) ok = v >= 32 && v <= 4096;
         else if (i == AMR_TUNE_RHS_SHAPE)
             ok = v >= 0 && v < (c->precision == 64 ? Kernels<double>::rhs_shapes(c->grid)
-                                                   : Kernels<float>::rhs_shapes(c->grid));
+                                                   : Kernels<float>::rhs_shapes(c->grid)) &&
+                 !(shape_needs_tma(c, v) && !c->tma_ok);
         else ok = v >= 1 && v <= 64;
         if (!ok) return fail(c, AMR_ERR_ARG, "launch parameter out of range");
     }

@@ -114,8 +114,11 @@ struct Kernels {
     // RHS + SSP-RK3 stage of every patch (or one patch if one_slot >= 0);
     // fuse_restrict: patches of the finest level L - 1 also restrict their
     // output into their parents (the restriction of level L - 1 is then done)
+    // tmap: the tensor map (CUtensorMap) of the state array Us, needed by the
+    // tile shapes that copy halo planes with TMA (else cudaErrorInvalidValue)
     static cudaError_t rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces,
-                                 int stage, int grid, cudaStream_t s, int one_slot, int fuse_restrict = 0);
+                                 int stage, int grid, cudaStream_t s, int one_slot, int fuse_restrict = 0,
+                                 const void* tmap = nullptr);
     static cudaError_t reflux(const Grid& g, T* Uout, const T* faces, int stage, int grid,
                               cudaStream_t s, int one_slot);
     // covered cells of level-1 patches from the children of level `level`

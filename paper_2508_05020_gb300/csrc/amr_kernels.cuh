@@ -5,6 +5,7 @@
 // FP64 unit is compiled with -fmad=false, so each operation rounds once and the
 // FP64 path reproduces an IEEE evaluation of the same formulas on the host.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <type_traits>
 #include <cstdint>
@@ -1042,16 +1043,18 @@ __device__ __forceinline__ T restrict_mean(const T (&ch)[1 << D]) {
 // ---------------------------------------------------------------------------
 // EXT: extra faces per dimension beyond the N + 1 of a patch row (2 for the
 // central scheme, whose divergence reads the faces at i -+ 3/2)
-template <int D, int N, int DZ, int EXT = 0> struct Chunk {
+// PADQ: per-variable blocks and the halo block start on 128-byte boundaries
+// (the halo planes are then tensor-copy destinations)
+template <int D, int N, int DZ, int EXT = 0, bool PADQ = false> struct Chunk {
     static constexpr int S = N + 2 * G;
     static constexpr int CX = N, CY = D >= 2 ? N : 1, CZ = D == 3 ? DZ : 1;
     // staged cells per variable: 1D/2D the whole slot; 3D the DZ centre planes
     // in full (S x S) and the 2G halo planes only over the interior N x N, the
     // only part the z-faces read
     static constexpr int QX = S, QY = D >= 2 ? S : 1, QZ = D == 3 ? DZ : 1;
-    static constexpr int QC = QX * QY * QZ;                       // centre cells
+    static constexpr int QC = PADQ ? (QX * QY * QZ + 31) / 32 * 32 : QX * QY * QZ;   // centre cells
     static constexpr int QH = D == 3 ? 2 * G * N * N : 0;         // compact halo cells
-    static constexpr int QN = QC + QH;
+    static constexpr int QN = PADQ ? (QC + QH + 31) / 32 * 32 : QC + QH;
     static constexpr int CELLS = CX * CY * CZ;
     static constexpr int NCH = D == 3 ? N / DZ : 1;
     static constexpr int F0 = (CX + 1 + EXT) * CY * CZ;
@@ -1068,26 +1071,84 @@ template <int D, int N, int DZ, int EXT = 0> struct Chunk {
     static constexpr int TRANS = D == 1 ? 1 : (D == 2 ? N : N * N);   // cells on a patch face
 };
 
-template <typename T, int D, int N, int DZ, int FLUX>
+template <typename T, int D, int N, int DZ, int FLUX, bool TMA = false>
 constexpr size_t rhs_smem_bytes() {
-    using C = Chunk<D, N, DZ, FLUX == AMR_FLUX_CENTRAL ? 2 : 0>;
-    return sizeof(T) * ((size_t)(D + 2) * C::QN + (size_t)(D + 2) * C::FMAX);
+    using C = Chunk<D, N, DZ, FLUX == AMR_FLUX_CENTRAL ? 2 : 0, TMA>;
+    // TMA: 128 bytes to align the base, an mbarrier and an abort word
+    return sizeof(T) * ((size_t)(D + 2) * C::QN + (size_t)(D + 2) * C::FMAX) + (TMA ? 128 + 16 : 0);
 }
 
-template <typename T, int D, int N, int DZ, int NTH, int MINB, int FLUX>
+// Tensor copies (TMA) of the halo planes: a 4D tiled load of a box into
+// shared memory, completing on an mbarrier with a transaction count
+__device__ __forceinline__ uint32_t rhs_smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void rhs_tma_load4(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                              uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void rhs_mbar_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(mbar), "r"(bytes)
+                 : "memory");
+}
+// wait for phase `parity` of the mbarrier: false once *abort is set, or after
+// TC_WAIT_CYCLES SM cycles (which sets *abort), so a copy that never lands
+// costs one bounded wait per CTA, not one per work item
+__device__ __forceinline__ bool rhs_mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
+    for (unsigned it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+        if ((it & 63u) == 63u && clock64() - t0 > TC_WAIT_CYCLES) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// TMA (3D, DZ >= 4): the 2G halo planes of a chunk arrive by tensor copies,
+// one 16 x 16 x 3 box per variable and side (each box has one source slot:
+// the same-level neighbour across z or the slot itself), issued by thread 0
+// while the other threads stage the centre planes; they land as conserved
+// variables in the halo block and are converted to primitives in place.
+template <typename T, int D, int N, int DZ, int NTH, int MINB, int FLUX, bool TMA = false>
 __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__ Us, const T* U0,
                                              T* Uout, T* __restrict__ faces,
-                                             int stage, int one_slot, int fuse_restrict) {
+                                             int stage, int one_slot, int fuse_restrict,
+                                             const __grid_constant__ CUtensorMap tmap) {
     constexpr bool CEN = FLUX == AMR_FLUX_CENTRAL;
     constexpr int EXT = CEN ? 2 : 0;                   // central: faces i - 3/2 .. N + 1/2 along d
-    using C = Chunk<D, N, DZ, EXT>;
+    static_assert(!TMA || (D == 3 && DZ >= 4 && sizeof(T) == 4 && !CEN), "halo boxes with one source slot");
+    using C = Chunk<D, N, DZ, EXT, TMA>;
     constexpr int NV = D + 2;
     constexpr int NT = D - 1;
     constexpr int CPT = (C::CELLS + NTH - 1) / NTH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (g.time->cancel) return;                          // a void step (see DevTime::cancel)
-    T* q = reinterpret_cast<T*>(smem_raw);                 // [NV][QZ][QY][QX]
+    unsigned char* sbase = smem_raw;
+    if constexpr (TMA)                                   // tensor-copy destinations: 128-byte aligned
+        sbase += (128u - (rhs_smem_addr(smem_raw) & 127u)) & 127u;
+    T* q = reinterpret_cast<T*>(sbase);                    // [NV][QZ][QY][QX]
     T* Fs = q + NV * C::QN;                               // [NV][FMAX]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(Fs + NV * C::FMAX);   // TMA: the halo copies' barrier
+    volatile int* tabort = reinterpret_cast<volatile int*>(mbar + 1);  // TMA: a wait gave up
+    uint32_t tparity = 0;
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rhs_smem_addr(mbar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            *tabort = 0;
+        }
+        __syncthreads();
+    }
     const T gamma = T(g.gamma);
     const T gm1 = T(g.gamma) - T(1);
     const double dtd = g.time->dt;
@@ -1149,6 +1210,30 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                 across(1, 0, sym, dym);
                 across(1, 1, syp, dyp);
             }
+            if constexpr (TMA) {
+                // the halo boxes: planes z0 .. z0 + 2 and z0 + DZ + 3 .. + 5 of the
+                // slot, from the z neighbour at the patch's ends (DZ >= 4: a box
+                // never straddles the interior's edge); interior x and y; the
+                // previous item's z faces, the last readers of this block, ended
+                // at a barrier this thread has passed
+                if (threadIdx.x == 0 && !*tabort) {
+                    int szm, dzm, szp, dzp;
+                    across(2, 0, szm, dzm);
+                    across(2, 1, szp, dzp);
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    const uint32_t mb = rhs_smem_addr(mbar);
+                    rhs_mbar_expect(mb, (uint32_t)(NV * C::QH * sizeof(T)));
+                    const int zl = z0 == 0 ? z0 + dzm : z0, wl = z0 == 0 ? szm : slot;
+                    const int zh = z0 + DZ + G + (z0 + DZ == N ? dzp : 0), wh = z0 + DZ == N ? szp : slot;
+                    constexpr int XP = PatchShape<T, N>::XP;
+#pragma unroll 1
+                    for (int v = 0; v < NV; ++v) {
+                        rhs_tma_load4(rhs_smem_addr(q + v * C::QN + C::QC), &tmap, XP + G, G, zl, wl * NV + v, mb);
+                        rhs_tma_load4(rhs_smem_addr(q + v * C::QN + C::QC + G * N * N), &tmap, XP + G, G, zh,
+                                      wh * NV + v, mb);
+                    }
+                }
+            }
             // centre planes (3D) or the whole slot (1D/2D): full rows; a row
             // outside the interior along y comes whole from its y source (its
             // x ghosts are edge cells, which no face reads)
@@ -1194,7 +1279,28 @@ __global__ void __launch_bounds__(NTH, MINB) k_rhs(Grid g, const T* __restrict__
                     if (qx >= 0 && qx < C::QX) stage(Uv, e, (qz * C::QY + qy) * C::QX + qx);
                 }
             }
-            if constexpr (D == 3) {
+            if constexpr (TMA) {
+                // the halo boxes have landed: conserved variables -> primitives
+                const bool landed = rhs_mbar_wait(rhs_smem_addr(mbar), tparity, tabort);
+                tparity ^= 1u;
+                if (!landed && threadIdx.x == 0) atomicOr(&g.time->err, ERR_TIMEOUT);
+#pragma unroll 2
+                for (int c = threadIdx.x; c < C::QH; c += NTH) {
+                    const int qidx = C::QC + c;
+                    T Uc[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Uc[v] = q[v * C::QN + qidx];
+                    T rho, u[D], p, Tt;
+                    primitives<T, D>(Uc, gm1, rho, u, p, Tt);
+                    q[qidx] = p;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) q[(1 + d) * C::QN + qidx] = u[d];
+                    q[(D + 1) * C::QN + qidx] = Tt;
+                }
+                // these generic writes before the next item's tensor copies into
+                // the block (ordered by the barriers between)
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            } else if constexpr (D == 3) {
                 // halo planes: interior x in [G, G + N), which starts on a
                 // 32-byte boundary, as N / VE aligned vectors, from the z
                 // source when the plane lies outside the interior

@@ -15,19 +15,32 @@ template <typename T, int D, int N, int V = 0> struct RhsCfg {
     static constexpr int DZ = D == 3 ? (sizeof(T) == 4 && N == 16 ? 4 : 2) : 1;
     static constexpr int NTH = D == 1 ? 64 : 256;
     static constexpr int MINB = (D == 3 && sizeof(T) == 4) ? (N == 16 ? 2 : 3) : 1;
+    static constexpr bool TMA = false;
 };
 // the other candidates of FP32 3D 16^3 patches: two-plane chunks (72 KB) at
 // three CTAs of at most 80 registers per SM (more warps to hide the staging
 // loads), and eight-plane chunks (195 KB) of 512 threads at one CTA per SM
-// (fewer halo planes staged per interior plane)
+// (fewer halo planes staged per interior plane); candidates 3 and 4 are 0 and 2
+// with the halo planes brought in by tensor copies (TMA) while the threads
+// stage the centre planes
 template <> struct RhsCfg<float, 3, 16, 1> {
     static constexpr int DZ = 2, NTH = 256, MINB = 3;
+    static constexpr bool TMA = false;
 };
 template <> struct RhsCfg<float, 3, 16, 2> {
     static constexpr int DZ = 8, NTH = 512, MINB = 1;
+    static constexpr bool TMA = false;
+};
+template <> struct RhsCfg<float, 3, 16, 3> {
+    static constexpr int DZ = 4, NTH = 256, MINB = 2;
+    static constexpr bool TMA = true;
+};
+template <> struct RhsCfg<float, 3, 16, 4> {
+    static constexpr int DZ = 8, NTH = 512, MINB = 1;
+    static constexpr bool TMA = true;
 };
 template <typename T, int D, int N, int FLUX> struct RhsShapes {
-    static constexpr int n = (sizeof(T) == 4 && D == 3 && N == 16 && FLUX == AMR_FLUX_RUSANOV) ? 3 : 1;
+    static constexpr int n = (sizeof(T) == 4 && D == 3 && N == 16 && FLUX == AMR_FLUX_RUSANOV) ? 5 : 1;
 };
 
 #define AMR_DISPATCH(g, CALL)                                   \
@@ -46,52 +59,64 @@ template <typename T, int D, int N, int FLUX> struct RhsShapes {
 inline double4 d4(const double* v) { return make_double4(v[0], v[1], v[2], v[3]); }
 
 template <typename T, int D, int N, int FLUX, int V>
-static void rhs_launch_v(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
-                         cudaStream_t s, int one_slot, int fuse) {
+static cudaError_t rhs_launch_v(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
+                                cudaStream_t s, int one_slot, int fuse, const CUtensorMap* tmap) {
     using C = RhsCfg<T, D, N, V>;
-    k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, FLUX>
-        <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, FLUX>(), s>>>(g, Us, U0, Uout, faces, stage, one_slot, fuse);
+    static const CUtensorMap none{};                     // the kernels without tensor copies ignore it
+    if (C::TMA && !tmap) return cudaErrorInvalidValue;   // no tensor map of this state array
+    k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, FLUX, C::TMA>
+        <<<grid, C::NTH, rhs_smem_bytes<T, D, N, C::DZ, FLUX, C::TMA>(), s>>>(g, Us, U0, Uout, faces, stage,
+                                                                          one_slot, fuse, tmap ? *tmap : none);
+    return cudaSuccess;
 }
 
 template <typename T, int D, int N, int FLUX>
-static void rhs_launch_f(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
-                         cudaStream_t s, int one_slot, int fuse) {
-    if constexpr (RhsShapes<T, D, N, FLUX>::n == 3) {
-        if (g.rhs_shape == 1) return rhs_launch_v<T, D, N, FLUX, 1>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
-        if (g.rhs_shape == 2) return rhs_launch_v<T, D, N, FLUX, 2>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
+static cudaError_t rhs_launch_f(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
+                                cudaStream_t s, int one_slot, int fuse, const CUtensorMap* tmap) {
+    if constexpr (RhsShapes<T, D, N, FLUX>::n == 5) {
+        switch (g.rhs_shape) {
+        case 1: return rhs_launch_v<T, D, N, FLUX, 1>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
+        case 2: return rhs_launch_v<T, D, N, FLUX, 2>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
+        case 3: return rhs_launch_v<T, D, N, FLUX, 3>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
+        case 4: return rhs_launch_v<T, D, N, FLUX, 4>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
+        default: break;
+        }
     }
-    rhs_launch_v<T, D, N, FLUX, 0>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
+    return rhs_launch_v<T, D, N, FLUX, 0>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
 }
 
 template <typename T, int D, int N>
 static cudaError_t rhs_launch(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
-                              cudaStream_t s, int one_slot, int fuse) {
+                              cudaStream_t s, int one_slot, int fuse, const CUtensorMap* tmap) {
     // one instantiation per flux: the Rusanov kernel carries no HLLC code
+    cudaError_t e;
     if (g.flux == AMR_FLUX_CENTRAL)
-        rhs_launch_f<T, D, N, AMR_FLUX_CENTRAL>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
+        e = rhs_launch_f<T, D, N, AMR_FLUX_CENTRAL>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
     else if (g.flux == AMR_FLUX_HYBRID)
-        rhs_launch_f<T, D, N, AMR_FLUX_HYBRID>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
+        e = rhs_launch_f<T, D, N, AMR_FLUX_HYBRID>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
     else if (g.flux == AMR_FLUX_HLLC)
-        rhs_launch_f<T, D, N, AMR_FLUX_HLLC>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
+        e = rhs_launch_f<T, D, N, AMR_FLUX_HLLC>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
     else
-        rhs_launch_f<T, D, N, AMR_FLUX_RUSANOV>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse);
-    return cudaGetLastError();
+        e = rhs_launch_f<T, D, N, AMR_FLUX_RUSANOV>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse, tmap);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T, int D, int N, int FLUX, int V>
 static cudaError_t rhs_prepare_v() {
     using C = RhsCfg<T, D, N, V>;
-    return cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, FLUX>,
+    return cudaFuncSetAttribute(k_rhs<T, D, N, C::DZ, C::NTH, C::MINB, FLUX, C::TMA>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)rhs_smem_bytes<T, D, N, C::DZ, FLUX>());
+                                (int)rhs_smem_bytes<T, D, N, C::DZ, FLUX, C::TMA>());
 }
 
 template <typename T, int D, int N, int FLUX>
 static cudaError_t rhs_prepare_f() {
     cudaError_t e = rhs_prepare_v<T, D, N, FLUX, 0>();
-    if constexpr (RhsShapes<T, D, N, FLUX>::n == 3) {
+    if constexpr (RhsShapes<T, D, N, FLUX>::n == 5) {
         if (e == cudaSuccess) e = rhs_prepare_v<T, D, N, FLUX, 1>();
         if (e == cudaSuccess) e = rhs_prepare_v<T, D, N, FLUX, 2>();
+        if (e == cudaSuccess) e = rhs_prepare_v<T, D, N, FLUX, 3>();
+        if (e == cudaSuccess) e = rhs_prepare_v<T, D, N, FLUX, 4>();
     }
     return e;
 }
@@ -155,8 +180,9 @@ cudaError_t Kernels<T>::ghost_fill(const Grid& g, T* U, int level, double tfrac,
 
 template <typename T>
 cudaError_t Kernels<T>::rhs_stage(const Grid& g, const T* Us, const T* U0, T* Uout, T* faces, int stage, int grid,
-                                  cudaStream_t s, int one_slot, int fuse_restrict) {
-    AMR_DISPATCH(g, return (rhs_launch<T, D, N>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse_restrict)));
+                                  cudaStream_t s, int one_slot, int fuse_restrict, const void* tmap) {
+    AMR_DISPATCH(g, return (rhs_launch<T, D, N>(g, Us, U0, Uout, faces, stage, grid, s, one_slot, fuse_restrict,
+                                                static_cast<const CUtensorMap*>(tmap))));
     return cudaSuccess;
 }
 

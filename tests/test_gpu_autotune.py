@@ -42,7 +42,7 @@ def test_autotune_leaves_results_unchanged(name, base, precision):
                   'rhs_tile_shape': 0}
     assert pb['ghost_ctas_per_sm'] in (4, 8, 16, 32) and pb['ghost_cells_per_item'] in (64, 128, 256, 512, 1024)
     assert pb['rhs_ctas_per_sm'] in (1, 2, 3, 4)
-    assert pb['rhs_tile_shape'] in ((0, 1, 2) if (w['dim'], w['patch'], precision) == (3, 16, 32) else (0,))
+    assert pb['rhs_tile_shape'] in ((0, 1, 2, 3, 4) if (w['dim'], w['patch'], precision) == (3, 16, 32) else (0,))
     assert all(tb[k] > 0 for k in TUNE_NAMES)
     # tuning again leaves the state, time and dt untouched
     s0, d0 = snapshot(b)
@@ -67,12 +67,13 @@ def test_autotune_leaves_results_unchanged(name, base, precision):
 
 def test_every_rhs_tile_shape_gives_the_same_bits():
     """The fused RHS's tile-shape candidates of FP32 3D 16^3 patches (four-,
-    two- and eight-plane z chunks) and other grids, set by amr_set_tuning:
-    the same results bit for bit; parameters out of range are refused."""
+    two- and eight-plane z chunks; four- and eight-plane chunks with the halo
+    planes copied by TMA) and other grids, set by amr_set_tuning: the same
+    results bit for bit; parameters out of range are refused."""
     from paper_2508_05020_gb300.amr import AMR, AMRError
     w = workload('blast3d', base_cells=(32, 32, 32))
     runs = []
-    for shape, grid in ((0, 2), (1, 3), (2, 1), (1, 1)):
+    for shape, grid in ((0, 2), (1, 3), (2, 1), (1, 1), (3, 2), (4, 1), (3, 4)):
         a = AMR(w, precision=32)
         a.set_tuning({'rhs_tile_shape': shape, 'rhs_ctas_per_sm': grid})
         assert a.tuning()[0]['rhs_tile_shape'] == shape
@@ -81,7 +82,7 @@ def test_every_rhs_tile_shape_gives_the_same_bits():
             a.regrid()
         runs.append(snapshot(a))
         if shape == 0:
-            for bad in ({'rhs_tile_shape': 3}, {'rhs_tile_shape': -1}, {'ghost_cells_per_item': 16},
+            for bad in ({'rhs_tile_shape': 5}, {'rhs_tile_shape': -1}, {'ghost_cells_per_item': 16},
                         {'cfl_ctas_per_sm': 0}):
                 with pytest.raises(AMRError):
                     a.set_tuning(bad)
