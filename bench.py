@@ -49,14 +49,15 @@ WEIGHTS_DIR = os.path.join(ROOT, 'paper_2508_05020_gb300', 'weights')
 # EOS, WENO5, face fluxes, the kernel and its launch) hash as recorded. Leaves
 # are independent work items, so a launch over another hierarchy of the same
 # workload moves this figure per leaf times its leaves.
-RHS_TRAFFIC = {'bytes': {0: 1131958784 + 415880448, 2: 973545216 + 413468160}, 'leaves': 4656, 'workload': 'blast3d', 'base': 128, 'levels': 3,
+RHS_TRAFFIC = {'bytes': {0: 1132389888 + 414993152, 2: 969363200 + 412371456, 3: 1134521856 + 417061376,
+                         4: 962697984 + 413609984}, 'leaves': 4656, 'workload': 'blast3d', 'base': 128, 'levels': 3,
                'regions': [('paper_2508_05020_gb300/csrc/amr_kernels.cuh', 'template <typename T> struct Num;',
                             '// Metadata of one patch staged'),
                            ('paper_2508_05020_gb300/csrc/amr_kernels.cuh', '// K4: fused right-hand side',
                             '// K5: coarse-fine flux correction'),
                            ('paper_2508_05020_gb300/csrc/amr_launch.cuh', 'template <typename T, int D, int N, int V = 0> struct RhsCfg',
                             'template <typename T>\ncudaError_t Kernels<T>::prepare')],
-               'hash': 'b6b57297e221ebb2'}
+               'hash': '2e0f7a645a629b19'}
 
 
 def rhs_source_hash():
