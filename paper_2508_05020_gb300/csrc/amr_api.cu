@@ -1011,7 +1011,11 @@ int autotune_impl(amr_ctx* c) {
         for (int sh = 0; sh < shapes && err == cudaSuccess; ++sh) {
             if (shape_needs_tma(c, sh) && !c->tma_ok) continue;
             c->grid.rhs_shape = sh;
-            for (int gr = 1; gr <= 4 && err == cudaSuccess; ++gr) {
+            // CTAs per SM of grid: beyond the resident count, a finer share of
+            // the work items per CTA evens out the tail of a launch
+            const int rgrid[] = {1, 2, 3, 4, 6, 8, 12, 16};
+            for (int gi = 0; gi < 8 && err == cudaSuccess; ++gi) {
+                const int gr = rgrid[gi];
                 float t = 0.f;
                 err = timed([&]() {
                     nk += 2;
