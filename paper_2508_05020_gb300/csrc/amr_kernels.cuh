@@ -887,7 +887,7 @@ __device__ void ghost_value(const Grid& g, const T* U, const PatchMeta& m, int* 
 // shared-memory copy; warps never wait for one another.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int N, bool STAGE>
-__global__ void __launch_bounds__(256, STAGE ? 3 : 0) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
+__global__ void __launch_bounds__(256, STAGE && sizeof(T) == 4 ? 3 : 0) k_ghost(Grid g, T* U, int level, double tfrac, int one_slot,
                                                double4 pre, double4 post, int chunk, int n_cells) {
     constexpr bool stage_only = STAGE;                  // compiled apart: the full fill keeps its registers
     constexpr int NV = D + 2;
